@@ -1,0 +1,149 @@
+"""Physics pins for the oracle Hamiltonian (Eq. hloc, Eq. hnloc, Eq. cellHam).
+
+Hermiticity, Kramers degeneracy, spin-rotation invariance with spin-orbit
+coupling off (and its breaking with it on), the separable harmonic
+oscillator (exact 1D tensor-product pin and continuum levels), and the
+algebra of the l = 1 spin-orbit projectors.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sps
+import scipy.sparse.linalg as spla
+
+from oracle import Hamiltonian, Mesh, p_orbital_L, soc_delta
+from oracle.hamiltonian import PAULI
+from oracle_cases import build_oracle, small_workload
+
+
+def test_hermitian_and_mass_positive():
+    H, *_ = build_oracle(small_workload())
+    Hd = H.dense()
+    assert np.max(np.abs(Hd - Hd.conj().T)) <= 1e-14 * np.max(np.abs(Hd))
+    assert np.all(H.Mdiag > 0)
+    # the nonlocal part really is present and couples the two spins
+    assert len(H.projectors) == 2
+    off = Hd[0::2, 1::2]
+    assert np.max(np.abs(off)) > 1e-6
+
+
+def test_kramers_degeneracy_without_B():
+    H, *_ = build_oracle(small_workload(), with_b=False)
+    lam = sla.eigh(H.dense(), np.diag(H.Mdiag), eigvals_only=True)
+    assert np.max(np.abs(lam[0::2] - lam[1::2])) < 1e-10
+    # with B on, the pairs split
+    H2, *_ = build_oracle(small_workload())
+    lam2 = sla.eigh(H2.dense(), np.diag(H2.Mdiag), eigvals_only=True)
+    assert np.max(np.abs(lam2[0::2] - lam2[1::2])) > 1e-4
+
+
+def _rotation(axis, angle):
+    axis = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + np.sin(angle) * K + (1 - np.cos(angle)) * K @ K
+
+
+def test_global_spin_rotation_of_B():
+    w = small_workload()
+    # SOC off: equal radial widths and equal couplings make the projector term spin-independent
+    H0, prm, V, B = build_oracle(w)
+    prm = dict(prm)
+    prm["proj_width"] = np.repeat(prm["proj_width"][:, :1], 2, axis=1)
+    prm["proj_h"] = np.repeat(prm["proj_h"][:, :1], 2, axis=1)
+    Rm = _rotation([0.3, -1.0, 0.5], 1.1)
+    Brot = np.einsum("de,eqk->dqk", Rm, B)
+    m = H0.mesh
+
+    def eig(Bf, p):
+        Hx = Hamiltonian(m, V, Bf, p["atoms"], p["proj_width"], p["proj_h"])
+        return sla.eigh(Hx.dense(), np.diag(Hx.Mdiag), eigvals_only=True)
+
+    off = np.max(np.abs(eig(B, prm) - eig(Brot, prm)))
+    assert off < 1e-10
+    # SOC on (the drawn couplings): a spin-only rotation is no longer a symmetry
+    _, prm_on, _, _ = build_oracle(w)
+    on = np.max(np.abs(eig(B, prm_on) - eig(Brot, prm_on)))
+    assert on > 1e-6
+
+
+def _one_d_ho(m, d, omega, x0):
+    K, W = m.assembled_1d(d)
+    idx = np.arange(m.G[d])
+    x = (idx // m.p) * m.h[d] + (m.xi[idx % m.p] + 1.0) * m.h[d] / 2.0
+    dx = x - x0
+    dx -= m.L[d] * np.round(dx / m.L[d])
+    A = 0.5 * K + np.diag(W * 0.5 * omega ** 2 * dx ** 2)
+    return sla.eigh(A, np.diag(W), eigvals_only=True)
+
+
+def _ho_hamiltonian(m, omega, x0):
+    q = m.quad_coords().reshape(-1, 3)
+    d = q - x0
+    d -= m.L * np.round(d / m.L)
+    V = 0.5 * omega ** 2 * np.sum(d * d, axis=1)
+    return Hamiltonian(m, V.reshape(m.ncells, m.nloc))
+
+
+def test_harmonic_oscillator_separable_exact():
+    m = Mesh((2, 2, 1), (5.0, 6.0, 3.0), 3)
+    x0 = np.array([2.2, 3.1, 1.4])
+    H = _ho_hamiltonian(m, 1.3, x0)
+    lam = sla.eigh(H.dense(), np.diag(H.Mdiag), eigvals_only=True)
+    e = [_one_d_ho(m, d, 1.3, x0[d]) for d in range(3)]
+    sums = np.sort((e[0][:, None, None] + e[1][None, :, None] + e[2][None, None, :]).ravel())
+    np.testing.assert_allclose(lam, np.sort(np.repeat(sums, 2)), atol=1e-9)
+
+
+def test_harmonic_oscillator_continuum_levels():
+    """omega (n + 3/2), degeneracy (n+1)(n+2)/2, for omega = 2 in an 8-bohr box.
+
+    H has no B and no projectors here, so it is real and spin-diagonal: the
+    spin-up block alone carries every level once.  The 1D factor converges
+    to omega (n + 1/2) as p grows."""
+    m = Mesh(2, 8.0, 8)
+    H = _ho_hamiltonian(m, 2.0, np.array([4.0, 4.0, 4.0]))
+    A = H.Hloc[0::2, 0::2].real.tocsc()
+    lam = np.sort(spla.eigsh(A, k=7, M=sps.diags(H.mass).tocsc(), sigma=0.0,
+                             return_eigenvectors=False))
+    ref = np.array([3.0] * 1 + [5.0] * 3 + [7.0] * 3)
+    assert np.max(np.abs(lam[:4] - ref[:4])) < 3e-3
+    assert np.max(np.abs(lam - ref)) < 3e-2
+    errs = []
+    for p in (4, 6, 8):
+        e1 = _one_d_ho(Mesh(4, 8.0, p), 0, 2.0, 4.0)[:3]
+        errs.append(np.max(np.abs(e1 - 2.0 * (np.arange(3) + 0.5))))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-4
+
+
+def test_soc_projector_algebra():
+    L = p_orbital_L()
+    # angular momentum commutation [L_x, L_y] = i L_z
+    assert np.allclose(L[0] @ L[1] - L[1] @ L[0], 1j * L[2])
+    Ls = sum(np.kron(L[k], PAULI[k]) for k in range(3))
+    P_half = (np.eye(6) - Ls) / 3
+    P_3half = (2 * np.eye(6) + Ls) / 3
+    for P, tr in ((P_half, 2), (P_3half, 4)):
+        assert np.allclose(P @ P, P) and np.allclose(P, P.conj().T)
+        assert abs(np.trace(P).real - tr) < 1e-14
+    assert np.allclose(P_half @ P_3half, 0)
+    assert np.allclose(P_half + P_3half, np.eye(6))
+    D = soc_delta(0.03, 0.07)
+    assert np.allclose(D, D.conj().T)
+    # time reversal Theta = (I_3 (x) i sigma_y) K commutes with Delta
+    T = np.kron(np.eye(3), 1j * PAULI[1])
+    assert np.allclose(T @ np.conj(soc_delta(0.03, 0.07)[6:, 6:]) @ np.linalg.inv(T), D[6:, 6:])
+    assert np.allclose(T @ np.conj(D[:6, :6]) @ np.linalg.inv(T), D[:6, :6])
+
+
+def test_projector_normalisation_converges():
+    """sum_I M_I beta(x_I)^2 -> int beta^2 = 1 under refinement."""
+    errs = []
+    for p in (3, 5, 7):
+        m = Mesh(4, 8.0, p)
+        H = Hamiltonian(m, np.zeros((m.ncells, m.nloc)), None, np.array([[3.3, 4.1, 3.9]]),
+                        np.array([[0.7, 0.7]]), np.array([[0.05, 0.05]]))
+        pr = H.projectors[0]
+        n2 = np.sum(H.mass[pr["support"], None] * pr["beta"] ** 2, axis=0)
+        errs.append(np.max(np.abs(n2 - 1.0)))
+    assert errs[2] < errs[0]
+    assert errs[2] < 1e-3
