@@ -1,0 +1,190 @@
+/*
+ * rchfsi.h - C ABI of the GB300 (sm_103a) R-ChFSI filter library (librchfsi.so).
+ *
+ * What it computes (arXiv 2605.30128):
+ *   the residual-based Chebyshev filtered subspace iteration (R-ChFSI) for the
+ *   noncollinear / spin-orbit finite-element eigenproblem H X = M X Lambda
+ *   (Section III-B-2, Eq. ghep, Eq. rChFSIrecurrence, Algorithm 1), with
+ *   H = H_loc + H_nloc (Eq. hloc, Eq. hnloc, Eq. cellHam) discretised on a
+ *   periodic hexahedral mesh with Lagrange degree p on GLL nodes (Section
+ *   III-A, Eq. FEWfns) and the GLL-lumped diagonal mass D = M.
+ *
+ * Conventions shared by every entry point
+ *   - Numbering: global node I = i + Gx (j + Gy k) with G_d = ncell_d * p;
+ *     cell e = ex + nx (ey + ny ez); local node l = a + np (b + np c),
+ *     np = p + 1; spinor row 2 I + alpha (alpha = 0 up, 1 down).
+ *   - Multivectors are COLUMN-MAJOR complex arrays: vector j starts at
+ *     element j * ld and holds rows 0 .. 2M-1 contiguously; ld >= 2M and ld
+ *     even, counted in complex elements.  "c128" = interleaved (re, im)
+ *     doubles; base pointers 32-byte aligned.  They are DEVICE pointers
+ *     unless stated otherwise, owned by the caller, on the device of the
+ *     context.
+ *   - Every call returns an rcf_status (0 = OK) and never throws; the text of
+ *     the last failure is rcf_last_error(ctx).  Work is enqueued on the
+ *     context's stream; results are valid after that stream synchronises.
+ *     Calls that return host scalars (Lanczos bounds, Rayleigh-Ritz values)
+ *     synchronise the stream themselves.
+ *   - Nothing here allocates memory that the caller must free, except the
+ *     handles, which the matching *_destroy releases.  Scratch memory is owned
+ *     by the context and reused across calls.
+ */
+#ifndef RCHFSI_H
+#define RCHFSI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rcf_ctx rcf_ctx;
+typedef struct rcf_mesh rcf_mesh;
+typedef struct rcf_op rcf_op;
+
+typedef enum {
+  RCF_OK = 0,
+  RCF_EINVAL = 1,    /* bad argument: null pointer, size, alignment, bounds order */
+  RCF_ENOMEM = 2,    /* device or host allocation failed */
+  RCF_ECUDA = 3,     /* a CUDA, cuBLAS or cuSOLVER call failed */
+  RCF_ENOTSPD = 4,   /* Cholesky-QR met a Gram matrix that is not positive definite */
+  RCF_ETIMEOUT = 5,  /* a bounded device-side wait ran out */
+  RCF_ENOTSUP = 6    /* combination not built (e.g. degree p > 8) */
+} rcf_status;
+
+/* Arithmetic of the filter's Hamiltonian-multivector products. */
+typedef enum { RCF_FP64 = 0, RCF_FP32 = 1 } rcf_precision;
+
+/* Filter form: plain ChFSI (Eq. ChFSIrecurrence) or R-ChFSI (Eq. rChFSIrecurrence). */
+typedef enum { RCF_CHFSI = 0, RCF_RCHFSI = 1 } rcf_mode;
+
+/* Operator form for rcf_apply: H, D^{-1} H or H D^{-1}. */
+typedef enum { RCF_FORM_H = 0, RCF_FORM_DINV_H = 1, RCF_FORM_H_DINV = 2 } rcf_form;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`, enqueueing all work on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The stream is borrowed,
+ * not owned.  Creates the cuBLAS / cuSOLVER handles used by Rayleigh-Ritz. */
+int rcf_create(rcf_ctx** out, int device, void* stream);
+int rcf_destroy(rcf_ctx* ctx);
+const char* rcf_status_string(int status);
+const char* rcf_last_error(const rcf_ctx* ctx);
+/* Block the host until the context's stream has finished. */
+int rcf_sync(rcf_ctx* ctx);
+
+/* ---- mesh (Section III-A) -------------------------------------------- */
+
+/* Periodic box of ncell[0] x ncell[1] x ncell[2] hexahedral cells with sides
+ * side[0..2] (bohr) and Lagrange degree p (1 <= p <= 8) on GLL nodes, GLL
+ * quadrature collocated with the nodes.  Host arrays are copied. */
+int rcf_mesh_create(rcf_ctx* ctx, const int ncell[3], const double side[3], int p, rcf_mesh** out);
+int rcf_mesh_destroy(rcf_mesh* mesh);
+/* Number of global nodes M (2M complex spinor DoF), cells, and nodes per cell (p+1)^3. */
+int rcf_mesh_info(const rcf_mesh* mesh, int64_t* nnodes, int64_t* ncells, int* nloc);
+/* Local-to-global map R^(e) (Section III-B-3, stage i) as int32 [ncells][nloc] into a host buffer. */
+int rcf_mesh_connectivity(const rcf_mesh* mesh, int32_t* host_out);
+/* Quadrature-point coordinates (= local GLL nodes, unwrapped) [ncells][nloc][3] into a host buffer. */
+int rcf_mesh_quadrature_points(const rcf_mesh* mesh, double* host_out);
+/* GLL-lumped mass M_I = sum_{(e,l) -> I} w_l |J|, [nnodes] into a host buffer. */
+int rcf_mesh_mass(const rcf_mesh* mesh, double* host_out);
+
+/* ---- operator: H and D = M (Eq. hloc, Eq. hnloc, Eq. cellHam) --------- */
+
+/* Operator on a mesh; V = B = 0 and no projectors until set.  The mesh must
+ * outlive the operator. */
+int rcf_op_create(rcf_ctx* ctx, const rcf_mesh* mesh, rcf_op** out);
+int rcf_op_destroy(rcf_op* op);
+/* Spinor potential at quadrature points: V [ncells][nloc], B [3][ncells][nloc]
+ * (B may be NULL for B = 0), FP64.  on_device = 0: host arrays; 1: device
+ * arrays.  Each node receives the 2x2 block sum_e w_q |J| (V I + B . sigma).
+ * Copied; the caller keeps ownership. */
+int rcf_potential_set(rcf_op* op, const double* V, const double* B, int on_device);
+/* Spin-orbit projectors (Eq. hnloc): per atom a, position pos[a][3], radial
+ * widths width[a][2] and couplings h[a][2] for channels j = 1/2, 3/2 (host
+ * arrays).  beta_{j,i}(r) = N_j d_i exp(-|d|^2 / 2 s_j^2) on |d| < rcut_factor
+ * s_j (d: minimum-image offset, int beta^2 = 1); Delta_a = h_{1/2} P_{1/2} (+)
+ * h_{3/2} P_{3/2}, P_{3/2} = (2 + L.sigma)/3, P_{1/2} = (1 - L.sigma)/3.
+ * natoms = 0 removes them. */
+int rcf_projectors_set(rcf_op* op, int natoms, const double* pos, const double* width,
+                       const double* h, double rcut_factor);
+/* Replace only the couplings h[natoms][2] (host). */
+int rcf_projectors_couplings(rcf_op* op, const double* h);
+/* Number of support nodes of atom `atom`; if host_nodes != NULL also the
+ * sorted global node indices (int32, `*count` entries). */
+int rcf_projector_support(const rcf_op* op, int atom, int64_t* count, int32_t* host_nodes);
+
+/* ---- Hamiltonian-multivector products --------------------------------- */
+
+/* Y = op(X) with op = H, D^{-1} H or H D^{-1} (rcf_form), for nvec vectors.
+ * prec = RCF_FP64: X, Y are c128; prec = RCF_FP32: X, Y are complex64
+ * (interleaved floats, 16-byte aligned).  Y must not overlap X. */
+int rcf_apply(rcf_ctx* ctx, const rcf_op* op, int form, const void* X, int64_t ldx, int nvec,
+              void* Y, int64_t ldy, int prec);
+
+/* ---- filter bounds (Section III-B-2; Lanczos as in Section III-C-1) --- */
+
+/* nsteps of Lanczos on D^{-1/2} H D^{-1/2} from the device c128 vector v0
+ * [2M] (not modified; need not be normalised).  Writes host scalars:
+ * *theta_min = smallest Ritz value, *upper = largest Ritz value + |beta_m|
+ * (the filter's lambda_max).  Synchronises. */
+int rcf_lanczos_bounds(rcf_ctx* ctx, const rcf_op* op, int nsteps, const double* v0,
+                       double* theta_min, double* upper);
+
+/* ---- residual (Algorithm 1, FP64) -------------------------------------- */
+
+/* R = H X - M X diag(ritz) in FP64.  ritz: host [nvec].  R (c128, ld ldr) and
+ * colnorm (device double [nvec], 2-norms of the columns of R) may each be
+ * NULL when not wanted. */
+int rcf_residual(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
+                 const double* ritz, double* R, int64_t ldr, double* colnorm);
+
+/* ---- the filter (Eq. ChFSIrecurrence / Eq. rChFSIrecurrence) ---------- */
+
+/* Y = filtered block of X, degree q = `degree` >= 1, bounds = {lambda_min,
+ * lambda_T, lambda_max} (host; need lambda_min < lambda_T < lambda_max).
+ * mode RCF_RCHFSI: R = H X - M X Lambda (FP64), Z_0 = 0, Z_1 = sigma_1 R / e,
+ * the residual recurrence in `prec`, Lambda_k propagated in FP64, recovery
+ * Y = D^{-1} Z_q + X Lambda_q in FP64.  mode RCF_CHFSI: Eq. ChFSIrecurrence
+ * with M^{-1} = D^{-1}; ritz may be NULL.  Vectors are processed in band
+ * blocks of `block` columns (block <= 0: all at once).  X and Y are c128 and
+ * must not overlap; ritz: host [nvec]. */
+int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
+               const double* ritz, int degree, const double bounds[3], int mode, int prec,
+               int block, double* Y, int64_t ldy);
+
+/* ---- Cholesky-QR2 + Rayleigh-Ritz (Algorithm 1, RR step) ---------------- */
+
+/* Y (c128, in/out) is made M-orthonormal by Cholesky-QR applied twice
+ * (S = Y^H M Y = L L^H, Y <- Y L^{-H}); then A = Y^H H Y is diagonalised and
+ * X_out = Y Q (c128, must not overlap Y) receives the Ritz vectors, ritz_out
+ * (host [nvec]) the Ritz values in ascending order.  Returns RCF_ENOTSPD if a
+ * Gram matrix is not positive definite.  Synchronises. */
+int rcf_rayleigh_ritz(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int nvec,
+                      double* X_out, int64_t ldx, double* ritz_out);
+
+/* ---- derivatives (no counterpart in the paper) ------------------------- */
+
+/* Accumulate (+=) the derivatives of weight * Re tr(W^H H U) with respect to
+ * V (dV, device [ncells][nloc]), B (dB, device [3][ncells][nloc]) and the
+ * couplings h (dh, host [natoms][2]; may be NULL).  W, U: c128, nvec columns. */
+int rcf_grad_bilinear(rcf_ctx* ctx, const rcf_op* op, const double* W, int64_t ldw,
+                      const double* U, int64_t ldu, int nvec, double weight,
+                      double* dV, double* dB, double* dh);
+
+/* Reverse-mode derivative of the R-ChFSI filter (X, Lambda and the bounds held
+ * constant): given Ybar = dL/dY (c128), accumulate (+=) dL/dV, dL/dB (device,
+ * per quadrature point, layouts as in rcf_potential_set) and dL/dh (host
+ * [natoms][2], may be NULL) of L = Re tr(Ybar^H Y).  The forward recurrence is
+ * recomputed from checkpoints stored every `ckpt_every` steps.  mode must be
+ * RCF_RCHFSI; prec = RCF_FP64 or RCF_FP32 (recurrences and products in that
+ * precision, gradients accumulated in FP64).  Processes all nvec columns as
+ * one block. */
+int rcf_adjoint_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
+                       const double* ritz, int degree, const double bounds[3], int mode, int prec,
+                       const double* Ybar, int64_t ldyb, int ckpt_every,
+                       double* dV, double* dB, double* dh);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RCHFSI_H */

@@ -70,7 +70,7 @@ class Hamiltonian:
 
     def __init__(self, mesh: Mesh, Vq: np.ndarray, Bq: np.ndarray | None = None,
                  atoms: np.ndarray | None = None, proj_width: np.ndarray | None = None,
-                 proj_h: np.ndarray | None = None, rcut_factor: float = 5.0):
+                 proj_h: np.ndarray | None = None, rcut_factor: float = 5.0, assemble: bool = True):
         self.mesh = mesh
         M = mesh.nnodes
         self.nnodes = M
@@ -81,14 +81,22 @@ class Hamiltonian:
         self.Vq, self.Bq = Vq, Bq
         self.mass = mesh.lumped_mass()                # M_I
         self.Mdiag = np.repeat(self.mass, 2)          # row 2I + alpha
-        # kinetic, spin-diagonal
-        K = mesh.kinetic()
-        Hk = sp.kron(K, sp.identity(2, format="csr"), format="csr").astype(np.complex128)
         # potential: per node 2x2 block sum_e w_q |J| (V I + B . sigma)
         wq = np.tile(mesh.quad_weights(), mesh.ncells)
         cidx = mesh.conn.ravel()
         pv = np.bincount(cidx, weights=wq * Vq.ravel(), minlength=M)
         pb = [np.bincount(cidx, weights=wq * Bq[d].ravel(), minlength=M) for d in range(3)]
+        self.pv, self.pb = pv, pb
+        self.projectors = []
+        if atoms is not None and len(atoms) > 0:
+            self._build_projectors(np.asarray(atoms, float), np.asarray(proj_width, float),
+                                   np.asarray(proj_h, float), rcut_factor)
+        self.Hloc = None
+        if not assemble:
+            return
+        # kinetic, spin-diagonal
+        K = mesh.kinetic()
+        Hk = sp.kron(K, sp.identity(2, format="csr"), format="csr").astype(np.complex128)
         rows, cols, vals = [], [], []
         I = np.arange(M)
         for al in range(2):
@@ -100,11 +108,6 @@ class Hamiltonian:
         Hp = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                            shape=(self.N, self.N)).tocsr()
         self.Hloc = (Hk + Hp).tocsr()
-        # nonlocal projectors
-        self.projectors = []
-        if atoms is not None and len(atoms) > 0:
-            self._build_projectors(np.asarray(atoms, float), np.asarray(proj_width, float),
-                                   np.asarray(proj_h, float), rcut_factor)
 
     def _build_projectors(self, atoms, widths, hcoup, rcut_factor):
         mesh = self.mesh
@@ -143,6 +146,33 @@ class Hamiltonian:
             C = pr["P"].T @ X[pr["rows"]]                 # P^H X (P real)
             Y[pr["rows"]] += pr["P"] @ (pr["Delta"] @ C)
         return Y
+
+    def apply_rows(self, X: np.ndarray, nodes) -> np.ndarray:
+        """Rows {2I, 2I+1 : I in nodes} of H X, each computed from the element matrices of the
+        cells that contain I (no global assembly); shape (2 len(nodes), nvec)."""
+        mesh = self.mesh
+        Ke = mesh.element_kinetic()
+        X = np.asarray(X).reshape(self.N, -1)
+        out = np.zeros((2 * len(nodes), X.shape[1]), dtype=np.complex128)
+        for r, I in enumerate(nodes):
+            cells, locs = np.nonzero(mesh.conn == I)
+            for e, l in zip(cells, locs):
+                J = mesh.conn[e]
+                for al in range(2):
+                    out[2 * r + al] += Ke[l] @ X[2 * J + al]
+            for al in range(2):
+                for be in range(2):
+                    blk = (self.pv[I] if al == be else 0.0) + sum(self.pb[d][I] * PAULI[d][al, be]
+                                                                for d in range(3))
+                    out[2 * r + al] += blk * X[2 * I + be]
+        for pr in self.projectors:
+            C = pr["Delta"] @ (pr["P"].T @ X[pr["rows"]])
+            pos = {int(I): k for k, I in enumerate(pr["support"])}
+            for r, I in enumerate(nodes):
+                k = pos.get(int(I))
+                if k is not None:
+                    out[2 * r:2 * r + 2] += pr["P"][2 * k:2 * k + 2] @ C
+        return out
 
     def dense(self) -> np.ndarray:
         """Dense H (tiny meshes only)."""

@@ -1,0 +1,733 @@
+// Host drivers: Hamiltonian-multivector products, the FP64 residual, the
+// ChFSI / R-ChFSI filters (Section III-B-2), the Lanczos bound, and the
+// checkpointed reverse-mode filter derivative.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace rcf {
+namespace {
+
+template <typename Real>
+const Real* pot_of(const rcf_op* op);
+template <>
+const double* pot_of<double>(const rcf_op* op) { return op->d_pot64; }
+template <>
+const float* pot_of<float>(const rcf_op* op) { return op->d_pot32; }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int check_block(rcf_ctx* ctx, const rcf_op* op, const void* p, int64_t ld, int nvec, size_t real,
+                const char* name) {
+  const int64_t rows = 2 * op->mesh->nnodes;
+  if (nvec < 0) return fail(ctx, RCF_EINVAL, "%s: nvec < 0", name);
+  if (nvec == 0) return RCF_OK;
+  if (!p) return fail(ctx, RCF_EINVAL, "%s is NULL", name);
+  if (ld < rows || (ld & 1)) return fail(ctx, RCF_EINVAL, "%s: ld=%lld must be even and >= 2M=%lld", name, (long long)ld, (long long)rows);
+  if (!aligned(p, 4 * real)) return fail(ctx, RCF_EINVAL, "%s: base must be %zu-byte aligned", name, 4 * real);
+  return RCF_OK;
+}
+
+bool overlaps(const void* a, int64_t lda, const void* b, int64_t ldb, int nvec, size_t cplx) {
+  if (!a || !b || nvec == 0) return false;
+  const char* a0 = static_cast<const char*>(a);
+  const char* b0 = static_cast<const char*>(b);
+  const char* a1 = a0 + size_t(lda) * nvec * cplx;
+  const char* b1 = b0 + size_t(ldb) * nvec * cplx;
+  return a0 < b1 && b0 < a1;
+}
+
+// Chebyshev scalars (Eq. ChFSIrecurrence): c, e, sigma[1..q]
+struct Cheb {
+  double c, e;
+  std::vector<double> sigma;  // index 1..q
+};
+int cheb_scalars(rcf_ctx* ctx, const double* bounds, int q, Cheb* out) {
+  if (!bounds) return fail(ctx, RCF_EINVAL, "bounds is NULL");
+  const double lmin = bounds[0], lT = bounds[1], lmax = bounds[2];
+  if (!(lmin < lT && lT < lmax) || !std::isfinite(lmin) || !std::isfinite(lmax))
+    return fail(ctx, RCF_EINVAL, "need lambda_min < lambda_T < lambda_max (got %g, %g, %g)", lmin, lT, lmax);
+  if (q < 1) return fail(ctx, RCF_EINVAL, "degree must be >= 1");
+  out->c = 0.5 * (lmax + lT);
+  out->e = 0.5 * (lmax - lT);
+  out->sigma.assign(q + 1, 0.0);
+  out->sigma[1] = out->e / (lmin - out->c);
+  for (int k = 1; k < q; ++k) out->sigma[k + 1] = 1.0 / (2.0 / out->sigma[1] - out->sigma[k]);
+  return RCF_OK;
+}
+
+// Lambda_k = C_k(Lambda) by the same three-term recurrence, FP64 (text after Eq. rChFSIrecurrence)
+void ritz_filter_values(const Cheb& ch, const double* lam, int nvec, int q, std::vector<double>* L) {
+  L->assign(size_t(q + 1) * nvec, 0.0);
+  for (int v = 0; v < nvec; ++v) {
+    (*L)[v] = 1.0;
+    if (q >= 1) (*L)[size_t(nvec) + v] = ch.sigma[1] * (lam[v] - ch.c) / ch.e;
+  }
+  for (int k = 1; k < q; ++k) {
+    const double a = 2.0 * ch.sigma[k + 1] / ch.e, b = ch.sigma[k] * ch.sigma[k + 1];
+    for (int v = 0; v < nvec; ++v)
+      (*L)[size_t(k + 1) * nvec + v] =
+          a * (lam[v] - ch.c) * (*L)[size_t(k) * nvec + v] - b * (*L)[size_t(k - 1) * nvec + v];
+  }
+}
+
+// y[v] += coef[v] x[v] over `rows` complex rows
+template <typename Real>
+__global__ void axpy_cols_kernel(int64_t rows, const Real* __restrict__ x, int64_t ldx,
+                                 const double* __restrict__ coef, Real* y, int64_t ldy) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (r >= rows) return;
+  const Real c = Real(coef[v]);
+  const Real* xs = x + 2 * (int64_t(v) * ldx + r);
+  Real* ys = y + 2 * (int64_t(v) * ldy + r);
+  ys[0] += c * xs[0];
+  ys[1] += c * xs[1];
+}
+template <typename Real>
+int launch_axpy_cols(rcf_ctx* ctx, int64_t rows, const Real* x, int64_t ldx, const double* coef,
+                     int nvec, Real* y, int64_t ldy) {
+  if (nvec <= 0) return RCF_OK;
+  axpy_cols_kernel<Real><<<dim3(unsigned((rows + 255) / 256), nvec), 256, 0, ctx->stream>>>(
+      rows, x, ldx, coef, y, ldy);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+
+// y = s x (Real), column-major blocks
+template <typename Real>
+__global__ void scale_cols_kernel(int64_t rows, const Real* __restrict__ x, int64_t ldx, Real s,
+                                  Real* y, int64_t ldy) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (r >= rows) return;
+  const Real* xs = x + 2 * (int64_t(v) * ldx + r);
+  Real* ys = y + 2 * (int64_t(v) * ldy + r);
+  ys[0] = s * xs[0];
+  ys[1] = s * xs[1];
+}
+template <typename Real>
+int launch_scale_cols(rcf_ctx* ctx, int64_t rows, const Real* x, int64_t ldx, Real s, int nvec,
+                      Real* y, int64_t ldy) {
+  if (nvec <= 0) return RCF_OK;
+  scale_cols_kernel<Real><<<dim3(unsigned((rows + 255) / 256), nvec), 256, 0, ctx->stream>>>(
+      rows, x, ldx, s, y, ldy);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+
+// Symmetric tridiagonal extreme eigenvalues by Sturm-sequence bisection.
+int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const double bb = i ? b[i - 1] * b[i - 1] : 0.0;
+    d = a[i] - x - (i ? bb / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0) ++cnt;
+  }
+  return cnt;
+}
+double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, int k) {
+  // k-th smallest eigenvalue (0-based)
+  double lo = 1e300, hi = -1e300;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const double r = (i ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < a.size() ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid == lo || mid == hi) break;
+    if (sturm_count(a, b, mid) > k) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+}  // namespace
+
+// Hamiltonian-multivector product with the nonlocal part.
+//   form H_DINV: out = A (H D^{-1}) in + ...       (R-ChFSI, Eq. rChFSIrecurrence)
+//   form DINV_H: out = A (D^{-1} H) in + ...       (ChFSI, Eq. ChFSIrecurrence)
+//   form H:      out = M (A (D^{-1} H_loc) in + B in + C prev + g rv) + A H_nloc in
+template <typename Real>
+int apply_full(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real>& a0) {
+  StepArgs<Real> a = a0;
+  a.pot = pot_of<Real>(op);
+  a.mass = op->mesh->d_mass;
+  Tables t;
+  build_tables(op->mesh, form == RCF_FORM_H_DINV ? TAB_COL_SCALED : TAB_ROW_SCALED, &t);
+  int proj_mass = 1, add_mass = 1;
+  if (form == RCF_FORM_H_DINV) { proj_mass = 0; add_mass = 1; a.scale_out = 0; }
+  else if (form == RCF_FORM_DINV_H) { proj_mass = 1; add_mass = 0; a.scale_out = 0; }
+  else { proj_mass = 1; add_mass = 1; a.scale_out = 1; }
+  const bool nl = op->proj.natoms > 0 && a.nvec > 0;
+  Real *C = nullptr, *C2 = nullptr;
+  if (nl) {
+    const size_t bytes = sizeof(Real) * 24 * size_t(op->proj.natoms) * a.nvec;
+    RCF_TRY(workspace(ctx, WS_NLC, bytes, reinterpret_cast<void**>(&C)));
+    RCF_TRY(workspace(ctx, WS_NLC2, bytes, reinterpret_cast<void**>(&C2)));
+    RCF_TRY(launch_nl_project<Real>(ctx, op, a.in, a.ld_in, a.nvec, proj_mass, C));
+    RCF_TRY(launch_nl_delta<Real>(ctx, op, C, a.nvec, a.A, C2));
+  }
+  RCF_TRY(launch_step<Real>(ctx, op->mesh, t, a));
+  if (nl) RCF_TRY(launch_nl_addback<Real>(ctx, op, C2, a.nvec, add_mass, a.out, a.ld_out));
+  return RCF_OK;
+}
+template int apply_full<float>(rcf_ctx*, const rcf_op*, int, const StepArgs<float>&);
+template int apply_full<double>(rcf_ctx*, const rcf_op*, int, const StepArgs<double>&);
+
+namespace {
+
+template <typename Real>
+StepArgs<Real> step_args(const Real* in, int64_t ldin, Real* out, int64_t ldout, int nvec, Real A,
+                         Real B) {
+  StepArgs<Real> a{};
+  a.in = in; a.ld_in = ldin;
+  a.out = out; a.ld_out = ldout;
+  a.A = A; a.B = B; a.C = Real(0);
+  a.nvec = nvec;
+  return a;
+}
+
+// FP64 residual R = H X - M X diag(lam) into R (c128); lam_d device [nvec]
+int residual_impl(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
+                  const double* neglam_d, double* R, int64_t ldr) {
+  StepArgs<double> a = step_args<double>(X, ldx, R, ldr, nvec, 1.0, 0.0);
+  a.rv = X; a.ld_rv = ldx; a.g = neglam_d;
+  return apply_full<double>(ctx, op, RCF_FORM_H, a);
+}
+
+// One R-ChFSI step (Eq. rChFSIrecurrence) for k >= 1:
+//   out = a_k H D^{-1} (zs Zk) - a_k c (zs Zk) + cp * Zkm1 + g[v] R
+template <typename Real>
+int rchfsi_step(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int k, const Real* Zk, double zs,
+                const Real* Zkm1, double cp, const Real* R, const double* g, Real* out, int64_t ld,
+                int nvec) {
+  const double ak = 2.0 * ch.sigma[k + 1] / ch.e;
+  StepArgs<Real> a = step_args<Real>(Zk, ld, out, ld, nvec, Real(ak * zs), Real(-ak * ch.c * zs));
+  if (Zkm1) { a.prev = Zkm1; a.ld_prev = ld; a.C = Real(cp); }
+  a.rv = R; a.ld_rv = ld; a.g = g;
+  return apply_full<Real>(ctx, op, RCF_FORM_H_DINV, a);
+}
+
+template <typename Real>
+int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
+                 int nvec, const double* lam_h, double* Y, int64_t ldy) {
+  const rcf_mesh* m = op->mesh;
+  const int64_t rows = 2 * m->nnodes;
+  const int64_t ld = rows;   // internal buffers: ld = 2M
+  // device coefficient table: row 0: -Lambda; rows k=1..q-1: a_k Lambda_k; row q: Lambda_q
+  std::vector<double> L;
+  ritz_filter_values(ch, lam_h, nvec, q, &L);
+  std::vector<double> tab(size_t(q + 1) * nvec);
+  for (int v = 0; v < nvec; ++v) tab[v] = -lam_h[v];
+  for (int k = 1; k < q; ++k) {
+    const double ak = 2.0 * ch.sigma[k + 1] / ch.e;
+    for (int v = 0; v < nvec; ++v) tab[size_t(k) * nvec + v] = ak * L[size_t(k) * nvec + v];
+  }
+  for (int v = 0; v < nvec; ++v) tab[size_t(q) * nvec + v] = L[size_t(q) * nvec + v];
+  double* tab_d = nullptr;
+  RCF_TRY(workspace(ctx, WS_COEF, sizeof(double) * tab.size(), reinterpret_cast<void**>(&tab_d)));
+  RCF_CUDA(ctx, cudaMemcpyAsync(tab_d, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
+
+  double* R64 = nullptr;
+  RCF_TRY(workspace(ctx, WS_R64, sizeof(double) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R64)));
+  RCF_TRY(residual_impl(ctx, op, X, ldx, nvec, tab_d, R64, ld));
+  const double s = ch.sigma[1] / ch.e;
+  const double* lamq_d = tab_d + size_t(q) * nvec;
+  if (q == 1) {
+    RCF_TRY(launch_recover<double>(ctx, m, R64, ld, s, X, ldx, lamq_d, nvec, Y, ldy));
+  } else {
+    const Real* R = nullptr;
+    if (sizeof(Real) == sizeof(double)) {
+      R = reinterpret_cast<const Real*>(R64);
+    } else {
+      float* R32 = nullptr;
+      RCF_TRY(workspace(ctx, WS_R32, sizeof(float) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R32)));
+      RCF_TRY(launch_to_c64(ctx, rows, R64, ld, nvec, R32, ld));
+      R = reinterpret_cast<const Real*>(R32);
+    }
+    Real *ZA = nullptr, *ZB = nullptr;
+    RCF_TRY(workspace(ctx, WS_ZA, sizeof(Real) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&ZA)));
+    RCF_TRY(workspace(ctx, WS_ZB, sizeof(Real) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&ZB)));
+    // k = 1: Z_2 = a_1 H D^-1 (s R) - a_1 c s R + a_1 Lambda_1 R   (Z_0 = 0)
+    RCF_TRY(rchfsi_step<Real>(ctx, op, ch, 1, R, s, nullptr, 0.0, R, tab_d + nvec, ZA, ld, nvec));
+    // Z_1 = s R is never materialised: it is R with the scale folded into the coefficients.
+    const Real* Zkm1 = R;
+    double zps = s;
+    Real* Zk = ZA;
+    for (int k = 2; k < q; ++k) {
+      const double bk = ch.sigma[k] * ch.sigma[k + 1];
+      Real* out = (Zkm1 == R) ? ZB : const_cast<Real*>(Zkm1);   // in place over Z_{k-1}
+      RCF_TRY(rchfsi_step<Real>(ctx, op, ch, k, Zk, 1.0, Zkm1, -bk * zps, R,
+                                tab_d + size_t(k) * nvec, out, ld, nvec));
+      Zkm1 = Zk;
+      zps = 1.0;
+      Zk = out;
+    }
+    RCF_TRY(launch_recover<Real>(ctx, m, Zk, ld, 1.0, X, ldx, lamq_d, nvec, Y, ldy));
+  }
+  return RCF_OK;
+}
+
+// ChFSI (Eq. ChFSIrecurrence) in FP64 on c128 blocks
+int chfsi_block64(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
+                  int nvec, double* Y, int64_t ldy) {
+  const int64_t ld = 2 * op->mesh->nnodes;
+  const double s = ch.sigma[1] / ch.e;
+  if (q == 1) {
+    StepArgs<double> a = step_args<double>(X, ldx, Y, ldy, nvec, s, -s * ch.c);
+    return apply_full<double>(ctx, op, RCF_FORM_DINV_H, a);
+  }
+  double *YA = nullptr, *YB = nullptr;
+  RCF_TRY(workspace(ctx, WS_ZA, sizeof(double) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&YA)));
+  RCF_TRY(workspace(ctx, WS_ZB, sizeof(double) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&YB)));
+  {
+    StepArgs<double> a = step_args<double>(X, ldx, YA, ld, nvec, s, -s * ch.c);
+    RCF_TRY(apply_full<double>(ctx, op, RCF_FORM_DINV_H, a));
+  }
+  const double* Yk = YA;
+  int64_t ldk = ld;
+  const double* Ykm1 = X;
+  int64_t ldkm1 = ldx;
+  for (int k = 1; k < q; ++k) {
+    const double ak = 2.0 * ch.sigma[k + 1] / ch.e, bk = ch.sigma[k] * ch.sigma[k + 1];
+    double* out;
+    int64_t ldo;
+    if (k == q - 1) { out = Y; ldo = ldy; }
+    else if (Ykm1 == X) { out = (Yk == YA) ? YB : YA; ldo = ld; }
+    else { out = const_cast<double*>(Ykm1); ldo = ld; }
+    StepArgs<double> a = step_args<double>(Yk, ldk, out, ldo, nvec, ak, -ak * ch.c);
+    a.prev = Ykm1; a.ld_prev = ldkm1; a.C = -bk;
+    RCF_TRY(apply_full<double>(ctx, op, RCF_FORM_DINV_H, a));
+    Ykm1 = Yk; ldkm1 = ldk;
+    Yk = out; ldk = ldo;
+  }
+  return RCF_OK;
+}
+
+// ChFSI in FP32 (complex64 recurrence from a rounded copy of X), result widened to c128
+int chfsi_block32(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
+                  int nvec, double* Y, int64_t ldy) {
+  const int64_t rows = 2 * op->mesh->nnodes, ld = rows;
+  float *X32 = nullptr, *YA = nullptr;
+  RCF_TRY(workspace(ctx, WS_R32, sizeof(float) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&X32)));
+  RCF_TRY(workspace(ctx, WS_ZA, sizeof(float) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&YA)));
+  RCF_TRY(launch_to_c64(ctx, rows, X, ldx, nvec, X32, ld));
+  const double s = ch.sigma[1] / ch.e;
+  {
+    StepArgs<float> a = step_args<float>(X32, ld, YA, ld, nvec, float(s), float(-s * ch.c));
+    RCF_TRY(apply_full<float>(ctx, op, RCF_FORM_DINV_H, a));
+  }
+  float* bufs[2] = {X32, YA};   // Y_{k+1} overwrites Y_{k-1} in place
+  int ikm1 = 0, ik = 1;
+  for (int k = 1; k < q; ++k) {
+    const double ak = 2.0 * ch.sigma[k + 1] / ch.e, bk = ch.sigma[k] * ch.sigma[k + 1];
+    const int io = ikm1;   // in place over Y_{k-1}
+    StepArgs<float> a = step_args<float>(bufs[ik], ld, bufs[io], ld, nvec, float(ak), float(-ak * ch.c));
+    a.prev = bufs[ikm1]; a.ld_prev = ld; a.C = float(-bk);
+    RCF_TRY(apply_full<float>(ctx, op, RCF_FORM_DINV_H, a));
+    ikm1 = ik;
+    ik = io;
+  }
+  return launch_c64_to_c128(ctx, rows, bufs[ik], ld, nvec, Y, ldy);
+}
+
+}  // namespace
+}  // namespace rcf
+
+using namespace rcf;
+
+extern "C" int rcf_apply(rcf_ctx* ctx, const rcf_op* op, int form, const void* X, int64_t ldx,
+                         int nvec, void* Y, int64_t ldy, int prec) {
+  if (!ctx || !op) return RCF_EINVAL;
+  if (form < 0 || form > 2) return fail(ctx, RCF_EINVAL, "unknown form %d", form);
+  const size_t real = prec == RCF_FP64 ? 8 : 4;
+  if (prec != RCF_FP64 && prec != RCF_FP32) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  RCF_TRY(check_block(ctx, op, X, ldx, nvec, real, "X"));
+  RCF_TRY(check_block(ctx, op, Y, ldy, nvec, real, "Y"));
+  if (overlaps(X, ldx, Y, ldy, nvec, 2 * real)) return fail(ctx, RCF_EINVAL, "Y overlaps X");
+  if (nvec == 0) return RCF_OK;
+  if (prec == RCF_FP64) {
+    StepArgs<double> a = step_args<double>(static_cast<const double*>(X), ldx, static_cast<double*>(Y), ldy, nvec, 1.0, 0.0);
+    return apply_full<double>(ctx, op, form, a);
+  }
+  StepArgs<float> a = step_args<float>(static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, nvec, 1.0f, 0.0f);
+  return apply_full<float>(ctx, op, form, a);
+}
+
+extern "C" int rcf_residual(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
+                            const double* ritz, double* R, int64_t ldr, double* colnorm) {
+  if (!ctx || !op) return RCF_EINVAL;
+  RCF_TRY(check_block(ctx, op, X, ldx, nvec, 8, "X"));
+  if (nvec == 0) return RCF_OK;
+  if (!ritz) return fail(ctx, RCF_EINVAL, "ritz is NULL");
+  const int64_t rows = 2 * op->mesh->nnodes;
+  if (R) {
+    RCF_TRY(check_block(ctx, op, R, ldr, nvec, 8, "R"));
+    if (overlaps(X, ldx, R, ldr, nvec, 16)) return fail(ctx, RCF_EINVAL, "R overlaps X");
+  } else {
+    ldr = rows;
+    RCF_TRY(workspace(ctx, WS_R64, sizeof(double) * 2 * size_t(ldr) * nvec, reinterpret_cast<void**>(&R)));
+  }
+  std::vector<double> neg(nvec);
+  for (int v = 0; v < nvec; ++v) neg[v] = -ritz[v];
+  double* neg_d = nullptr;
+  RCF_TRY(workspace(ctx, WS_COEF, sizeof(double) * nvec, reinterpret_cast<void**>(&neg_d)));
+  RCF_CUDA(ctx, cudaMemcpyAsync(neg_d, neg.data(), sizeof(double) * nvec, cudaMemcpyHostToDevice, ctx->stream));
+  RCF_TRY(residual_impl(ctx, op, X, ldx, nvec, neg_d, R, ldr));
+  if (colnorm) {
+    RCF_CUDA(ctx, cudaMemsetAsync(colnorm, 0, sizeof(double) * nvec, ctx->stream));
+    RCF_TRY(launch_colnorm2(ctx, rows, R, ldr, nvec, colnorm));
+    RCF_TRY(launch_sqrt_inplace(ctx, colnorm, nvec));
+  }
+  // neg is a host stack buffer read by an async copy
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RCF_OK;
+}
+
+extern "C" int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
+                          const double* ritz, int degree, const double bounds[3], int mode, int prec,
+                          int block, double* Y, int64_t ldy) {
+  if (!ctx || !op) return RCF_EINVAL;
+  RCF_TRY(check_block(ctx, op, X, ldx, nvec, 8, "X"));
+  RCF_TRY(check_block(ctx, op, Y, ldy, nvec, 8, "Y"));
+  if (overlaps(X, ldx, Y, ldy, nvec, 16)) return fail(ctx, RCF_EINVAL, "Y overlaps X");
+  if (mode != RCF_CHFSI && mode != RCF_RCHFSI) return fail(ctx, RCF_EINVAL, "unknown mode %d", mode);
+  if (prec != RCF_FP64 && prec != RCF_FP32) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  if (mode == RCF_RCHFSI && !ritz && nvec > 0) return fail(ctx, RCF_EINVAL, "ritz is NULL");
+  Cheb ch;
+  RCF_TRY(cheb_scalars(ctx, bounds, degree, &ch));
+  if (nvec == 0) return RCF_OK;
+  const int nb = (block <= 0 || block > nvec) ? nvec : block;
+  for (int b0 = 0; b0 < nvec; b0 += nb) {
+    const int n = std::min(nb, nvec - b0);
+    const double* Xb = X + 2 * int64_t(b0) * ldx;
+    double* Yb = Y + 2 * int64_t(b0) * ldy;
+    if (mode == RCF_RCHFSI) {
+      if (prec == RCF_FP64) RCF_TRY((rchfsi_block<double>(ctx, op, ch, degree, Xb, ldx, n, ritz + b0, Yb, ldy)));
+      else RCF_TRY((rchfsi_block<float>(ctx, op, ch, degree, Xb, ldx, n, ritz + b0, Yb, ldy)));
+    } else {
+      if (prec == RCF_FP64) RCF_TRY(chfsi_block64(ctx, op, ch, degree, Xb, ldx, n, Yb, ldy));
+      else RCF_TRY(chfsi_block32(ctx, op, ch, degree, Xb, ldx, n, Yb, ldy));
+    }
+    // the per-block coefficient table is a host vector copied asynchronously
+    RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  return RCF_OK;
+}
+
+extern "C" int rcf_lanczos_bounds(rcf_ctx* ctx, const rcf_op* op, int nsteps, const double* v0,
+                                  double* theta_min, double* upper) {
+  if (!ctx || !op) return RCF_EINVAL;
+  if (!v0 || !theta_min || !upper) return fail(ctx, RCF_EINVAL, "NULL argument");
+  if (nsteps < 1) return fail(ctx, RCF_EINVAL, "nsteps must be >= 1");
+  const rcf_mesh* m = op->mesh;
+  const int64_t n = 2 * m->nnodes;   // complex entries
+  double* buf = nullptr;
+  RCF_TRY(workspace(ctx, WS_LANCZOS, sizeof(double) * (2 * 4 * size_t(n) + 8), reinterpret_cast<void**>(&buf)));
+  double *v = buf, *vprev = buf + 2 * n, *w = buf + 4 * n, *t = buf + 6 * n, *dot = buf + 8 * n;
+  double h = 0.0;
+  RCF_CUDA(ctx, cudaMemsetAsync(dot, 0, sizeof(double), ctx->stream));
+  RCF_TRY(launch_dot_re(ctx, n, v0, v0, dot));
+  RCF_CUDA(ctx, cudaMemcpyAsync(&h, dot, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (!(h > 0.0)) return fail(ctx, RCF_EINVAL, "v0 is zero");
+  RCF_TRY(launch_scale_vec(ctx, n, v0, 1.0 / std::sqrt(h), v));
+  RCF_CUDA(ctx, cudaMemsetAsync(vprev, 0, sizeof(double) * 2 * n, ctx->stream));
+  std::vector<double> al, be;
+  double beta_prev = 0.0;
+  for (int j = 0; j < nsteps; ++j) {
+    // w = D^{-1/2} H D^{-1/2} v
+    RCF_TRY(launch_scale_mass(ctx, m, v, n, 1, -0.5, t, n));
+    StepArgs<double> a = step_args<double>(t, n, w, n, 1, 1.0, 0.0);
+    RCF_TRY(apply_full<double>(ctx, op, RCF_FORM_H, a));
+    RCF_TRY(launch_scale_mass(ctx, m, w, n, 1, -0.5, w, n));
+    double alpha = 0.0, bnew = 0.0;
+    RCF_CUDA(ctx, cudaMemsetAsync(dot, 0, sizeof(double), ctx->stream));
+    RCF_TRY(launch_dot_re(ctx, n, v, w, dot));
+    RCF_CUDA(ctx, cudaMemcpyAsync(&alpha, dot, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    RCF_TRY(launch_lanczos_update(ctx, n, w, v, vprev, alpha, beta_prev));
+    RCF_CUDA(ctx, cudaMemsetAsync(dot, 0, sizeof(double), ctx->stream));
+    RCF_TRY(launch_dot_re(ctx, n, w, w, dot));
+    RCF_CUDA(ctx, cudaMemcpyAsync(&bnew, dot, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    bnew = std::sqrt(bnew);
+    al.push_back(alpha);
+    be.push_back(bnew);
+    if (j + 1 < nsteps) {
+      if (!(bnew > 0.0)) break;   // invariant subspace found
+      RCF_CUDA(ctx, cudaMemcpyAsync(vprev, v, sizeof(double) * 2 * n, cudaMemcpyDeviceToDevice, ctx->stream));
+      RCF_TRY(launch_scale_vec(ctx, n, w, 1.0 / bnew, v));
+      beta_prev = bnew;
+    }
+  }
+  std::vector<double> off(be.begin(), be.end() - 1);
+  *theta_min = tridiag_eig(al, off, 0);
+  *upper = tridiag_eig(al, off, int(al.size()) - 1) + std::fabs(be.back());
+  return RCF_OK;
+}
+
+extern "C" int rcf_grad_bilinear(rcf_ctx* ctx, const rcf_op* op, const double* W, int64_t ldw,
+                                 const double* U, int64_t ldu, int nvec, double weight, double* dV,
+                                 double* dB, double* dh) {
+  if (!ctx || !op) return RCF_EINVAL;
+  RCF_TRY(check_block(ctx, op, W, ldw, nvec, 8, "W"));
+  RCF_TRY(check_block(ctx, op, U, ldu, nvec, 8, "U"));
+  if (!dV || !dB) return fail(ctx, RCF_EINVAL, "dV and dB must be device buffers");
+  if (nvec == 0) return RCF_OK;
+  const rcf_mesh* m = op->mesh;
+  double* g = nullptr;
+  RCF_TRY(workspace(ctx, WS_GRAD, sizeof(double) * 4 * size_t(m->nnodes) + 16 * sizeof(double) * std::max(1, op->proj.natoms), reinterpret_cast<void**>(&g)));
+  RCF_CUDA(ctx, cudaMemsetAsync(g, 0, sizeof(double) * (4 * size_t(m->nnodes) + 2 * std::max(1, op->proj.natoms)), ctx->stream));
+  RCF_TRY(launch_grad_local<double>(ctx, m, W, ldw, U, ldu, nvec, weight, 0, g));
+  RCF_TRY(launch_grad_to_quadrature(ctx, m, g, dV, dB));
+  if (dh && op->proj.natoms > 0) {
+    const int na = op->proj.natoms;
+    double* gh = g + 4 * m->nnodes;
+    double *CW = nullptr, *CU = nullptr;
+    const size_t bytes = sizeof(double) * 24 * size_t(na) * nvec;
+    RCF_TRY(workspace(ctx, WS_NLC, bytes, reinterpret_cast<void**>(&CW)));
+    RCF_TRY(workspace(ctx, WS_NLC2, bytes, reinterpret_cast<void**>(&CU)));
+    RCF_TRY(launch_nl_project<double>(ctx, op, W, ldw, nvec, 1, CW));
+    RCF_TRY(launch_nl_project<double>(ctx, op, U, ldu, nvec, 1, CU));
+    RCF_TRY(launch_grad_h<double>(ctx, op, CW, CU, nvec, weight, gh));
+    std::vector<double> tmp(2 * na);
+    RCF_CUDA(ctx, cudaMemcpyAsync(tmp.data(), gh, sizeof(double) * 2 * na, cudaMemcpyDeviceToHost, ctx->stream));
+    RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 2 * na; ++i) dh[i] += tmp[i];
+  }
+  return RCF_OK;
+}
+
+namespace rcf {
+namespace {
+
+// Reverse sweep of the R-ChFSI filter in precision Real (see rcf_adjoint_filter).
+template <typename Real>
+int adjoint_impl(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
+                 int nvec, const double* lam_h, const double* Ybar, int64_t ldyb, int kc, double* gnode,
+                 double* gh) {
+  const rcf_mesh* m = op->mesh;
+  const int64_t rows = 2 * m->nnodes, ld = rows;
+  const size_t blk = sizeof(Real) * 2 * size_t(ld) * nvec;   // one block in Real
+  const size_t blk64 = sizeof(double) * 2 * size_t(ld) * nvec;
+  // coefficient table (rows as in rchfsi_block) + a_k rows for Rbar
+  std::vector<double> L;
+  ritz_filter_values(ch, lam_h, nvec, q, &L);
+  std::vector<double> tab(size_t(q + 1) * nvec);
+  for (int v = 0; v < nvec; ++v) tab[v] = -lam_h[v];
+  for (int k = 1; k < q; ++k) {
+    const double ak = 2.0 * ch.sigma[k + 1] / ch.e;
+    for (int v = 0; v < nvec; ++v) tab[size_t(k) * nvec + v] = ak * L[size_t(k) * nvec + v];
+  }
+  for (int v = 0; v < nvec; ++v) tab[size_t(q) * nvec + v] = ch.sigma[1] / ch.e;   // s, for Rbar += s Zbar_1
+  double* tab_d = nullptr;
+  RCF_TRY(workspace(ctx, WS_COEF, sizeof(double) * tab.size(), reinterpret_cast<void**>(&tab_d)));
+  RCF_CUDA(ctx, cudaMemcpyAsync(tab_d, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
+
+  // R (FP64, then Real copy)
+  double* R64 = nullptr;
+  RCF_TRY(workspace(ctx, WS_R64, blk64, reinterpret_cast<void**>(&R64)));
+  RCF_TRY(residual_impl(ctx, op, X, ldx, nvec, tab_d, R64, ld));
+  Real* R = nullptr;
+  if (sizeof(Real) == sizeof(double)) R = reinterpret_cast<Real*>(R64);
+  else {
+    float* R32 = nullptr;
+    RCF_TRY(workspace(ctx, WS_R32, blk, reinterpret_cast<void**>(&R32)));
+    RCF_TRY(launch_to_c64(ctx, rows, R64, ld, nvec, R32, ld));
+    R = reinterpret_cast<Real*>(R32);
+  }
+  const double s = ch.sigma[1] / ch.e;
+  // checkpoints: pairs (Z_{k-1}, Z_k) at k = 1 + j kc, and a segment buffer of kc blocks
+  const int nseg = (q - 1 + kc - 1) / kc;   // segments cover k = 1 .. q-1
+  char* ck = nullptr;
+  char* seg = nullptr;
+  RCF_TRY(workspace(ctx, WS_CKPT, blk * size_t(2 * std::max(nseg, 1)), reinterpret_cast<void**>(&ck)));
+  RCF_TRY(workspace(ctx, WS_ADJ_U, blk * size_t(kc + 1), reinterpret_cast<void**>(&seg)));
+  auto ckp = [&](int j, int which) { return reinterpret_cast<Real*>(ck + blk * size_t(2 * j + which)); };
+  auto segp = [&](int i) { return reinterpret_cast<Real*>(seg + blk * size_t(i)); };
+  Real *ZA = nullptr, *ZB = nullptr;
+  RCF_TRY(workspace(ctx, WS_ZA, blk, reinterpret_cast<void**>(&ZA)));
+  RCF_TRY(workspace(ctx, WS_ZB, blk, reinterpret_cast<void**>(&ZB)));
+
+  // forward step helper: out = Z_{k+1} from (Z_k, Z_{k-1}); Z_0 = 0 (kprev null)
+  auto fwd = [&](int k, const Real* Zk, const Real* Zkm1, Real* out) {
+    const double bk = ch.sigma[k] * ch.sigma[k + 1];
+    return rchfsi_step<Real>(ctx, op, ch, k, Zk, 1.0, Zkm1, -bk, R, tab_d + size_t(k) * nvec, out, ld, nvec);
+  };
+  // forward sweep storing checkpoints. Z_1 = s R materialised.
+  {
+    Real* z1 = ckp(0, 1);
+    RCF_TRY(launch_scale_cols<Real>(ctx, rows, R, ld, Real(s), nvec, z1, ld));
+    RCF_CUDA(ctx, cudaMemsetAsync(ckp(0, 0), 0, blk, ctx->stream));
+    const Real* Zkm1 = ckp(0, 0);
+    const Real* Zk = z1;
+    for (int k = 1; k < q - 1; ++k) {   // produce Z_{k+1} for k+1 <= q-1 (Z_q is not needed)
+      // in place over Z_{k-1} when it is a scratch buffer, never over a checkpoint
+      Real* out = (Zkm1 == ZA || Zkm1 == ZB) ? const_cast<Real*>(Zkm1) : (Zk == ZA ? ZB : ZA);
+      RCF_TRY(fwd(k, Zk, k == 1 ? nullptr : Zkm1, out));
+      const int kn = k + 1;
+      if ((kn - 1) % kc == 0) {
+        const int j = (kn - 1) / kc;
+        RCF_CUDA(ctx, cudaMemcpyAsync(ckp(j, 0), Zk, blk, cudaMemcpyDeviceToDevice, ctx->stream));
+        RCF_CUDA(ctx, cudaMemcpyAsync(ckp(j, 1), out, blk, cudaMemcpyDeviceToDevice, ctx->stream));
+        Zkm1 = ckp(j, 0);
+        Zk = ckp(j, 1);
+      } else {
+        Zkm1 = Zk;
+        Zk = out;
+      }
+    }
+  }
+  // reverse sweep buffers: Zbar (3 rotating), Rbar, projections
+  Real *B0 = nullptr, *B1 = nullptr, *B2 = nullptr, *Rbar = nullptr;
+  RCF_TRY(workspace(ctx, WS_ADJ_A, blk, reinterpret_cast<void**>(&B0)));
+  RCF_TRY(workspace(ctx, WS_ADJ_B, blk, reinterpret_cast<void**>(&B1)));
+  RCF_TRY(workspace(ctx, WS_ADJ_C, blk * 2, reinterpret_cast<void**>(&B2)));
+  Rbar = reinterpret_cast<Real*>(reinterpret_cast<char*>(B2) + blk);
+  RCF_CUDA(ctx, cudaMemsetAsync(Rbar, 0, blk, ctx->stream));
+  Real *CW = nullptr, *CU = nullptr;
+  const int na = op->proj.natoms;
+  if (na > 0) {
+    const size_t bytes = sizeof(Real) * 24 * size_t(na) * nvec;
+    RCF_TRY(workspace(ctx, WS_NLC, bytes, reinterpret_cast<void**>(&CW)));
+    RCF_TRY(workspace(ctx, WS_NLC2, bytes, reinterpret_cast<void**>(&CU)));
+  }
+  // Zbar_q = D^{-1} Ybar (in Real)
+  Real* zbk1 = B0;   // Zbar_{k+1}
+  Real* zbk2 = nullptr;   // Zbar_{k+2}
+  if (sizeof(Real) == sizeof(double)) {
+    RCF_TRY(launch_scale_mass(ctx, m, Ybar, ldyb, nvec, -1.0, reinterpret_cast<double*>(zbk1), ld));
+  } else {
+    double* tmp64 = R64;   // R64 is no longer needed in FP64 once R32 exists
+    RCF_TRY(launch_scale_mass(ctx, m, Ybar, ldyb, nvec, -1.0, tmp64, ld));
+    RCF_TRY(launch_to_c64(ctx, rows, tmp64, ld, nvec, reinterpret_cast<float*>(zbk1), ld));
+  }
+  Real* freebufs[2] = {B1, B2};
+  for (int j = nseg - 1; j >= 0; --j) {
+    const int k0 = 1 + j * kc;
+    const int k1 = std::min(k0 + kc - 1, q - 1);
+    // recompute Z_{k0} .. Z_{k1} into seg[0 .. k1-k0]
+    RCF_CUDA(ctx, cudaMemcpyAsync(segp(0), ckp(j, 1), blk, cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int k = k0; k < k1; ++k) {
+      const Real* Zk = segp(k - k0);
+      const Real* Zkm1 = (k == k0) ? ckp(j, 0) : segp(k - k0 - 1);
+      RCF_TRY(fwd(k, Zk, k == 1 ? nullptr : Zkm1, segp(k - k0 + 1)));
+    }
+    for (int k = k1; k >= k0; --k) {
+      const double ak = 2.0 * ch.sigma[k + 1] / ch.e;
+      const Real* Zk = segp(k - k0);
+      // gradient: a_k Re tr(Zbar_{k+1}^H dH D^{-1} Z_k)
+      RCF_TRY(launch_grad_local<Real>(ctx, m, zbk1, ld, Zk, ld, nvec, ak, 1, gnode));
+      if (na > 0 && gh) {
+        RCF_TRY(launch_nl_project<Real>(ctx, op, zbk1, ld, nvec, 1, CW));   // P^H Zbar = beta^T M Zbar
+        RCF_TRY(launch_nl_project<Real>(ctx, op, Zk, ld, nvec, 0, CU));     // P^H D^{-1} Z = beta^T Z
+        RCF_TRY(launch_grad_h<Real>(ctx, op, CW, CU, nvec, ak, gh));
+      }
+      // Rbar += a_k Lambda_k Zbar_{k+1}
+      RCF_TRY(launch_axpy_cols<Real>(ctx, rows, zbk1, ld, tab_d + size_t(k) * nvec, nvec, Rbar, ld));
+      // Zbar_k = a_k (D^{-1} H - c) Zbar_{k+1} - b_{k+1} Zbar_{k+2}
+      Real* out = zbk2 ? zbk2 : freebufs[0];
+      StepArgs<Real> a = step_args<Real>(zbk1, ld, out, ld, nvec, Real(ak), Real(-ak * ch.c));
+      if (zbk2) { a.prev = zbk2; a.ld_prev = ld; a.C = Real(-ch.sigma[k + 1] * ch.sigma[k + 2]); }
+      RCF_TRY(apply_full<Real>(ctx, op, RCF_FORM_DINV_H, a));
+      zbk2 = zbk1;
+      zbk1 = out;
+      // the third buffer: whichever of B0, B1, B2 is neither zbk1 nor zbk2
+      Real* cand[3] = {B0, B1, B2};
+      for (Real* c : cand)
+        if (c != zbk1 && c != zbk2) { freebufs[0] = c; break; }
+    }
+  }
+  // Rbar += s Zbar_1
+  RCF_TRY(launch_axpy_cols<Real>(ctx, rows, zbk1, ld, tab_d + size_t(q) * nvec, nvec, Rbar, ld));
+  // gradient of R = H X - M X Lambda: Re tr(Rbar^H dH X), with X in Real
+  const Real* XR = nullptr;
+  if (sizeof(Real) == sizeof(double)) {
+    XR = reinterpret_cast<const Real*>(X);
+    RCF_TRY(launch_grad_local<Real>(ctx, m, Rbar, ld, XR, ldx, nvec, 1.0, 0, gnode));
+    if (na > 0 && gh) {
+      RCF_TRY(launch_nl_project<Real>(ctx, op, Rbar, ld, nvec, 1, CW));
+      RCF_TRY(launch_nl_project<Real>(ctx, op, XR, ldx, nvec, 1, CU));
+      RCF_TRY(launch_grad_h<Real>(ctx, op, CW, CU, nvec, 1.0, gh));
+    }
+  } else {
+    // widen Rbar to FP64 and use the FP64 X
+    double* Rb64 = R64;
+    RCF_TRY(launch_c64_to_c128(ctx, rows, reinterpret_cast<const float*>(Rbar), ld, nvec, Rb64, ld));
+    RCF_TRY(launch_grad_local<double>(ctx, m, Rb64, ld, X, ldx, nvec, 1.0, 0, gnode));
+    if (na > 0 && gh) {
+      double *CW64 = nullptr, *CU64 = nullptr;
+      const size_t bytes = sizeof(double) * 24 * size_t(na) * nvec;
+      RCF_TRY(workspace(ctx, WS_NLC, bytes, reinterpret_cast<void**>(&CW64)));
+      RCF_TRY(workspace(ctx, WS_NLC2, bytes, reinterpret_cast<void**>(&CU64)));
+      RCF_TRY(launch_nl_project<double>(ctx, op, Rb64, ld, nvec, 1, CW64));
+      RCF_TRY(launch_nl_project<double>(ctx, op, X, ldx, nvec, 1, CU64));
+      RCF_TRY(launch_grad_h<double>(ctx, op, CW64, CU64, nvec, 1.0, gh));
+    }
+  }
+  return RCF_OK;
+}
+
+}  // namespace
+}  // namespace rcf
+
+extern "C" int rcf_adjoint_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx,
+                                  int nvec, const double* ritz, int degree, const double bounds[3],
+                                  int mode, int prec, const double* Ybar, int64_t ldyb,
+                                  int ckpt_every, double* dV, double* dB, double* dh) {
+  if (!ctx || !op) return RCF_EINVAL;
+  RCF_TRY(check_block(ctx, op, X, ldx, nvec, 8, "X"));
+  RCF_TRY(check_block(ctx, op, Ybar, ldyb, nvec, 8, "Ybar"));
+  if (mode != RCF_RCHFSI) return fail(ctx, RCF_ENOTSUP, "the adjoint is built for mode RCF_RCHFSI");
+  if (prec != RCF_FP64 && prec != RCF_FP32) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  if (!dV || !dB) return fail(ctx, RCF_EINVAL, "dV and dB must be device buffers");
+  if (nvec > 0 && !ritz) return fail(ctx, RCF_EINVAL, "ritz is NULL");
+  if (ckpt_every < 1) return fail(ctx, RCF_EINVAL, "ckpt_every must be >= 1");
+  Cheb ch;
+  RCF_TRY(cheb_scalars(ctx, bounds, degree + 1, &ch));   // sigma up to q+1 for b_{k+1}
+  if (nvec == 0) return RCF_OK;
+  const rcf_mesh* m = op->mesh;
+  const int na = op->proj.natoms;
+  double* g = nullptr;
+  RCF_TRY(workspace(ctx, WS_GRAD, sizeof(double) * (4 * size_t(m->nnodes) + 2 * size_t(std::max(na, 1))), reinterpret_cast<void**>(&g)));
+  RCF_CUDA(ctx, cudaMemsetAsync(g, 0, sizeof(double) * (4 * size_t(m->nnodes) + 2 * size_t(std::max(na, 1))), ctx->stream));
+  double* gh = (dh && na > 0) ? g + 4 * m->nnodes : nullptr;
+  if (degree == 1) {
+    // Y = D^{-1} s R + X Lambda_1: Rbar = s D^{-1} Ybar
+    double* R64 = nullptr;
+    RCF_TRY(workspace(ctx, WS_R64, sizeof(double) * 4 * size_t(m->nnodes) * nvec, reinterpret_cast<void**>(&R64)));
+    const int64_t ld = 2 * m->nnodes;
+    RCF_TRY(launch_scale_mass(ctx, m, Ybar, ldyb, nvec, -1.0, R64, ld));
+    const double s = ch.sigma[1] / ch.e;
+    RCF_TRY(launch_grad_local<double>(ctx, m, R64, ld, X, ldx, nvec, s, 0, g));
+    if (gh) {
+      double *CW = nullptr, *CU = nullptr;
+      const size_t bytes = sizeof(double) * 24 * size_t(na) * nvec;
+      RCF_TRY(workspace(ctx, WS_NLC, bytes, reinterpret_cast<void**>(&CW)));
+      RCF_TRY(workspace(ctx, WS_NLC2, bytes, reinterpret_cast<void**>(&CU)));
+      RCF_TRY(launch_nl_project<double>(ctx, op, R64, ld, nvec, 1, CW));
+      RCF_TRY(launch_nl_project<double>(ctx, op, X, ldx, nvec, 1, CU));
+      RCF_TRY(launch_grad_h<double>(ctx, op, CW, CU, nvec, s, gh));
+    }
+  } else if (prec == RCF_FP64) {
+    RCF_TRY((adjoint_impl<double>(ctx, op, ch, degree, X, ldx, nvec, ritz, Ybar, ldyb, ckpt_every, g, gh)));
+  } else {
+    RCF_TRY((adjoint_impl<float>(ctx, op, ch, degree, X, ldx, nvec, ritz, Ybar, ldyb, ckpt_every, g, gh)));
+  }
+  RCF_TRY(launch_grad_to_quadrature(ctx, m, g, dV, dB));
+  if (gh) {
+    std::vector<double> tmp(2 * na);
+    RCF_CUDA(ctx, cudaMemcpyAsync(tmp.data(), gh, sizeof(double) * 2 * na, cudaMemcpyDeviceToHost, ctx->stream));
+    RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 2 * na; ++i) dh[i] += tmp[i];
+  }
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RCF_OK;
+}

@@ -1,0 +1,210 @@
+// Internal types of librchfsi: context, mesh, operator, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/rchfsi.h"
+
+namespace rcf {
+
+constexpr int kMaxP = 8;
+
+// ---------------------------------------------------------------------------
+// error plumbing: every failing call records a message in the context
+// ---------------------------------------------------------------------------
+struct Error {
+  int status;
+  std::string msg;
+};
+
+}  // namespace rcf
+
+struct rcf_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cublasHandle_t blas = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  std::string last_error;
+  double* d_pj = nullptr;   // spin-orbit channel projectors P_{1/2}, P_{3/2} (6x6 complex each)
+  // grow-only scratch buffers, one per slot
+  std::vector<void*> ws_ptr;
+  std::vector<size_t> ws_size;
+};
+
+struct rcf_mesh {
+  rcf_ctx* ctx = nullptr;
+  int n[3];        // cells per direction
+  double L[3];     // sides
+  double h[3];     // cell edges
+  int p, np;       // degree, nodes per direction per cell
+  int G[3];        // nodes per direction
+  int64_t nnodes, ncells;
+  int nloc;
+  std::vector<double> xi, w;  // GLL nodes and weights on [-1, 1]
+  std::vector<double> D;      // D[q*np + a] = l_a'(xi_q)
+  std::vector<double> K1;     // K1[a*np + b] = sum_q w_q D[q,a] D[q,b]
+  double detJ;
+  std::vector<double> mass;   // host M_I
+  double* d_mass = nullptr;   // device M_I
+};
+
+struct ProjAtoms {
+  int natoms = 0;
+  std::vector<int> offsets;      // [natoms + 1] entry ranges
+  std::vector<int> node;         // [nent] support nodes (sorted per atom)
+  std::vector<int> atom;         // [nent]
+  std::vector<double> beta;      // [nent][6]  column 3 j + i
+  std::vector<double> delta;     // [natoms][12][12] complex (re, im) interleaved
+  std::vector<double> hcoup;     // [natoms][2]
+  // device copies
+  int* d_offsets = nullptr;
+  int* d_node = nullptr;
+  int* d_atom = nullptr;
+  double* d_beta64 = nullptr;
+  float* d_beta32 = nullptr;
+  double* d_delta64 = nullptr;   // [natoms][144] complex
+  float* d_delta32 = nullptr;
+  int64_t nent = 0;
+};
+
+struct rcf_op {
+  rcf_ctx* ctx = nullptr;
+  const rcf_mesh* mesh = nullptr;
+  double* d_pot64 = nullptr;   // [nnodes][4] (pv, pbx, pby, pbz) / M_I
+  float* d_pot32 = nullptr;
+  ProjAtoms proj;
+};
+
+namespace rcf {
+
+// ---------------------------------------------------------------------------
+// status helpers
+// ---------------------------------------------------------------------------
+int fail(rcf_ctx* ctx, int status, const char* fmt, ...);
+int cuda_fail(rcf_ctx* ctx, cudaError_t e, const char* what, const char* file, int line);
+
+#define RCF_CUDA(ctx, expr)                                                   \
+  do {                                                                        \
+    cudaError_t _e = (expr);                                                  \
+    if (_e != cudaSuccess) return rcf::cuda_fail((ctx), _e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+#define RCF_CHECK_LAUNCH(ctx) RCF_CUDA(ctx, cudaGetLastError())
+
+#define RCF_TRY(expr)              \
+  do {                             \
+    int _s = (expr);               \
+    if (_s != RCF_OK) return _s;   \
+  } while (0)
+
+// grow-only scratch buffer `slot` of at least `bytes`
+int workspace(rcf_ctx* ctx, int slot, size_t bytes, void** out);
+enum WsSlot {
+  WS_R64 = 0, WS_R32, WS_ZA, WS_ZB, WS_COEF, WS_NLC, WS_NLC2, WS_LANCZOS, WS_RR_W, WS_RR_S,
+  WS_RR_T, WS_RR_INFO, WS_RR_WORK, WS_GRAD, WS_CKPT, WS_ADJ_A, WS_ADJ_B, WS_ADJ_C, WS_ADJ_U,
+  WS_NORM, WS_COUNT
+};
+
+// ---------------------------------------------------------------------------
+// stencil step (stencil.cu)
+//
+//   out = A * (D^{-1} H_loc or H_loc D^{-1}) in + B * in + C * prev + g[v] * rv
+//   then optionally out *= M_I
+// where H_loc = kinetic + spinor potential (Eq. hloc, Eq. cellHam).
+// ---------------------------------------------------------------------------
+template <typename Real>
+struct StepArgs {
+  const Real* in;    int64_t ld_in;     // complex elements per vector (even)
+  const Real* prev;  int64_t ld_prev;   // may be null
+  const Real* rv;    int64_t ld_rv;     // may be null
+  const double* g;                      // [nvec] coefficients of rv (device), may be null
+  Real* out;         int64_t ld_out;
+  Real A, B, C;
+  const Real* pot;                      // [nnodes][4]
+  const double* mass;                   // used if scale_out
+  int scale_out;
+  int nvec;
+};
+
+// coefficient tables for the three 1D operators: coef[d][a][a']
+struct Tables {
+  double c[3][kMaxP + 1][kMaxP + 1];
+};
+enum TableKind { TAB_ROW_SCALED = 0 /* D^{-1} H */, TAB_COL_SCALED = 1 /* H D^{-1} */ };
+void build_tables(const rcf_mesh* m, int kind, Tables* t);
+
+template <typename Real>
+int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a);
+
+// ---------------------------------------------------------------------------
+// nonlocal projectors (nonlocal.cu)
+// ---------------------------------------------------------------------------
+// C[a][f][v] = sum_e w_e beta_e[j,i] in[v][node_e][sigma],  f = 6 j + 2 i + sigma,
+// w_e = M_node if proj_mass else 1.   C is complex (Real2) [natoms][12][nvec].
+template <typename Real>
+int launch_nl_project(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ld, int nvec,
+                      int proj_mass, Real* C);
+// C2 = A * Delta_a C
+template <typename Real>
+int launch_nl_delta(rcf_ctx* ctx, const rcf_op* op, const Real* C, int nvec, Real A, Real* C2);
+// out[v][node_e][sigma] += w_e sum_{j,i} beta_e[j,i] C2[a][6j+2i+sigma][v], w_e = M if add_mass
+template <typename Real>
+int launch_nl_addback(rcf_ctx* ctx, const rcf_op* op, const Real* C2, int nvec, int add_mass,
+                      Real* out, int64_t ld);
+
+// ---------------------------------------------------------------------------
+// vector kernels (vectors.cu)
+// ---------------------------------------------------------------------------
+// y[v][r] = s(r) * x[v][r], s = M_I^pow (pow in {-1, -0.5, 0.5, 1}) or 1 (pow = 0)
+int launch_scale_mass(rcf_ctx* ctx, const rcf_mesh* m, const double* x, int64_t ldx, int nvec,
+                      double pw, double* y, int64_t ldy);
+// Y = dinv * Z * zs + X * lam[v]     (recovery, Algorithm 1)
+template <typename ZReal>
+int launch_recover(rcf_ctx* ctx, const rcf_mesh* m, const ZReal* Z, int64_t ldz, double zs,
+                   const double* X, int64_t ldx, const double* lam, int nvec, double* Y,
+                   int64_t ldy);
+// y = (float) x, and optional column norms^2 accumulated into nrm2 (device, pre-zeroed)
+int launch_to_c64(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, int nvec, float* y,
+                  int64_t ldy);
+int launch_colnorm2(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, int nvec,
+                    double* nrm2);
+int launch_sqrt_inplace(rcf_ctx* ctx, double* v, int n);
+int launch_copy_c128(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, int nvec,
+                     double* y, int64_t ldy);
+int launch_c64_to_c128(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec,
+                       double* y, int64_t ldy);
+// Lanczos helpers on single vectors of length n complex
+int launch_dot_re(rcf_ctx* ctx, int64_t n, const double* a, const double* b, double* out);
+int launch_lanczos_update(rcf_ctx* ctx, int64_t n, double* w, const double* v,
+                          const double* vprev, double alpha, double beta);
+int launch_scale_vec(rcf_ctx* ctx, int64_t n, const double* x, double s, double* y);
+
+// ---------------------------------------------------------------------------
+// gradients (nonlocal.cu / vectors.cu)
+// ---------------------------------------------------------------------------
+// gnode[0][I] += wgt Re sum_v W^H U ; gnode[1+d][I] += wgt Re sum_v W^H sigma_d U
+// (U scaled by 1/M_I first if u_dinv)
+template <typename Real>
+int launch_grad_local(rcf_ctx* ctx, const rcf_mesh* m, const Real* W, int64_t ldw, const Real* U,
+                      int64_t ldu, int nvec, double wgt, int u_dinv, double* gnode);
+// gh[a][j] += wgt Re sum_v CW^H P_j CU  (CW, CU from launch_nl_project with mass weights)
+template <typename Real>
+int launch_grad_h(rcf_ctx* ctx, const rcf_op* op, const Real* CW, const Real* CU, int nvec,
+                  double wgt, double* gh);
+void channel_projector_table(double* h /* [2][6][6] complex */);
+// dV[e][l] += |J| w_l gnode[0][I(e,l)], dB[d][e][l] += |J| w_l gnode[1+d][I(e,l)]
+int launch_grad_to_quadrature(rcf_ctx* ctx, const rcf_mesh* m, const double* gnode, double* dV,
+                              double* dB);
+
+// the Hamiltonian-multivector product with the nonlocal part (filter.cu)
+template <typename Real>
+int apply_full(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real>& a);
+
+}  // namespace rcf

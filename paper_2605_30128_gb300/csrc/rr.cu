@@ -1,0 +1,176 @@
+// Cholesky-QR2 and the Rayleigh-Ritz step in FP64 (Algorithm 1, RR step; Section III-C-4).
+//
+// The Gram matrix S = Y^H M Y is accumulated over row chunks as a Hermitian
+// rank-k update of W = M^{1/2} Y (ZHERK), factorised S = L L^H (ZPOTRF) and
+// applied as Y <- Y L^{-H} (ZTRSM); twice.  A non-positive pivot triggers one
+// shifted pass (shifted Cholesky-QR) before giving up with RCF_ENOTSPD.  The
+// projected matrix A = Y^H H Y is formed from column chunks of H Y (the
+// library's own matrix-free product) with ZGEMM, diagonalised by ZHEEVD, and
+// the rotation X = Y Q is one ZGEMM.  These are plain dense library
+// routines; the problem-specific work (H Y, the M weighting) runs in this
+// library's kernels.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace rcf {
+namespace {
+
+__global__ void sqrt_mass_rows_kernel(const double* __restrict__ mass, const double* __restrict__ Y,
+                                      int64_t ldy, int64_t r0, int64_t cr, double* __restrict__ W) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (r >= cr) return;
+  const double s = sqrt(mass[(r0 + r) >> 1]);
+  const double2 y = reinterpret_cast<const double2*>(Y + 2 * int64_t(v) * ldy)[r0 + r];
+  reinterpret_cast<double2*>(W + 2 * int64_t(v) * cr)[r] = make_double2(s * y.x, s * y.y);
+}
+
+const char* cublas_name(cublasStatus_t s) {
+  switch (s) {
+    case CUBLAS_STATUS_SUCCESS: return "success";
+    case CUBLAS_STATUS_NOT_INITIALIZED: return "not initialized";
+    case CUBLAS_STATUS_ALLOC_FAILED: return "alloc failed";
+    case CUBLAS_STATUS_INVALID_VALUE: return "invalid value";
+    case CUBLAS_STATUS_EXECUTION_FAILED: return "execution failed";
+    default: return "error";
+  }
+}
+
+#define RCF_BLAS(ctx, expr)                                                                  \
+  do {                                                                                       \
+    cublasStatus_t _s = (expr);                                                              \
+    if (_s != CUBLAS_STATUS_SUCCESS)                                                         \
+      return fail((ctx), RCF_ECUDA, "cuBLAS %s failed: %s", #expr, cublas_name(_s));         \
+  } while (0)
+#define RCF_SOLVER(ctx, expr)                                                                \
+  do {                                                                                       \
+    cusolverStatus_t _s = (expr);                                                            \
+    if (_s != CUSOLVER_STATUS_SUCCESS)                                                       \
+      return fail((ctx), RCF_ECUDA, "cuSOLVER %s failed: status %d", #expr, int(_s));        \
+  } while (0)
+
+// S = Y^H M Y  (lower triangle), S: n x n
+int gram(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int n, cuDoubleComplex* S) {
+  const int64_t N = 2 * op->mesh->nnodes;
+  int64_t cr = std::max<int64_t>(1024, (int64_t(1) << 26) / std::max(n, 1));   // ~1 GiB chunks
+  cr = std::min<int64_t>(cr, N);
+  double* W = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_W, sizeof(double) * 2 * size_t(cr) * n, reinterpret_cast<void**>(&W)));
+  const double one = 1.0, zero = 0.0;
+  for (int64_t r0 = 0; r0 < N; r0 += cr) {
+    const int64_t c = std::min(cr, N - r0);
+    sqrt_mass_rows_kernel<<<dim3(unsigned((c + 255) / 256), n), 256, 0, ctx->stream>>>(
+        op->mesh->d_mass, Y, ldy, r0, c, W);
+    RCF_CHECK_LAUNCH(ctx);
+    RCF_BLAS(ctx, cublasZherk(ctx->blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, n, int(c), &one,
+                              reinterpret_cast<const cuDoubleComplex*>(W), int(c),
+                              r0 == 0 ? &zero : &one, S, n));
+  }
+  return RCF_OK;
+}
+
+// one Cholesky-QR pass; returns RCF_ENOTSPD (without touching Y) on breakdown unless shifted
+int cholqr_pass(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int n, bool shift) {
+  const int64_t N = 2 * op->mesh->nnodes;
+  cuDoubleComplex* S = nullptr;
+  int* info = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_S, sizeof(cuDoubleComplex) * size_t(n) * n, reinterpret_cast<void**>(&S)));
+  RCF_TRY(workspace(ctx, WS_RR_INFO, sizeof(int) * 4, reinterpret_cast<void**>(&info)));
+  RCF_TRY(gram(ctx, op, Y, ldy, n, S));
+  if (shift) {
+    // shifted Cholesky-QR: S += 11 (N n + n (n + 1)) u tr(S) I   (tr(S) >= ||S||_2 for SPD S)
+    std::vector<cuDoubleComplex> h(size_t(n) * n);
+    RCF_CUDA(ctx, cudaMemcpyAsync(h.data(), S, sizeof(cuDoubleComplex) * h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i) tr += h[size_t(i) * n + i].x;
+    const double sh = 11.0 * (double(N) * n + double(n) * (n + 1)) * 1.1102230246251565e-16 * tr;
+    for (int i = 0; i < n; ++i) h[size_t(i) * n + i].x += sh;
+    RCF_CUDA(ctx, cudaMemcpyAsync(S, h.data(), sizeof(cuDoubleComplex) * h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  int lwork = 0;
+  RCF_SOLVER(ctx, cusolverDnZpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_LOWER, n, S, n, &lwork));
+  cuDoubleComplex* work = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_WORK, sizeof(cuDoubleComplex) * size_t(std::max(lwork, 1)), reinterpret_cast<void**>(&work)));
+  RCF_SOLVER(ctx, cusolverDnZpotrf(ctx->solver, CUBLAS_FILL_MODE_LOWER, n, S, n, work, lwork, info));
+  int hinfo = 0;
+  RCF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (hinfo != 0)
+    return fail(ctx, RCF_ENOTSPD, "Cholesky-QR: Gram matrix not positive definite (pivot %d)", hinfo);
+  const cuDoubleComplex onec = make_cuDoubleComplex(1.0, 0.0);
+  RCF_BLAS(ctx, cublasZtrsm(ctx->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C,
+                            CUBLAS_DIAG_NON_UNIT, int(N), n, &onec, S, n,
+                            reinterpret_cast<cuDoubleComplex*>(Y), int(ldy)));
+  return RCF_OK;
+}
+
+}  // namespace
+}  // namespace rcf
+
+using namespace rcf;
+
+extern "C" int rcf_rayleigh_ritz(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int nvec,
+                                 double* X_out, int64_t ldx, double* ritz_out) {
+  if (!ctx || !op) return RCF_EINVAL;
+  const int64_t N = 2 * op->mesh->nnodes;
+  if (nvec <= 0) return fail(ctx, RCF_EINVAL, "nvec must be >= 1");
+  if (!Y || !X_out || !ritz_out) return fail(ctx, RCF_EINVAL, "NULL argument");
+  if (ldy < N || ldx < N || (ldy & 1) || (ldx & 1)) return fail(ctx, RCF_EINVAL, "bad leading dimension");
+  if (ldy > INT32_MAX || ldx > INT32_MAX || N > INT32_MAX)
+    return fail(ctx, RCF_ENOTSUP, "leading dimensions above 2^31 are not supported by the BLAS path");
+  {
+    const char* y0 = reinterpret_cast<const char*>(Y);
+    const char* x0 = reinterpret_cast<const char*>(X_out);
+    if (y0 < x0 + size_t(ldx) * nvec * 16 && x0 < y0 + size_t(ldy) * nvec * 16)
+      return fail(ctx, RCF_EINVAL, "X_out overlaps Y");
+  }
+  // Cholesky-QR2, with one shifted pass in front if the first factorisation breaks down
+  int s = cholqr_pass(ctx, op, Y, ldy, nvec, false);
+  if (s == RCF_ENOTSPD) {
+    RCF_TRY(cholqr_pass(ctx, op, Y, ldy, nvec, true));
+    RCF_TRY(cholqr_pass(ctx, op, Y, ldy, nvec, false));
+  } else if (s != RCF_OK) {
+    return s;
+  }
+  RCF_TRY(cholqr_pass(ctx, op, Y, ldy, nvec, false));
+  // A = Y^H H Y, column chunks of H Y
+  cuDoubleComplex* A = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_S, sizeof(cuDoubleComplex) * size_t(nvec) * nvec, reinterpret_cast<void**>(&A)));
+  const int cb = std::min(nvec, 256);
+  double* T = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_T, sizeof(double) * 2 * size_t(N) * cb, reinterpret_cast<void**>(&T)));
+  const cuDoubleComplex onec = make_cuDoubleComplex(1.0, 0.0), zeroc = make_cuDoubleComplex(0.0, 0.0);
+  for (int c0 = 0; c0 < nvec; c0 += cb) {
+    const int nc = std::min(cb, nvec - c0);
+    RCF_TRY(rcf_apply(ctx, op, RCF_FORM_H, Y + 2 * int64_t(c0) * ldy, ldy, nc, T, N, RCF_FP64));
+    RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_C, CUBLAS_OP_N, nvec, nc, int(N), &onec,
+                              reinterpret_cast<const cuDoubleComplex*>(Y), int(ldy),
+                              reinterpret_cast<const cuDoubleComplex*>(T), int(N), &zeroc,
+                              A + size_t(c0) * nvec, nvec));
+  }
+  double* w = nullptr;
+  int* info = nullptr;
+  RCF_TRY(workspace(ctx, WS_NORM, sizeof(double) * nvec, reinterpret_cast<void**>(&w)));
+  RCF_TRY(workspace(ctx, WS_RR_INFO, sizeof(int) * 4, reinterpret_cast<void**>(&info)));
+  int lwork = 0;
+  RCF_SOLVER(ctx, cusolverDnZheevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                              nvec, A, nvec, w, &lwork));
+  cuDoubleComplex* work = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_WORK, sizeof(cuDoubleComplex) * size_t(std::max(lwork, 1)), reinterpret_cast<void**>(&work)));
+  RCF_SOLVER(ctx, cusolverDnZheevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nvec, A,
+                                   nvec, w, work, lwork, info));
+  RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, int(N), nvec, nvec, &onec,
+                            reinterpret_cast<const cuDoubleComplex*>(Y), int(ldy), A, nvec, &zeroc,
+                            reinterpret_cast<cuDoubleComplex*>(X_out), int(ldx)));
+  int hinfo = 0;
+  RCF_CUDA(ctx, cudaMemcpyAsync(ritz_out, w, sizeof(double) * nvec, cudaMemcpyDeviceToHost, ctx->stream));
+  RCF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (hinfo != 0) return fail(ctx, RCF_ECUDA, "ZHEEVD did not converge (info %d)", hinfo);
+  return RCF_OK;
+}

@@ -1,0 +1,338 @@
+// Matrix-free local Hamiltonian step on the periodic GLL spectral-element mesh.
+//
+// On a uniform mesh with GLL quadrature collocated at the nodes, the
+// assembled kinetic matrix of the cell-level form (Eq. cellHam, stages i-iii
+// of Section III-B-3) factors into three 1D banded operators:
+//   K = 1/2 (K1g (x) Wg (x) Wg + Wg (x) K1g (x) Wg + Wg (x) Wg (x) K1g),
+//   M = Wg (x) Wg (x) Wg,
+// so (D^{-1} K u)_{ijk} = sum_d (A_d u)_{along d} with 1D matrices A_d that
+// couple only the nodes of one 1D element (two for element vertices).  The
+// same holds for K D^{-1}.  This is the same matrix as the cell-assembled one;
+// the kernel evaluates it node by node ("owner computes"), so no cell buffer,
+// no scatter and no atomics are needed.
+//
+// Data layout: column-major multivectors; vector v is a 3D field of nodes
+// I = x + Gx (y + Gy z), each node a 4-tuple (re_up, im_up, re_dn, im_dn).
+// A block owns a TX x TY tile of (x, y) columns of one vector and marches
+// through all z planes.  Each plane (tile plus the x/y halo of one element
+// width) is staged in shared memory by cp.async through an NST-deep ring; the
+// z direction is handled in registers (each thread keeps its z-line of the
+// current element).  Every input element is read from L2/HBM once per plane
+// visit; outputs are written once.
+#include "internal.h"
+
+namespace rcf {
+namespace {
+
+template <typename Real>
+struct alignas(4 * sizeof(Real)) R4 {
+  Real v[4];
+};
+
+template <typename Real>
+__device__ __forceinline__ R4<Real> zero4() {
+  R4<Real> r;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.v[i] = Real(0);
+  return r;
+}
+
+template <typename Real>
+__device__ __forceinline__ void fma4(R4<Real>& acc, Real c, const R4<Real>& x) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc.v[i] = fma(c, x.v[i], acc.v[i]);
+}
+
+__device__ __forceinline__ R4<float> ldg4(const R4<float>* p) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  R4<float> r;
+  r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  return r;
+}
+__device__ __forceinline__ R4<double> ldg4(const R4<double>* p) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  R4<double> r;
+  r.v[0] = a.x; r.v[1] = a.y; r.v[2] = b.x; r.v[3] = b.y;
+  return r;
+}
+// plain (coherent) load for buffers that the same kernel may write (prev aliases out)
+template <typename Real>
+__device__ __forceinline__ R4<Real> ld4(const R4<Real>* p) {
+  return *p;
+}
+template <typename Real>
+__device__ __forceinline__ void st4(R4<Real>* p, const R4<Real>& x) {
+  *p = x;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename Real>
+__device__ __forceinline__ void cp_async_r4(R4<Real>* dst, const R4<Real>* src) {
+#pragma unroll
+  for (int i = 0; i < int(sizeof(R4<Real>) / 16); ++i)
+    cp_async16(reinterpret_cast<char*>(dst) + 16 * i, reinterpret_cast<const char*>(src) + 16 * i);
+}
+
+// 2x2 spinor potential (Eq. hloc): [[pv + bz, bx - i by], [bx + i by, pv - bz]] u
+template <typename Real>
+__device__ __forceinline__ void add_potential(R4<Real>& acc, const R4<Real>& pot, const R4<Real>& u) {
+  const Real pv = pot.v[0], bx = pot.v[1], by = pot.v[2], bz = pot.v[3];
+  const Real ur = u.v[0], ui = u.v[1], dr = u.v[2], di = u.v[3];
+  // up row
+  acc.v[0] += (pv + bz) * ur + bx * dr + by * di;
+  acc.v[1] += (pv + bz) * ui + bx * di - by * dr;
+  // down row
+  acc.v[2] += bx * ur - by * ui + (pv - bz) * dr;
+  acc.v[3] += bx * ui + by * ur + (pv - bz) * di;
+}
+
+template <typename Real, int P>
+struct KTab {
+  Real c[3][P + 1][P + 1];
+};
+
+template <typename Real, int P, int TX, int TY, int NST>
+__global__ void __launch_bounds__(TX* TY)
+    step_kernel(const StepArgs<Real> a, const KTab<Real, P> tab, const int Gx, const int Gy,
+                const int Gz) {
+  constexpr int W = TX + P + 1;   // staged columns: x0 - P .. x0 + TX
+  constexpr int H = TY + P + 1;   // staged rows:    y0 - P .. y0 + TY
+  constexpr int NT = TX * TY;
+  using V4 = R4<Real>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  V4* S = reinterpret_cast<V4*>(smem_raw);                         // [NST][H][W]
+  Real* ST = reinterpret_cast<Real*>(S + NST * H * W);            // [3][P+1][P+1]
+
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 3 * (P + 1) * (P + 1); i += NT) ST[i] = (&tab.c[0][0][0])[i];
+
+  const int lx = tid % TX, ly = tid / TX;
+  const int ntx = (Gx + TX - 1) / TX;
+  const int x0 = (blockIdx.x % ntx) * TX;
+  const int y0 = (blockIdx.x / ntx) * TY;
+  const int v = blockIdx.y;
+  const int gx = x0 + lx, gy = y0 + ly;
+  const bool active = (gx < Gx) && (gy < Gy);
+  const int nz = Gz / P;
+  const int64_t plane = int64_t(Gx) * Gy;
+
+  const V4* in = reinterpret_cast<const V4*>(a.in + 2 * int64_t(v) * a.ld_in);
+
+  auto issue_plane = [&](int z, int s) {
+    V4* dst = S + s * H * W;
+    const V4* src = in + int64_t(z) * plane;
+    for (int e = tid; e < H * W; e += NT) {
+      const int r = e / W, c = e - r * W;
+      const bool need = (r >= P && r < P + TY) || (c >= P && c < P + TX);
+      if (!need) continue;
+      int xx = (x0 - P + c) % Gx;
+      if (xx < 0) xx += Gx;
+      int yy = (y0 - P + r) % Gy;
+      if (yy < 0) yy += Gy;
+      cp_async_r4(dst + e, src + xx + int64_t(Gx) * yy);
+    }
+    cp_async_commit();
+  };
+
+  // prologue: start the plane ring
+#pragma unroll
+  for (int s = 0; s < NST - 1; ++s) {
+    if (s < Gz) issue_plane(s, s);
+    else cp_async_commit();
+  }
+  int zload = NST - 1;
+
+  __syncthreads();  // coefficient table visible
+  const int ax = lx % P, by = ly % P;
+  Real cx[P + 1], cy[P + 1];
+#pragma unroll
+  for (int q = 0; q <= P; ++q) {
+    cx[q] = ST[(0 * (P + 1) + ax) * (P + 1) + q];
+    cy[q] = ST[(1 * (P + 1) + by) * (P + 1) + q];
+  }
+
+  // own z-line of element -1 (planes Gz-P .. Gz-1), for the vertex carry
+  V4 zprev[P];
+  const int64_t col = int64_t(gx) + int64_t(Gx) * gy;
+#pragma unroll
+  for (int c = 0; c < P; ++c)
+    zprev[c] = active ? ldg4(in + col + int64_t(Gz - P + c) * plane) : zero4<Real>();
+
+  // wait for plane z, refill the ring, return own value and the x + y terms
+  auto consume = [&](int z, V4& own, V4& xy) {
+    cp_async_wait<NST - 2>();
+    __syncthreads();
+    if (zload < Gz) issue_plane(zload, zload % NST);
+    else cp_async_commit();
+    ++zload;
+    const V4* Pl = S + (z % NST) * H * W;
+    own = Pl[(ly + P) * W + lx + P];
+    V4 t = zero4<Real>();
+    // x: right element (a' = 0..P) and, for a vertex, the left element
+    const V4* row = Pl + (ly + P) * W;
+    const int cb = lx - ax + P;
+#pragma unroll
+    for (int q = 0; q <= P; ++q) fma4(t, cx[q], row[cb + q]);
+    if (ax == 0) {
+#pragma unroll
+      for (int q = 0; q <= P; ++q) fma4(t, ST[(0 * (P + 1) + P) * (P + 1) + q], row[cb - P + q]);
+    }
+    // y
+    const int rb = ly - by + P;
+#pragma unroll
+    for (int q = 0; q <= P; ++q) fma4(t, cy[q], Pl[(rb + q) * W + lx + P]);
+    if (by == 0) {
+#pragma unroll
+      for (int q = 0; q <= P; ++q) fma4(t, ST[(1 * (P + 1) + P) * (P + 1) + q], Pl[(rb - P + q) * W + lx + P]);
+    }
+    xy = t;
+  };
+
+  const Real* Tz = ST + 2 * (P + 1) * (P + 1);
+  V4 zl[P + 1], acc[P];
+  V4 accn = zero4<Real>();
+  consume(0, zl[0], acc[0]);
+  const V4 zfirst = zl[0];
+  V4 carry = zero4<Real>();
+#pragma unroll
+  for (int c = 0; c < P; ++c) fma4(carry, Tz[P * (P + 1) + c], zprev[c]);
+  fma4(carry, Tz[P * (P + 1) + P], zl[0]);
+
+  const V4* prev = a.prev ? reinterpret_cast<const V4*>(a.prev + 2 * int64_t(v) * a.ld_prev) : nullptr;
+  const V4* rv = a.rv ? reinterpret_cast<const V4*>(a.rv + 2 * int64_t(v) * a.ld_rv) : nullptr;
+  V4* out = reinterpret_cast<V4*>(a.out + 2 * int64_t(v) * a.ld_out);
+  const V4* pot = reinterpret_cast<const V4*>(a.pot);
+  const Real gv = a.g ? Real(a.g[v]) : Real(0);
+
+  for (int ez = 0; ez < nz; ++ez) {
+#pragma unroll
+    for (int c = 1; c <= P; ++c) {
+      if (c < P) {
+        consume(ez * P + c, zl[c], acc[c]);
+      } else if (ez < nz - 1) {
+        consume(ez * P + c, zl[P], accn);
+      } else {
+        zl[P] = zfirst;
+      }
+    }
+    // z term of this element
+#pragma unroll
+    for (int cc = 0; cc < P; ++cc) {
+#pragma unroll
+      for (int q = 0; q <= P; ++q) fma4(acc[cc], Tz[cc * (P + 1) + q], zl[q]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[0].v[i] += carry.v[i];
+    carry = zero4<Real>();
+#pragma unroll
+    for (int q = 0; q <= P; ++q) fma4(carry, Tz[P * (P + 1) + q], zl[q]);
+
+    if (active) {
+#pragma unroll
+      for (int cc = 0; cc < P; ++cc) {
+        const int64_t I = col + int64_t(ez * P + cc) * plane;
+        V4 hu = acc[cc];
+        add_potential(hu, ldg4(pot + I), zl[cc]);
+        V4 res;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) res.v[i] = a.A * hu.v[i] + a.B * zl[cc].v[i];
+        if (prev) {
+          const V4 pv = ld4(prev + I);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) res.v[i] = fma(a.C, pv.v[i], res.v[i]);
+        }
+        if (rv) {
+          const V4 r = ldg4(rv + I);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) res.v[i] = fma(gv, r.v[i], res.v[i]);
+        }
+        if (a.scale_out) {
+          const Real mI = Real(a.mass[I]);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) res.v[i] *= mI;
+        }
+        st4(out + I, res);
+      }
+    }
+    zl[0] = zl[P];
+    acc[0] = accn;
+  }
+  cp_async_wait<0>();
+}
+
+template <typename Real, int P>
+struct TileOf {
+  // tile edge in nodes (a multiple of P): about 16 for FP32, 8 for FP64
+  static constexpr int base = sizeof(Real) == 4 ? 16 : 8;
+  static constexpr int T = P * ((base + P - 1) / P);
+};
+
+template <typename Real, int P>
+int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a) {
+  constexpr int T = TileOf<Real, P>::T;
+  constexpr int NST = 4;
+  KTab<Real, P> kt;
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i <= P; ++i)
+      for (int j = 0; j <= P; ++j) kt.c[d][i][j] = Real(t.c[d][i][j]);
+  const int ntx = (m->G[0] + T - 1) / T, nty = (m->G[1] + T - 1) / T;
+  const size_t smem = size_t(NST) * (T + P + 1) * (T + P + 1) * sizeof(R4<Real>) +
+                      3 * (P + 1) * (P + 1) * sizeof(Real);
+  auto kern = step_kernel<Real, P, T, T, NST>;
+  if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  dim3 grid(ntx * nty, a.nvec);
+  kern<<<grid, T * T, smem, ctx->stream>>>(a, kt, m->G[0], m->G[1], m->G[2]);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+
+}  // namespace
+
+void build_tables(const rcf_mesh* m, int kind, Tables* t) {
+  // C_d[a][a'] = 1/2 (2/h_d) K1[a][a'] / Wg(a'') with a'' = a' (column scaled,
+  // H D^{-1}) or a'' = a (row scaled, D^{-1} H); Wg = (h/2) w at interior
+  // nodes and h w_0 at vertices (two elements meet there).
+  const int P = m->p, np = m->np;
+  for (int d = 0; d < 3; ++d) {
+    const double h = m->h[d];
+    for (int i = 0; i <= kMaxP; ++i)
+      for (int j = 0; j <= kMaxP; ++j) t->c[d][i][j] = 0.0;
+    auto wg = [&](int a) { return (a == 0 || a == P) ? h * m->w[0] : 0.5 * h * m->w[a]; };
+    for (int i = 0; i < np; ++i)
+      for (int j = 0; j < np; ++j) {
+        const double k = 0.5 * (2.0 / h) * m->K1[i * np + j];
+        t->c[d][i][j] = k / (kind == TAB_COL_SCALED ? wg(j) : wg(i));
+      }
+  }
+}
+
+template <typename Real>
+int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a) {
+  if (a.nvec <= 0) return RCF_OK;
+  switch (m->p) {
+    case 1: return launch_p<Real, 1>(ctx, m, t, a);
+    case 2: return launch_p<Real, 2>(ctx, m, t, a);
+    case 3: return launch_p<Real, 3>(ctx, m, t, a);
+    case 4: return launch_p<Real, 4>(ctx, m, t, a);
+    case 5: return launch_p<Real, 5>(ctx, m, t, a);
+    case 6: return launch_p<Real, 6>(ctx, m, t, a);
+    case 7: return launch_p<Real, 7>(ctx, m, t, a);
+    case 8: return launch_p<Real, 8>(ctx, m, t, a);
+    default: return fail(ctx, RCF_ENOTSUP, "degree p=%d not built (1..8)", m->p);
+  }
+}
+
+template int launch_step<float>(rcf_ctx*, const rcf_mesh*, const Tables&, const StepArgs<float>&);
+template int launch_step<double>(rcf_ctx*, const rcf_mesh*, const Tables&, const StepArgs<double>&);
+
+}  // namespace rcf

@@ -1,0 +1,294 @@
+"""Thin ctypes binding of librchfsi (include/rchfsi.h), same names as the C ABI.
+
+Only argument marshalling happens here: every step of the computation runs in
+the library's CUDA kernels.  Device multivectors are torch tensors of shape
+(nvec, 2M) (row j = vector j, so the memory is the column-major layout of
+the C ABI), dtype complex128 (or complex64 where the C call accepts FP32).
+If the library is missing, loading raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librchfsi.so")
+
+RCF_OK, RCF_EINVAL, RCF_ENOMEM, RCF_ECUDA, RCF_ENOTSPD, RCF_ETIMEOUT, RCF_ENOTSUP = range(7)
+RCF_FP64, RCF_FP32 = 0, 1
+RCF_CHFSI, RCF_RCHFSI = 0, 1
+RCF_FORM_H, RCF_FORM_DINV_H, RCF_FORM_H_DINV = 0, 1, 2
+
+EXPORTS = [
+    "rcf_create", "rcf_destroy", "rcf_status_string", "rcf_last_error", "rcf_sync",
+    "rcf_mesh_create", "rcf_mesh_destroy", "rcf_mesh_info", "rcf_mesh_connectivity",
+    "rcf_mesh_quadrature_points", "rcf_mesh_mass", "rcf_op_create", "rcf_op_destroy",
+    "rcf_potential_set", "rcf_projectors_set", "rcf_projectors_couplings", "rcf_projector_support",
+    "rcf_apply", "rcf_lanczos_bounds", "rcf_residual", "rcf_filter", "rcf_rayleigh_ritz",
+    "rcf_grad_bilinear", "rcf_adjoint_filter",
+]
+
+_lib = None
+
+
+class RcfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"rcf status {status}: {msg}")
+        self.status = status
+
+
+def lib() -> ctypes.CDLL:
+    """Load librchfsi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2605_30128_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    pvp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "rcf_create": (i32, [pvp, i32, vp]),
+        "rcf_destroy": (i32, [vp]),
+        "rcf_status_string": (ctypes.c_char_p, [i32]),
+        "rcf_last_error": (ctypes.c_char_p, [vp]),
+        "rcf_sync": (i32, [vp]),
+        "rcf_mesh_create": (i32, [vp, vp, vp, i32, pvp]),
+        "rcf_mesh_destroy": (i32, [vp]),
+        "rcf_mesh_info": (i32, [vp, vp, vp, vp]),
+        "rcf_mesh_connectivity": (i32, [vp, vp]),
+        "rcf_mesh_quadrature_points": (i32, [vp, vp]),
+        "rcf_mesh_mass": (i32, [vp, vp]),
+        "rcf_op_create": (i32, [vp, vp, pvp]),
+        "rcf_op_destroy": (i32, [vp]),
+        "rcf_potential_set": (i32, [vp, vp, vp, i32]),
+        "rcf_projectors_set": (i32, [vp, i32, vp, vp, vp, dbl]),
+        "rcf_projectors_couplings": (i32, [vp, vp]),
+        "rcf_projector_support": (i32, [vp, i32, vp, vp]),
+        "rcf_apply": (i32, [vp, vp, i32, vp, i64, i32, vp, i64, i32]),
+        "rcf_lanczos_bounds": (i32, [vp, vp, i32, vp, vp, vp]),
+        "rcf_residual": (i32, [vp, vp, vp, i64, i32, vp, vp, i64, vp]),
+        "rcf_filter": (i32, [vp, vp, vp, i64, i32, vp, i32, vp, i32, i32, i32, vp, i64]),
+        "rcf_rayleigh_ritz": (i32, [vp, vp, vp, i64, i32, vp, i64, vp]),
+        "rcf_grad_bilinear": (i32, [vp, vp, vp, i64, vp, i64, i32, dbl, vp, vp, vp]),
+        "rcf_adjoint_filter": (i32, [vp, vp, vp, i64, i32, vp, i32, vp, i32, i32, vp, i64, i32, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(ctx, status: int):
+    if status != RCF_OK:
+        L = lib()
+        msg = L.rcf_last_error(ctx).decode() if ctx else L.rcf_status_string(status).decode()
+        raise RcfError(status, msg or L.rcf_status_string(status).decode())
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev(t, dtype=None, name="tensor"):
+    """(pointer, ld) of a device multivector tensor of shape (nvec, rows)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.dim() == 1:
+        return ctypes.c_void_p(t.data_ptr()), t.shape[0]
+    if t.stride(-1) != 1:
+        raise ValueError(f"{name} rows must be contiguous")
+    return ctypes.c_void_p(t.data_ptr()), t.stride(0)
+
+
+# ---- context / mesh / operator ---------------------------------------------------
+
+def rcf_create(device: int = 0, stream=None):
+    """Context on `device`, enqueueing on `stream` (a torch.cuda.Stream, an int handle or None
+    for torch's current stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device).cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = ctypes.c_void_p()
+    _check(None, lib().rcf_create(ctypes.byref(h), device, ctypes.c_void_p(stream)))
+    return h
+
+
+def rcf_destroy(ctx):
+    lib().rcf_destroy(ctx)
+
+
+def rcf_sync(ctx):
+    _check(ctx, lib().rcf_sync(ctx))
+
+
+def rcf_status_string(status: int) -> str:
+    return lib().rcf_status_string(status).decode()
+
+
+def rcf_last_error(ctx) -> str:
+    return lib().rcf_last_error(ctx).decode()
+
+
+def rcf_mesh_create(ctx, ncell, side, p: int):
+    n = np.ascontiguousarray(np.broadcast_to(np.asarray(ncell, dtype=np.int32), (3,)))
+    s = np.ascontiguousarray(np.broadcast_to(np.asarray(side, dtype=np.float64), (3,)))
+    h = ctypes.c_void_p()
+    _check(ctx, lib().rcf_mesh_create(ctx, _np_ptr(n), _np_ptr(s), int(p), ctypes.byref(h)))
+    return h
+
+
+def rcf_mesh_destroy(mesh):
+    lib().rcf_mesh_destroy(mesh)
+
+
+def rcf_mesh_info(mesh):
+    nn, nc, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+    _check(None, lib().rcf_mesh_info(mesh, ctypes.byref(nn), ctypes.byref(nc), ctypes.byref(nl)))
+    return nn.value, nc.value, nl.value
+
+
+def rcf_mesh_connectivity(mesh) -> np.ndarray:
+    nn, nc, nl = rcf_mesh_info(mesh)
+    out = np.empty((nc, nl), dtype=np.int32)
+    _check(None, lib().rcf_mesh_connectivity(mesh, _np_ptr(out)))
+    return out
+
+
+def rcf_mesh_quadrature_points(mesh) -> np.ndarray:
+    nn, nc, nl = rcf_mesh_info(mesh)
+    out = np.empty((nc, nl, 3), dtype=np.float64)
+    _check(None, lib().rcf_mesh_quadrature_points(mesh, _np_ptr(out)))
+    return out
+
+
+def rcf_mesh_mass(mesh) -> np.ndarray:
+    nn, nc, nl = rcf_mesh_info(mesh)
+    out = np.empty(nn, dtype=np.float64)
+    _check(None, lib().rcf_mesh_mass(mesh, _np_ptr(out)))
+    return out
+
+
+def rcf_op_create(ctx, mesh):
+    h = ctypes.c_void_p()
+    _check(ctx, lib().rcf_op_create(ctx, mesh, ctypes.byref(h)))
+    return h
+
+
+def rcf_op_destroy(op):
+    lib().rcf_op_destroy(op)
+
+
+def rcf_potential_set(ctx, op, V, B=None):
+    """V: [ncells][nloc], B: [3][ncells][nloc] FP64, numpy (host) or CUDA tensors (device)."""
+    import torch
+    if isinstance(V, torch.Tensor):
+        if V.dtype != torch.float64 or not V.is_cuda or not V.is_contiguous():
+            raise TypeError("V must be a contiguous float64 CUDA tensor")
+        if B is not None and (B.dtype != torch.float64 or not B.is_cuda or not B.is_contiguous()):
+            raise TypeError("B must be a contiguous float64 CUDA tensor")
+        _check(ctx, lib().rcf_potential_set(op, ctypes.c_void_p(V.data_ptr()),
+                                            ctypes.c_void_p(B.data_ptr()) if B is not None else None, 1))
+        return
+    Vh = np.ascontiguousarray(V, dtype=np.float64)
+    Bh = None if B is None else np.ascontiguousarray(B, dtype=np.float64)
+    _check(ctx, lib().rcf_potential_set(op, _np_ptr(Vh), _np_ptr(Bh) if Bh is not None else None, 0))
+
+
+def rcf_projectors_set(ctx, op, pos, width, h, rcut_factor: float = 5.0):
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    width = np.ascontiguousarray(width, dtype=np.float64).reshape(-1, 2)
+    h = np.ascontiguousarray(h, dtype=np.float64).reshape(-1, 2)
+    _check(ctx, lib().rcf_projectors_set(op, pos.shape[0], _np_ptr(pos), _np_ptr(width), _np_ptr(h),
+                                         float(rcut_factor)))
+
+
+def rcf_projectors_couplings(ctx, op, h):
+    h = np.ascontiguousarray(h, dtype=np.float64).reshape(-1, 2)
+    _check(ctx, lib().rcf_projectors_couplings(op, _np_ptr(h)))
+
+
+def rcf_projector_support(op, atom: int) -> np.ndarray:
+    n = ctypes.c_int64()
+    _check(None, lib().rcf_projector_support(op, atom, ctypes.byref(n), None))
+    out = np.empty(n.value, dtype=np.int32)
+    _check(None, lib().rcf_projector_support(op, atom, ctypes.byref(n), _np_ptr(out)))
+    return out
+
+
+# ---- compute -----------------------------------------------------------------------
+
+def rcf_apply(ctx, op, form: int, X, Y, prec: int = RCF_FP64):
+    import torch
+    dt = torch.complex128 if prec == RCF_FP64 else torch.complex64
+    px, ldx = _dev(X, dt, "X")
+    py, ldy = _dev(Y, dt, "Y")
+    nvec = X.shape[0] if X.dim() == 2 else 1
+    _check(ctx, lib().rcf_apply(ctx, op, form, px, ldx, nvec, py, ldy, prec))
+
+
+def rcf_lanczos_bounds(ctx, op, nsteps: int, v0):
+    import torch
+    pv, _ = _dev(v0, torch.complex128, "v0")
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().rcf_lanczos_bounds(ctx, op, int(nsteps), pv, ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def rcf_residual(ctx, op, X, ritz, R=None, colnorm=None):
+    import torch
+    px, ldx = _dev(X, torch.complex128, "X")
+    rz = np.ascontiguousarray(ritz, dtype=np.float64)
+    pr, ldr = (None, 0) if R is None else _dev(R, torch.complex128, "R")
+    pc = None if colnorm is None else ctypes.c_void_p(colnorm.data_ptr())
+    _check(ctx, lib().rcf_residual(ctx, op, px, ldx, X.shape[0], _np_ptr(rz), pr, ldr, pc))
+
+
+def rcf_filter(ctx, op, X, ritz, degree: int, bounds, mode: int, prec: int, block: int, Y):
+    import torch
+    px, ldx = _dev(X, torch.complex128, "X")
+    py, ldy = _dev(Y, torch.complex128, "Y")
+    rz = None if ritz is None else np.ascontiguousarray(ritz, dtype=np.float64)
+    b = np.ascontiguousarray(bounds, dtype=np.float64)
+    _check(ctx, lib().rcf_filter(ctx, op, px, ldx, X.shape[0], _np_ptr(rz) if rz is not None else None,
+                                 int(degree), _np_ptr(b), int(mode), int(prec), int(block), py, ldy))
+
+
+def rcf_rayleigh_ritz(ctx, op, Y, X_out):
+    import torch
+    py, ldy = _dev(Y, torch.complex128, "Y")
+    px, ldx = _dev(X_out, torch.complex128, "X_out")
+    ritz = np.empty(Y.shape[0], dtype=np.float64)
+    _check(ctx, lib().rcf_rayleigh_ritz(ctx, op, py, ldy, Y.shape[0], px, ldx, _np_ptr(ritz)))
+    return ritz
+
+
+def rcf_grad_bilinear(ctx, op, W, U, weight: float, dV, dB, dh=None):
+    import torch
+    pw, ldw = _dev(W, torch.complex128, "W")
+    pu, ldu = _dev(U, torch.complex128, "U")
+    _check(ctx, lib().rcf_grad_bilinear(ctx, op, pw, ldw, pu, ldu, W.shape[0], float(weight),
+                                        ctypes.c_void_p(dV.data_ptr()), ctypes.c_void_p(dB.data_ptr()),
+                                        _np_ptr(dh) if dh is not None else None))
+
+
+def rcf_adjoint_filter(ctx, op, X, ritz, degree: int, bounds, mode: int, prec: int, Ybar,
+                       ckpt_every: int, dV, dB, dh=None):
+    import torch
+    px, ldx = _dev(X, torch.complex128, "X")
+    pyb, ldyb = _dev(Ybar, torch.complex128, "Ybar")
+    rz = np.ascontiguousarray(ritz, dtype=np.float64)
+    b = np.ascontiguousarray(bounds, dtype=np.float64)
+    _check(ctx, lib().rcf_adjoint_filter(ctx, op, px, ldx, X.shape[0], _np_ptr(rz), int(degree), _np_ptr(b),
+                                         int(mode), int(prec), pyb, ldyb, int(ckpt_every),
+                                         ctypes.c_void_p(dV.data_ptr()), ctypes.c_void_p(dB.data_ptr()),
+                                         _np_ptr(dh) if dh is not None else None))

@@ -1,0 +1,111 @@
+"""GPU path (librchfsi through the C ABI) against the FP64 CPU oracle, element by element.
+
+Meshes span several stencil tiles with a ragged tail in x and y (FP32 tiles
+are about 16 nodes, FP64 tiles about 8), single-cell directions, and degrees
+p = 1 .. 6.  Tolerances: FP64 products 1e-12 relative (rounding of ~30-term
+sums); FP64 filters 1e-10 relative Frobenius (the target for filtered
+blocks); FP32 products 2e-6 relative (float rounding of the same sums,
+about 30 eps_32 in the worst row).
+"""
+import numpy as np
+import pytest
+
+import workloads
+from gpu_cases import Pair, rel, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+MESHES = [
+    ((7, 3, 2), (7.0, 4.5, 3.0), 3),    # Gx = 21: two FP32 tiles, three FP64 tiles, ragged
+    ((4, 4, 4), 8.0, 4),                 # the 4^3 p=4 workload mesh
+    ((5, 3, 2), (10.0, 6.0, 4.0), 5),    # p = 5, Gx = 25 > 20
+    ((4, 3, 2), (8.0, 6.0, 4.0), 6),     # p = 6, Gx = 24 > 18
+    ((1, 2, 3), (2.0, 4.0, 6.0), 2),     # one cell along x: a node is its own periodic image
+    ((9, 2, 1), (9.0, 2.0, 1.0), 1),     # p = 1
+]
+
+
+@pytest.fixture(scope="module", params=MESHES, ids=lambda m: f"n{m[0]}-p{m[2]}")
+def pair(request):
+    n, L, p = request.param
+    pr = Pair(n, L, p, natoms=2)
+    yield pr
+    pr.close()
+
+
+def test_connectivity_and_mass_bit_exact(pair):
+    from paper_2605_30128_gb300 import rchfsi as R
+    conn = R.rcf_mesh_connectivity(pair.g.mesh)
+    assert np.array_equal(conn.astype(np.int64), pair.H.mesh.conn)
+    mass = R.rcf_mesh_mass(pair.g.mesh)
+    np.testing.assert_allclose(mass, pair.H.mass, rtol=1e-14)
+    q = R.rcf_mesh_quadrature_points(pair.g.mesh)
+    np.testing.assert_allclose(q, pair.H.mesh.quad_coords(), atol=1e-13)
+    for a, pj in enumerate(pair.H.projectors):
+        sup = R.rcf_projector_support(pair.g.op, a)
+        assert np.array_equal(sup.astype(np.int64), pj["support"])
+
+
+@pytest.mark.parametrize("form", [0, 1, 2], ids=["H", "DinvH", "HDinv"])
+def test_apply_fp64(pair, form):
+    from paper_2605_30128_gb300 import rchfsi as R
+    H = pair.H
+    X = workloads.complex_normal(3, (H.N, 5))
+    if form == 0:
+        ref = H.apply(X)
+    elif form == 1:
+        ref = H.apply(X) / H.Mdiag[:, None]
+    else:
+        ref = H.apply(X / H.Mdiag[:, None])
+    Xd = to_dev(X)
+    Yd = Xd.new_zeros(Xd.shape)
+    R.rcf_apply(pair.g.ctx, pair.g.op, form, Xd, Yd, R.RCF_FP64)
+    Y = to_host(Yd)
+    assert rel(Y, ref) < 1e-12
+    assert np.max(np.abs(Y - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("form", [1, 2], ids=["DinvH", "HDinv"])
+def test_apply_fp32(pair, form):
+    import torch
+    from paper_2605_30128_gb300 import rchfsi as R
+    H = pair.H
+    X = workloads.complex_normal(4, (H.N, 3))
+    X32 = X.astype(np.complex64).astype(np.complex128)
+    ref = H.apply(X32) / H.Mdiag[:, None] if form == 1 else H.apply(X32 / H.Mdiag[:, None])
+    Xd = to_dev(X, torch.complex64)
+    Yd = Xd.new_zeros(Xd.shape)
+    R.rcf_apply(pair.g.ctx, pair.g.op, form, Xd, Yd, R.RCF_FP32)
+    Y = to_host(Yd)
+    assert rel(Y, ref) < 2e-6
+
+
+def test_apply_strided_leading_dimension(pair):
+    """ld > 2M: vectors inside a wider buffer."""
+    from paper_2605_30128_gb300 import rchfsi as R
+    H = pair.H
+    X = workloads.complex_normal(5, (H.N, 3))
+    ref = H.apply(X)
+    t = to_dev(X)
+    import torch
+    big = torch.zeros((3, H.N + 6), dtype=torch.complex128, device="cuda")
+    big[:, :H.N] = t
+    out = torch.full((3, H.N + 10), 7.0, dtype=torch.complex128, device="cuda")
+    R.rcf_apply(pair.g.ctx, pair.g.op, 0, big[:, :H.N], out[:, :H.N], R.RCF_FP64)
+    assert rel(to_host(out[:, :H.N]), ref) < 1e-12
+    assert torch.all(out[:, H.N:] == 7.0)   # nothing written past the rows
+
+
+def test_residual(pair):
+    import torch
+    from paper_2605_30128_gb300 import rchfsi as R
+    H = pair.H
+    X = workloads.complex_normal(6, (H.N, 4))
+    lam = np.array([-0.3, 0.1, 0.5, 2.0])
+    ref = H.apply(X) - H.Mdiag[:, None] * X * lam[None, :]
+    Xd = to_dev(X)
+    Rd = torch.zeros_like(Xd)
+    cn = torch.zeros(4, dtype=torch.float64, device="cuda")
+    R.rcf_residual(pair.g.ctx, pair.g.op, Xd, lam, Rd, cn)
+    assert rel(to_host(Rd), ref) < 1e-12
+    np.testing.assert_allclose(cn.cpu().numpy(), np.linalg.norm(ref, axis=0), rtol=1e-12)
