@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Throughput of the mixed-precision R-ChFSI filter on one GB300, in filtered DoF*vec*deg/s.
+
+Workload (default): periodic 20^3 cells, p = 5 (100^3 nodes, 2,000,000 complex
+spinor DoF), 32 atoms with spin-orbit projectors, 1024 spinor vectors filtered
+in band blocks of 256 at degree 40.  The recurrence runs in complex64 (FP32
+stencil products); X, the residual and the recovery are complex128.  A step is
+one rcf_filter call over all 1024 vectors: X -> Y_q including the FP64
+residual and the recovery.  Units per step = 2M * nvec * degree.
+
+Also reported on the same JSON line: the dominant kernel (the FP32 recurrence
+step) against the measured HBM copy bandwidth, the FP64 ChFSI filter on the
+same mesh and block, an end-to-end figure through the C ABI with host
+buffers, the CPU oracle on a bounded sample, sampled SM clocks, and the
+number of this library's kernel launches in the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank filters its own band of 1024
+vectors (band partitioning with one GPU per column group: the filter needs no
+communication), so per-GPU work is fixed ("weak" scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "filtered DoF·vec·deg/s: mixed-prec R-ChFSI vs FP64 ChFSI at ≤1e-7 Ha eig err"
+UNIT = "DoF·vec·deg/s"
+BYTES_PER_UNIT = 32.0   # read Z_k, Z_{k-1}, R (complex64) + write Z_{k+1}
+KERNEL_SRC = os.path.join(ROOT, "paper_2605_30128_gb300", "csrc", "stencil.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg3")
+    ap.add_argument("--nvec", type=int, default=None, help="override (profiling runs only)")
+    ap.add_argument("--block", type=int, default=None)
+    ap.add_argument("--degree", type=int, default=None)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64, e2e and CPU legs (profiling runs only)")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "gloo" if args.impl == "reference" else "nccl"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_of(args):
+    import workloads
+    over = {}
+    if args.nvec:
+        over["nvec"] = args.nvec
+    if args.block:
+        over["block"] = args.block
+    if args.degree:
+        over["degree"] = args.degree
+    return workloads.workload(args.workload, **over)
+
+
+def describe(w) -> str:
+    return (f"{w.name}: periodic {w.ncell}^3 cells, p={w.p}, side {w.side:g} bohr, "
+            f"{w.ndof:,} complex spinor DoF, {w.natoms} spin-orbit atoms, {w.nvec} vectors "
+            f"in blocks of {w.block}, degree {w.degree}")
+
+
+# ----------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the reference arm and the cpu_baseline leg)
+# ----------------------------------------------------------------------------------------
+
+def oracle_setup(w):
+    import numpy as np
+    import workloads
+    from oracle import Hamiltonian, Mesh
+    prm = workloads.draw_parameters(w)
+    m = Mesh(w.ncell, w.side, w.p)
+    q = m.quad_coords().reshape(-1, 3)
+    V = workloads.gaussian_sum_potential(q, prm["centres"], prm["depths"], prm["widths"], prm["L"])
+    B = workloads.smooth_periodic_field(q, prm["kvec"], prm["amps"], prm["phases"], prm["L"], prm["bmax"])
+    H = Hamiltonian(m, V.reshape(m.ncells, m.nloc), B.reshape(3, m.ncells, m.nloc), prm["atoms"],
+                    prm["proj_width"], prm["proj_h"])
+    return H
+
+
+def oracle_sample(H, nv: int, q: int, seed: int):
+    """Time the oracle's R-ChFSI filter (FP64, scipy sparse) on nv vectors at degree q."""
+    import numpy as np
+    import workloads
+    from oracle import rchfsi_filter
+    X = workloads.complex_normal(seed, (H.N, nv))
+    lam = np.linspace(-1.0, 0.5, nv)
+    t0 = time.perf_counter()
+    rchfsi_filter(H, X, lam, -1.5, 1.0, 60.0, q)
+    dt = time.perf_counter() - t0
+    return H.N * nv * q / dt, dt
+
+
+ORACLE_NV, ORACLE_Q = 16, 6
+
+
+def run_reference(args):
+    ws, rank, local = dist_init(args)
+    if rank != 0:
+        return 0
+    w = workload_of(args)
+    H = oracle_setup(w)
+    for i in range(args.warmup):
+        oracle_sample(H, ORACLE_NV, ORACLE_Q, 500 + i)
+    times, vals = [], []
+    for i in range(args.steps):
+        v, dt = oracle_sample(H, ORACLE_NV, ORACLE_Q, 600 + i)
+        vals.append(v)
+        times.append(dt)
+    value = statistics.median(vals)
+    sample = (f"oracle R-ChFSI filter (NumPy/SciPy FP64, CSR sparse H) on the full {w.ncell}^3 p={w.p} mesh, "
+              f"{ORACLE_NV} vectors, degree {ORACLE_Q} per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": describe(w)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host_cores": os.cpu_count()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            rows = []
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------------------
+
+def traffic_record():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None when
+    the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+        return rec if rec.get("kernel_sha256") == h else None
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2605_30128_gb300 import build as pbuild
+    from paper_2605_30128_gb300 import rchfsi as R
+    from paper_2605_30128_gb300.problem import GPUProblem
+
+    ws, rank, local = dist_init(args)
+    torch.cuda.set_device(local)
+    if rank == 0:
+        pbuild.build()
+    barrier(ws)
+    w = workload_of(args)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    prob = GPUProblem(w, device=local, stream=stream)
+    ctx, op = prob.ctx, prob.op
+    N, nvec, q = prob.N, w.nvec, w.degree
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w.seed + 100 + rank)
+    X = torch.randn((nvec, N), dtype=torch.complex128, device=dev, generator=gen)
+    Y = torch.empty_like(X)
+    # filter bounds from a seeded Lanczos run; Ritz values spread below lambda_T
+    v0 = torch.randn((N,), dtype=torch.complex128, device=dev, generator=gen)
+    lo, hi = R.rcf_lanczos_bounds(ctx, op, w.lanczos, v0)
+    lT = lo + 0.05 * (hi - lo)
+    ritz = np.linspace(lo, lT, nvec, endpoint=False)
+    bounds = (lo - 1e-3 * abs(lo), lT, hi)
+
+    def step():
+        R.rcf_filter(ctx, op, X, ritz, q, bounds, R.RCF_RCHFSI, R.RCF_FP32, w.block, Y)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    l0 = R.rcf_launch_count(ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(ws)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    launches = (R.rcf_launch_count(ctx) - l0)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ws, ms)
+    units = float(N) * nvec * q
+    value = units * ws / (ms * 1e-3)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": describe(w),
+                   "precision": "recurrence and stencil products complex64 (FP32); X, residual, recovery complex128",
+                   "l2": "inputs larger than L2 (X and Y are %.1f GB each)" % (X.numel() * 16 / 1e9),
+                   "parallelism": "band partitioning, one GPU per column group (no filter communication)"
+                                  if ws > 1 else "single GPU"},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+
+    # ---- dominant kernel: one FP32 recurrence step on a block, timed alone ----
+    blk = min(w.block, nvec)
+    op1 = R.rcf_op_create(ctx, prob.mesh)       # same mesh and potential, no projectors: one launch
+    R.rcf_potential_set(ctx, op1, prob.V, prob.B)
+    Zk = torch.randn((blk, N), dtype=torch.complex64, device=dev, generator=gen)
+    Zm = torch.randn((blk, N), dtype=torch.complex64, device=dev, generator=gen)
+    Rr = torch.randn((blk, N), dtype=torch.complex64, device=dev, generator=gen)
+    g = torch.full((blk,), 0.25, dtype=torch.float64, device=dev)
+    nrep = 10
+    for _ in range(3):
+        R.rcf_cheb_step(ctx, op1, R.RCF_FORM_H_DINV, R.RCF_FP32, Zk, Zm, Rr, 0.1, -0.5, -1.0, g, Zm)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(nrep):
+        R.rcf_cheb_step(ctx, op1, R.RCF_FORM_H_DINV, R.RCF_FP32, Zk, Zm, Rr, 0.1, -0.5, -1.0, g, Zm)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    k_ms = ev0.elapsed_time(ev1) / nrep
+    # the same step with the projectors (four launches)
+    ev0.record(stream)
+    for _ in range(nrep):
+        R.rcf_cheb_step(ctx, op, R.RCF_FORM_H_DINV, R.RCF_FP32, Zk, Zm, Rr, 0.1, -0.5, -1.0, g, Zm)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    step_ms = ev0.elapsed_time(ev1) / nrep
+    R.rcf_op_destroy(op1)
+    del Zk, Zm, Rr
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = BYTES_PER_UNIT * N * blk / (k_ms * 1e-3) / 1e9
+    tr = traffic_record()
+    line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": (tr["bytes_per_launch_full_block"] if tr else None),
+                        "kernel": "step_kernel<float,5> (FP32 R-ChFSI recurrence step, %d vectors)" % blk,
+                        "kernel_ms": k_ms, "algorithmic_bytes": BYTES_PER_UNIT * N * blk,
+                        "peak_source": "measured" if peaks else "fallback",
+                        "step_with_projectors_ms": step_ms}
+
+    if not args.no_extras:
+        # ---- FP64 ChFSI on one block, same mesh and degree ----
+        Xb = X[:blk]
+        Yb = Y[:blk]
+        R.rcf_filter(ctx, op, Xb, ritz[:blk], q, bounds, R.RCF_CHFSI, R.RCF_FP64, blk, Yb)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        R.rcf_filter(ctx, op, Xb, ritz[:blk], q, bounds, R.RCF_CHFSI, R.RCF_FP64, blk, Yb)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        f64_ms = ev0.elapsed_time(ev1)
+        f64_val = float(N) * blk * q / (f64_ms * 1e-3)
+        # the mixed filter on the same single block, for a like-for-like ratio
+        ev0.record(stream)
+        R.rcf_filter(ctx, op, Xb, ritz[:blk], q, bounds, R.RCF_RCHFSI, R.RCF_FP32, blk, Yb)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        mix_ms = ev0.elapsed_time(ev1)
+        line["fp64_chfsi"] = {"value": f64_val * ws, "unit": UNIT, "ms_one_block": f64_ms,
+                              "mixed_rchfsi_ms_one_block": mix_ms, "speedup_mixed_over_fp64": f64_ms / mix_ms,
+                              "sample": f"one block of {blk} vectors, degree {q}"}
+
+        # ---- end to end through the C ABI with host buffers ----
+        try:
+            Xh = torch.empty((nvec, N), dtype=torch.complex128, pin_memory=True)
+            Yh = torch.empty((nvec, N), dtype=torch.complex128, pin_memory=True)
+            Xh.copy_(X)
+            sample = "full workload"
+        except Exception:
+            Xh = torch.empty((blk, N), dtype=torch.complex128, pin_memory=True)
+            Yh = torch.empty((blk, N), dtype=torch.complex128, pin_memory=True)
+            Xh.copy_(X[:blk])
+            sample = f"first block of {blk} vectors (pinned host memory for the full block set unavailable)"
+        ne = Xh.shape[0]
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(max(1, args.steps)):
+            X[:ne].copy_(Xh, non_blocking=True)
+            R.rcf_filter(ctx, op, X[:ne], ritz[:ne], q, bounds, R.RCF_RCHFSI, R.RCF_FP32, w.block, Y[:ne])
+            Yh.copy_(Y[:ne], non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = ev0.elapsed_time(ev1) / max(1, args.steps)
+        e_ms = max_over_ranks(ws, e_ms)
+        line["e2e"] = {"value": float(N) * ne * q * ws / (e_ms * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": int(Xh.numel() * 16), "d2h_bytes_per_step": int(Yh.numel() * 16),
+                       "ms_per_step": e_ms, "sample": sample}
+        del Xh, Yh
+
+        # ---- CPU oracle on a bounded sample (rank 0, one GPU only) ----
+        if ws == 1 and rank == 0:
+            H = oracle_setup(w)
+            v, dt = oracle_sample(H, ORACLE_NV, ORACLE_Q, 700)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"oracle R-ChFSI filter (NumPy/SciPy FP64, single-threaded CSR "
+                                              f"products) on the full mesh, {ORACLE_NV} vectors, degree "
+                                              f"{ORACLE_Q}: {dt:.1f} s",
+                                    "host_cores": os.cpu_count()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    prob.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -121,6 +121,20 @@ int rcf_projector_support(const rcf_op* op, int atom, int64_t* count, int32_t* h
 int rcf_apply(rcf_ctx* ctx, const rcf_op* op, int form, const void* X, int64_t ldx, int nvec,
               void* Y, int64_t ldy, int prec);
 
+/* One step of the three-term recurrence (Eq. ChFSIrecurrence with form
+ * RCF_FORM_DINV_H, Eq. rChFSIrecurrence with form RCF_FORM_H_DINV):
+ *   out = alpha op(Zk) + beta Zk + gamma Zkm1 + g[v] R_v     (v = column)
+ * Zk, Zkm1, R, out share the leading dimension ld; Zkm1, R and g (device
+ * double [nvec]) may be NULL.  out may alias Zkm1 (updated in place) but not
+ * Zk or R.  prec as in rcf_apply. */
+int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec, const void* Zk,
+                  const void* Zkm1, const void* R, int64_t ld, int nvec, double alpha, double beta,
+                  double gamma, const double* g, void* out);
+
+/* Number of kernels this context has launched so far (its own kernels; the
+ * dense library routines of Rayleigh-Ritz are not counted). */
+int64_t rcf_launch_count(const rcf_ctx* ctx);
+
 /* ---- filter bounds (Section III-B-2; Lanczos as in Section III-C-1) --- */
 
 /* nsteps of Lanczos on D^{-1/2} H D^{-1/2} from the device c128 vector v0

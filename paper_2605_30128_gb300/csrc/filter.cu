@@ -360,6 +360,37 @@ extern "C" int rcf_apply(rcf_ctx* ctx, const rcf_op* op, int form, const void* X
   return apply_full<float>(ctx, op, form, a);
 }
 
+extern "C" int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec, const void* Zk,
+                             const void* Zkm1, const void* R, int64_t ld, int nvec, double alpha,
+                             double beta, double gamma, const double* g, void* out) {
+  if (!ctx || !op) return RCF_EINVAL;
+  if (form < 0 || form > 2) return fail(ctx, RCF_EINVAL, "unknown form %d", form);
+  if (prec != RCF_FP64 && prec != RCF_FP32) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  const size_t real = prec == RCF_FP64 ? 8 : 4;
+  RCF_TRY(check_block(ctx, op, Zk, ld, nvec, real, "Zk"));
+  RCF_TRY(check_block(ctx, op, out, ld, nvec, real, "out"));
+  if (Zkm1) RCF_TRY(check_block(ctx, op, Zkm1, ld, nvec, real, "Zkm1"));
+  if (R) RCF_TRY(check_block(ctx, op, R, ld, nvec, real, "R"));
+  if (overlaps(Zk, ld, out, ld, nvec, 2 * real) || overlaps(R, ld, out, ld, nvec, 2 * real))
+    return fail(ctx, RCF_EINVAL, "out overlaps Zk or R");
+  if (Zkm1 && Zkm1 != out && overlaps(Zkm1, ld, out, ld, nvec, 2 * real))
+    return fail(ctx, RCF_EINVAL, "out partly overlaps Zkm1");
+  if (R && !g) return fail(ctx, RCF_EINVAL, "R given without g");
+  if (nvec == 0) return RCF_OK;
+  if (prec == RCF_FP64) {
+    StepArgs<double> a = step_args<double>(static_cast<const double*>(Zk), ld, static_cast<double*>(out), ld, nvec, alpha, beta);
+    if (Zkm1) { a.prev = static_cast<const double*>(Zkm1); a.ld_prev = ld; a.C = gamma; }
+    if (R) { a.rv = static_cast<const double*>(R); a.ld_rv = ld; a.g = g; }
+    return apply_full<double>(ctx, op, form, a);
+  }
+  StepArgs<float> a = step_args<float>(static_cast<const float*>(Zk), ld, static_cast<float*>(out), ld, nvec, float(alpha), float(beta));
+  if (Zkm1) { a.prev = static_cast<const float*>(Zkm1); a.ld_prev = ld; a.C = float(gamma); }
+  if (R) { a.rv = static_cast<const float*>(R); a.ld_rv = ld; a.g = g; }
+  return apply_full<float>(ctx, op, form, a);
+}
+
+extern "C" int64_t rcf_launch_count(const rcf_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
 extern "C" int rcf_residual(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
                             const double* ritz, double* R, int64_t ldr, double* colnorm) {
   if (!ctx || !op) return RCF_EINVAL;

@@ -33,6 +33,7 @@ struct rcf_ctx {
   cusolverDnHandle_t solver = nullptr;
   std::string last_error;
   double* d_pj = nullptr;   // spin-orbit channel projectors P_{1/2}, P_{3/2} (6x6 complex each)
+  int64_t launches = 0;     // kernels launched by this library on this context
   // grow-only scratch buffers, one per slot
   std::vector<void*> ws_ptr;
   std::vector<size_t> ws_size;
@@ -96,7 +97,11 @@ int cuda_fail(rcf_ctx* ctx, cudaError_t e, const char* what, const char* file, i
     if (_e != cudaSuccess) return rcf::cuda_fail((ctx), _e, #expr, __FILE__, __LINE__); \
   } while (0)
 
-#define RCF_CHECK_LAUNCH(ctx) RCF_CUDA(ctx, cudaGetLastError())
+#define RCF_CHECK_LAUNCH(ctx)          \
+  do {                                 \
+    ++(ctx)->launches;                 \
+    RCF_CUDA(ctx, cudaGetLastError()); \
+  } while (0)
 
 #define RCF_TRY(expr)              \
   do {                             \

@@ -27,7 +27,7 @@ EXPORTS = [
     "rcf_mesh_quadrature_points", "rcf_mesh_mass", "rcf_op_create", "rcf_op_destroy",
     "rcf_potential_set", "rcf_projectors_set", "rcf_projectors_couplings", "rcf_projector_support",
     "rcf_apply", "rcf_lanczos_bounds", "rcf_residual", "rcf_filter", "rcf_rayleigh_ritz",
-    "rcf_grad_bilinear", "rcf_adjoint_filter",
+    "rcf_grad_bilinear", "rcf_adjoint_filter", "rcf_cheb_step", "rcf_launch_count",
 ]
 
 _lib = None
@@ -74,6 +74,8 @@ def lib() -> ctypes.CDLL:
         "rcf_rayleigh_ritz": (i32, [vp, vp, vp, i64, i32, vp, i64, vp]),
         "rcf_grad_bilinear": (i32, [vp, vp, vp, i64, vp, i64, i32, dbl, vp, vp, vp]),
         "rcf_adjoint_filter": (i32, [vp, vp, vp, i64, i32, vp, i32, vp, i32, i32, vp, i64, i32, vp, vp, vp]),
+        "rcf_cheb_step": (i32, [vp, vp, i32, i32, vp, vp, vp, i64, i32, dbl, dbl, dbl, vp, vp]),
+        "rcf_launch_count": (i64, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -292,3 +294,23 @@ def rcf_adjoint_filter(ctx, op, X, ritz, degree: int, bounds, mode: int, prec: i
                                          int(mode), int(prec), pyb, ldyb, int(ckpt_every),
                                          ctypes.c_void_p(dV.data_ptr()), ctypes.c_void_p(dB.data_ptr()),
                                          _np_ptr(dh) if dh is not None else None))
+
+
+def rcf_cheb_step(ctx, op, form: int, prec: int, Zk, Zkm1, R, alpha: float, beta: float, gamma: float,
+                  g, out):
+    """out = alpha op(Zk) + beta Zk + gamma Zkm1 + g[v] R (tensors of shape (nvec, rows))."""
+    import torch
+    dt = torch.complex128 if prec == RCF_FP64 else torch.complex64
+    pz, ld = _dev(Zk, dt, "Zk")
+    po, ldo = _dev(out, dt, "out")
+    if ldo != ld:
+        raise ValueError("Zk and out must share the leading dimension")
+    pm = None if Zkm1 is None else _dev(Zkm1, dt, "Zkm1")[0]
+    pr = None if R is None else _dev(R, dt, "R")[0]
+    pg = None if g is None else ctypes.c_void_p(g.data_ptr())
+    _check(ctx, lib().rcf_cheb_step(ctx, op, int(form), int(prec), pz, pm, pr, ld, Zk.shape[0],
+                                    float(alpha), float(beta), float(gamma), pg, po))
+
+
+def rcf_launch_count(ctx) -> int:
+    return int(lib().rcf_launch_count(ctx))

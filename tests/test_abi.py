@@ -12,7 +12,7 @@ HEADER = os.path.join(ROOT, "include", "rchfsi.h")
 
 def declared_symbols():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|int)\s+(rcf_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+char\s*\*|int64_t|int)\s+(rcf_\w+)\s*\(", text, re.M)))
 
 
 @pytest.fixture(scope="module")
