@@ -240,14 +240,14 @@ def run_ours(args):
     import numpy as np
     import torch
 
-    from paper_2605_30128_gb300 import build as pbuild
+    from paper_2605_30128_gb300.build import build as build_library
     from paper_2605_30128_gb300 import rchfsi as R
     from paper_2605_30128_gb300.problem import GPUProblem
 
     ws, rank, local = dist_init(args)
     torch.cuda.set_device(local)
     if rank == 0:
-        pbuild.build()
+        build_library()
     barrier(ws)
     w = workload_of(args)
     dev = torch.device("cuda", local)

@@ -266,10 +266,22 @@ extern "C" int rcf_mesh_create(rcf_ctx* ctx, const int ncell[3], const double si
   m->mass.assign(size_t(m->nnodes), 0.0);
   for (int64_t e = 0; e < m->ncells; ++e)
     for (int l = 0; l < m->nloc; ++l) m->mass[size_t(node_of(m, e, l))] += wq(m, l);
+  std::vector<double> inv64(size_t(m->nnodes));
+  std::vector<float> inv32(size_t(m->nnodes));
+  for (int64_t I = 0; I < m->nnodes; ++I) {
+    inv64[I] = 1.0 / m->mass[I];
+    inv32[I] = float(inv64[I]);
+  }
   cudaError_t err = cudaMalloc(&m->d_mass, sizeof(double) * m->nnodes);
   if (err == cudaSuccess) err = cudaMemcpy(m->d_mass, m->mass.data(), sizeof(double) * m->nnodes, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMalloc(&m->d_inv_mass64, sizeof(double) * m->nnodes);
+  if (err == cudaSuccess) err = cudaMemcpy(m->d_inv_mass64, inv64.data(), sizeof(double) * m->nnodes, cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMalloc(&m->d_inv_mass32, sizeof(float) * m->nnodes);
+  if (err == cudaSuccess) err = cudaMemcpy(m->d_inv_mass32, inv32.data(), sizeof(float) * m->nnodes, cudaMemcpyHostToDevice);
   if (err != cudaSuccess) {
     cudaFree(m->d_mass);
+    cudaFree(m->d_inv_mass64);
+    cudaFree(m->d_inv_mass32);
     delete m;
     return cuda_fail(ctx, err, "mass upload", __FILE__, __LINE__);
   }
@@ -280,6 +292,8 @@ extern "C" int rcf_mesh_create(rcf_ctx* ctx, const int ncell[3], const double si
 extern "C" int rcf_mesh_destroy(rcf_mesh* m) {
   if (!m) return RCF_OK;
   cudaFree(m->d_mass);
+  cudaFree(m->d_inv_mass64);
+  cudaFree(m->d_inv_mass32);
   delete m;
   return RCF_OK;
 }

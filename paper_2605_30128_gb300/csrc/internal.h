@@ -54,6 +54,8 @@ struct rcf_mesh {
   double detJ;
   std::vector<double> mass;   // host M_I
   double* d_mass = nullptr;   // device M_I
+  double* d_inv_mass64 = nullptr;   // device 1 / M_I
+  float* d_inv_mass32 = nullptr;
 };
 
 struct ProjAtoms {

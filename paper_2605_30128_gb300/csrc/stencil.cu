@@ -15,10 +15,14 @@
 // I = x + Gx (y + Gy z), each node a 4-tuple (re_up, im_up, re_dn, im_dn).
 // A block owns a TX x TY tile of (x, y) columns of one vector and marches
 // through all z planes.  Each plane (tile plus the x/y halo of one element
-// width) is staged in shared memory by cp.async through an NST-deep ring; the
-// z direction is handled in registers (each thread keeps its z-line of the
-// current element).  Every input element is read from L2/HBM once per plane
-// visit; outputs are written once.
+// width), and the tile's potential, previous iterate and residual, are
+// staged in shared memory by cp.async through an NST-deep ring, so every
+// global load is issued NST-1 planes ahead of its use.  The z direction is
+// accumulated incrementally: when plane c of a 1D element arrives, its
+// contribution A Cz[cc][c] u_c is added to all P outputs of the element, and
+// the element's P planes are written when its closing vertex plane arrives.
+// Every input element is read from L2/HBM once per plane visit; outputs are
+// written once.
 #include "internal.h"
 
 namespace rcf {
@@ -102,19 +106,23 @@ struct KTab {
 };
 
 template <typename Real, int P, int TX, int TY, int NST>
-__global__ void __launch_bounds__(TX* TY)
+__global__ void __launch_bounds__(TX* TY, 1)
     step_kernel(const StepArgs<Real> a, const KTab<Real, P> tab, const int Gx, const int Gy,
                 const int Gz) {
-  constexpr int W = TX + P + 1;   // staged columns: x0 - P .. x0 + TX
-  constexpr int H = TY + P + 1;   // staged rows:    y0 - P .. y0 + TY
+  // tab holds A * (x, y, z 1D operators); see launch_p.
+  constexpr int W = TX + P + 1;        // staged columns: x0 - P .. x0 + TX
+  constexpr int H = TY + P + 1;        // staged rows:    y0 - P .. y0 + TY
   constexpr int NT = TX * TY;
+  constexpr int HALO = H * W;
+  constexpr int KMAX = (HALO + NT - 1) / NT;
+  constexpr int STAGE = HALO + 3 * NT; // plane with halo, then own potential, prev, rv
   using V4 = R4<Real>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  V4* S = reinterpret_cast<V4*>(smem_raw);                         // [NST][H][W]
-  Real* ST = reinterpret_cast<Real*>(S + NST * H * W);            // [3][P+1][P+1]
+  V4* S = reinterpret_cast<V4*>(smem_raw);                        // [NST][STAGE]
+  Real* ST = reinterpret_cast<Real*>(S + NST * STAGE);           // [2][P+1][P+1] x and y tables
 
   const int tid = threadIdx.x;
-  for (int i = tid; i < 3 * (P + 1) * (P + 1); i += NT) ST[i] = (&tab.c[0][0][0])[i];
+  for (int i = tid; i < 2 * (P + 1) * (P + 1); i += NT) ST[i] = (&tab.c[0][0][0])[i];
 
   const int lx = tid % TX, ly = tid / TX;
   const int ntx = (Gx + TX - 1) / TX;
@@ -125,26 +133,56 @@ __global__ void __launch_bounds__(TX* TY)
   const bool active = (gx < Gx) && (gy < Gy);
   const int nz = Gz / P;
   const int64_t plane = int64_t(Gx) * Gy;
+  const int64_t col = active ? int64_t(gx) + int64_t(Gx) * gy : 0;
 
   const V4* in = reinterpret_cast<const V4*>(a.in + 2 * int64_t(v) * a.ld_in);
+  const V4* prev = a.prev ? reinterpret_cast<const V4*>(a.prev + 2 * int64_t(v) * a.ld_prev) : nullptr;
+  const V4* rv = a.rv ? reinterpret_cast<const V4*>(a.rv + 2 * int64_t(v) * a.ld_rv) : nullptr;
+  V4* out = reinterpret_cast<V4*>(a.out + 2 * int64_t(v) * a.ld_out);
+  const V4* pot = reinterpret_cast<const V4*>(a.pot);
+
+  // this thread's share of the halo plane: shared-memory slot and in-plane offset (periodic wrap)
+  int hs[KMAX], hg[KMAX];
+#pragma unroll
+  for (int k = 0; k < KMAX; ++k) {
+    const int e = tid + k * NT;
+    hs[k] = -1;
+    hg[k] = 0;
+    if (e < HALO) {
+      const int r = e / W, c = e - r * W;
+      if ((r >= P && r < P + TY) || (c >= P && c < P + TX)) {
+        int xx = (x0 - P + c) % Gx;
+        if (xx < 0) xx += Gx;
+        int yy = (y0 - P + r) % Gy;
+        if (yy < 0) yy += Gy;
+        hs[k] = e;
+        hg[k] = xx + Gx * yy;
+      }
+    }
+  }
 
   auto issue_plane = [&](int z, int s) {
-    V4* dst = S + s * H * W;
+    V4* st = S + s * STAGE;
     const V4* src = in + int64_t(z) * plane;
-    for (int e = tid; e < H * W; e += NT) {
-      const int r = e / W, c = e - r * W;
-      const bool need = (r >= P && r < P + TY) || (c >= P && c < P + TX);
-      if (!need) continue;
-      int xx = (x0 - P + c) % Gx;
-      if (xx < 0) xx += Gx;
-      int yy = (y0 - P + r) % Gy;
-      if (yy < 0) yy += Gy;
-      cp_async_r4(dst + e, src + xx + int64_t(Gx) * yy);
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k)
+      if (hs[k] >= 0) cp_async_r4(st + hs[k], src + hg[k]);
+    if (active) {
+      const int64_t I = col + int64_t(z) * plane;
+      cp_async_r4(st + HALO + tid, pot + I);
+      if (prev) cp_async_r4(st + HALO + NT + tid, prev + I);
+      if (rv) cp_async_r4(st + HALO + 2 * NT + tid, rv + I);
     }
     cp_async_commit();
   };
 
-  // prologue: start the plane ring
+  // element -1 (planes Gz-P .. Gz-1) contributes row P of its 1D matrix to the vertex plane 0
+  V4 accn = zero4<Real>();
+  if (active) {
+#pragma unroll
+    for (int c = 0; c < P; ++c) fma4(accn, tab.c[2][P][c], ldg4(in + col + int64_t(Gz - P + c) * plane));
+  }
+
 #pragma unroll
   for (int s = 0; s < NST - 1; ++s) {
     if (s < Gz) issue_plane(s, s);
@@ -152,7 +190,7 @@ __global__ void __launch_bounds__(TX* TY)
   }
   int zload = NST - 1;
 
-  __syncthreads();  // coefficient table visible
+  __syncthreads();  // tables visible
   const int ax = lx % P, by = ly % P;
   Real cx[P + 1], cy[P + 1];
 #pragma unroll
@@ -160,113 +198,107 @@ __global__ void __launch_bounds__(TX* TY)
     cx[q] = ST[(0 * (P + 1) + ax) * (P + 1) + q];
     cy[q] = ST[(1 * (P + 1) + by) * (P + 1) + q];
   }
-
-  // own z-line of element -1 (planes Gz-P .. Gz-1), for the vertex carry
-  V4 zprev[P];
-  const int64_t col = int64_t(gx) + int64_t(Gx) * gy;
-#pragma unroll
-  for (int c = 0; c < P; ++c)
-    zprev[c] = active ? ldg4(in + col + int64_t(Gz - P + c) * plane) : zero4<Real>();
-
-  // wait for plane z, refill the ring, return own value and the x + y terms
-  auto consume = [&](int z, V4& own, V4& xy) {
-    cp_async_wait<NST - 2>();
-    __syncthreads();
-    if (zload < Gz) issue_plane(zload, zload % NST);
-    else cp_async_commit();
-    ++zload;
-    const V4* Pl = S + (z % NST) * H * W;
-    own = Pl[(ly + P) * W + lx + P];
-    V4 t = zero4<Real>();
-    // x: right element (a' = 0..P) and, for a vertex, the left element
-    const V4* row = Pl + (ly + P) * W;
-    const int cb = lx - ax + P;
-#pragma unroll
-    for (int q = 0; q <= P; ++q) fma4(t, cx[q], row[cb + q]);
-    if (ax == 0) {
-#pragma unroll
-      for (int q = 0; q <= P; ++q) fma4(t, ST[(0 * (P + 1) + P) * (P + 1) + q], row[cb - P + q]);
-    }
-    // y
-    const int rb = ly - by + P;
-#pragma unroll
-    for (int q = 0; q <= P; ++q) fma4(t, cy[q], Pl[(rb + q) * W + lx + P]);
-    if (by == 0) {
-#pragma unroll
-      for (int q = 0; q <= P; ++q) fma4(t, ST[(1 * (P + 1) + P) * (P + 1) + q], Pl[(rb - P + q) * W + lx + P]);
-    }
-    xy = t;
-  };
-
-  const Real* Tz = ST + 2 * (P + 1) * (P + 1);
-  V4 zl[P + 1], acc[P];
-  V4 accn = zero4<Real>();
-  consume(0, zl[0], acc[0]);
-  const V4 zfirst = zl[0];
-  V4 carry = zero4<Real>();
-#pragma unroll
-  for (int c = 0; c < P; ++c) fma4(carry, Tz[P * (P + 1) + c], zprev[c]);
-  fma4(carry, Tz[P * (P + 1) + P], zl[0]);
-
-  const V4* prev = a.prev ? reinterpret_cast<const V4*>(a.prev + 2 * int64_t(v) * a.ld_prev) : nullptr;
-  const V4* rv = a.rv ? reinterpret_cast<const V4*>(a.rv + 2 * int64_t(v) * a.ld_rv) : nullptr;
-  V4* out = reinterpret_cast<V4*>(a.out + 2 * int64_t(v) * a.ld_out);
-  const V4* pot = reinterpret_cast<const V4*>(a.pot);
+  const Real* cxv = ST + (0 * (P + 1) + P) * (P + 1);   // vertex rows (left element)
+  const Real* cyv = ST + (1 * (P + 1) + P) * (P + 1);
+  const Real A = a.A, B = a.B, C = a.C;
   const Real gv = a.g ? Real(a.g[v]) : Real(0);
+
+  V4 acc[P];
+  V4 u0 = zero4<Real>();
+
+  auto emit = [&](int ez) {
+    if (!active) return;
+#pragma unroll
+    for (int cc = 0; cc < P; ++cc) {
+      const int64_t I = col + int64_t(ez * P + cc) * plane;
+      V4 r = acc[cc];
+      if (a.scale_out) {
+        const Real mI = Real(a.mass[I]);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) r.v[i] *= mI;
+      }
+      st4(out + I, r);
+    }
+  };
 
   for (int ez = 0; ez < nz; ++ez) {
 #pragma unroll
-    for (int c = 1; c <= P; ++c) {
-      if (c < P) {
-        consume(ez * P + c, zl[c], acc[c]);
-      } else if (ez < nz - 1) {
-        consume(ez * P + c, zl[P], accn);
-      } else {
-        zl[P] = zfirst;
+    for (int c = 0; c < P; ++c) {
+      const int z = ez * P + c;
+      cp_async_wait<NST - 2>();
+      __syncthreads();
+      if (zload < Gz) issue_plane(zload, zload % NST);
+      else cp_async_commit();
+      ++zload;
+      const V4* Pl = S + (z % NST) * STAGE;
+      const V4 u = Pl[(ly + P) * W + lx + P];
+      // x and y terms (tables carry the factor A)
+      V4 self = zero4<Real>();
+      {
+        const V4* row = Pl + (ly + P) * W;
+        const int cb = lx - ax + P;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) fma4(self, cx[q], row[cb + q]);
+        if (ax == 0) {
+#pragma unroll
+          for (int q = 0; q <= P; ++q) fma4(self, cxv[q], row[cb - P + q]);
+        }
+        const int rb = ly - by + P;
+#pragma unroll
+        for (int q = 0; q <= P; ++q) fma4(self, cy[q], Pl[(rb + q) * W + lx + P]);
+        if (by == 0) {
+#pragma unroll
+          for (int q = 0; q <= P; ++q) fma4(self, cyv[q], Pl[(rb - P + q) * W + lx + P]);
+        }
       }
-    }
-    // z term of this element
+      // A (potential) u + B u + C prev + g rv
+      {
+        V4 hp = zero4<Real>();
+        add_potential(hp, Pl[HALO + tid], u);
 #pragma unroll
-    for (int cc = 0; cc < P; ++cc) {
-#pragma unroll
-      for (int q = 0; q <= P; ++q) fma4(acc[cc], Tz[cc * (P + 1) + q], zl[q]);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) acc[0].v[i] += carry.v[i];
-    carry = zero4<Real>();
-#pragma unroll
-    for (int q = 0; q <= P; ++q) fma4(carry, Tz[P * (P + 1) + q], zl[q]);
-
-    if (active) {
-#pragma unroll
-      for (int cc = 0; cc < P; ++cc) {
-        const int64_t I = col + int64_t(ez * P + cc) * plane;
-        V4 hu = acc[cc];
-        add_potential(hu, ldg4(pot + I), zl[cc]);
-        V4 res;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) res.v[i] = a.A * hu.v[i] + a.B * zl[cc].v[i];
+        for (int i = 0; i < 4; ++i) self.v[i] = fma(A, hp.v[i], fma(B, u.v[i], self.v[i]));
         if (prev) {
-          const V4 pv = ld4(prev + I);
+          const V4 pv = Pl[HALO + NT + tid];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) res.v[i] = fma(a.C, pv.v[i], res.v[i]);
+          for (int i = 0; i < 4; ++i) self.v[i] = fma(C, pv.v[i], self.v[i]);
         }
         if (rv) {
-          const V4 r = ldg4(rv + I);
+          const V4 rr = Pl[HALO + 2 * NT + tid];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) res.v[i] = fma(gv, r.v[i], res.v[i]);
+          for (int i = 0; i < 4; ++i) self.v[i] = fma(gv, rr.v[i], self.v[i]);
         }
-        if (a.scale_out) {
-          const Real mI = Real(a.mass[I]);
+      }
+      if (c == 0) {
+        // the vertex plane closes element ez-1 (its local node P) and opens element ez
+        fma4(accn, tab.c[2][P][P], u);
+        if (ez > 0) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) res.v[i] *= mI;
+          for (int cc = 0; cc < P; ++cc) fma4(acc[cc], tab.c[2][cc][P], u);
+          emit(ez - 1);
+        } else {
+          u0 = u;
         }
-        st4(out + I, res);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[0].v[i] = accn.v[i] + self.v[i];
+#pragma unroll
+        for (int cc = 1; cc < P; ++cc) acc[cc] = zero4<Real>();
+#pragma unroll
+        for (int cc = 0; cc < P; ++cc) fma4(acc[cc], tab.c[2][cc][0], u);
+        accn = zero4<Real>();
+        fma4(accn, tab.c[2][P][0], u);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[c].v[i] += self.v[i];
+#pragma unroll
+        for (int cc = 0; cc < P; ++cc) fma4(acc[cc], tab.c[2][cc][c], u);
+        fma4(accn, tab.c[2][P][c], u);
       }
     }
-    zl[0] = zl[P];
-    acc[0] = accn;
   }
+  // the last element closes on plane Gz = 0 (periodic)
+#pragma unroll
+  for (int cc = 0; cc < P; ++cc) fma4(acc[cc], tab.c[2][cc][P], u0);
+  emit(nz - 1);
   cp_async_wait<0>();
 }
 
@@ -280,14 +312,15 @@ struct TileOf {
 template <typename Real, int P>
 int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a) {
   constexpr int T = TileOf<Real, P>::T;
-  constexpr int NST = 4;
+  constexpr int NST = 4;   // three planes in flight per block
+  // the kernel multiplies the operator by A through its tables
   KTab<Real, P> kt;
   for (int d = 0; d < 3; ++d)
     for (int i = 0; i <= P; ++i)
-      for (int j = 0; j <= P; ++j) kt.c[d][i][j] = Real(t.c[d][i][j]);
+      for (int j = 0; j <= P; ++j) kt.c[d][i][j] = Real(double(a.A) * t.c[d][i][j]);
   const int ntx = (m->G[0] + T - 1) / T, nty = (m->G[1] + T - 1) / T;
-  const size_t smem = size_t(NST) * (T + P + 1) * (T + P + 1) * sizeof(R4<Real>) +
-                      3 * (P + 1) * (P + 1) * sizeof(Real);
+  const size_t stage = size_t(T + P + 1) * (T + P + 1) + 3 * size_t(T) * T;
+  const size_t smem = size_t(NST) * stage * sizeof(R4<Real>) + 2 * (P + 1) * (P + 1) * sizeof(Real);
   auto kern = step_kernel<Real, P, T, T, NST>;
   if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   dim3 grid(ntx * nty, a.nvec);

@@ -27,19 +27,32 @@ __global__ void scale_mass_kernel(const double* __restrict__ mass, int64_t rows,
   reinterpret_cast<double2*>(y + 2 * int64_t(v) * ldy)[r] = make_double2(s * a.x, s * a.y);
 }
 
-template <typename ZReal>
-__global__ void recover_kernel(const double* __restrict__ mass, int64_t rows, const ZReal* __restrict__ Z,
-                               int64_t ldz, double zs, const double* __restrict__ X, int64_t ldx,
-                               const double* __restrict__ lam, double* __restrict__ Y, int64_t ldy) {
+// Y = zs D^{-1} Z + X lam[v]; the D^{-1} Z term in the precision of Z, the rest in FP64
+__global__ void recover_kernel_f32(const float* __restrict__ invm, int64_t rows, const float* __restrict__ Z,
+                                   int64_t ldz, float zs, const double* __restrict__ X, int64_t ldx,
+                                   const double* __restrict__ lam, double* __restrict__ Y, int64_t ldy) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   const int v = blockIdx.y;
   if (r >= rows) return;
-  const double d = zs / mass[r >> 1];
-  const ZReal* z = Z + 2 * (int64_t(v) * ldz + r);
+  const float d = zs * invm[r >> 1];
+  const float2 z = reinterpret_cast<const float2*>(Z + 2 * int64_t(v) * ldz)[r];
   const double2 xv = reinterpret_cast<const double2*>(X + 2 * int64_t(v) * ldx)[r];
   const double l = lam[v];
   reinterpret_cast<double2*>(Y + 2 * int64_t(v) * ldy)[r] =
-      make_double2(fma(d, double(z[0]), l * xv.x), fma(d, double(z[1]), l * xv.y));
+      make_double2(fma(l, xv.x, double(d * z.x)), fma(l, xv.y, double(d * z.y)));
+}
+
+__global__ void recover_kernel_f64(const double* __restrict__ invm, int64_t rows, const double* __restrict__ Z,
+                                   int64_t ldz, double zs, const double* __restrict__ X, int64_t ldx,
+                                   const double* __restrict__ lam, double* __restrict__ Y, int64_t ldy) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (r >= rows) return;
+  const double d = zs * invm[r >> 1];
+  const double2 z = reinterpret_cast<const double2*>(Z + 2 * int64_t(v) * ldz)[r];
+  const double2 xv = reinterpret_cast<const double2*>(X + 2 * int64_t(v) * ldx)[r];
+  const double l = lam[v];
+  reinterpret_cast<double2*>(Y + 2 * int64_t(v) * ldy)[r] = make_double2(fma(d, z.x, l * xv.x), fma(d, z.y, l * xv.y));
 }
 
 __global__ void to_c64_kernel(int64_t rows, const double* __restrict__ x, int64_t ldx,
@@ -204,21 +217,26 @@ int launch_scale_mass(rcf_ctx* ctx, const rcf_mesh* m, const double* x, int64_t 
   return RCF_OK;
 }
 
-template <typename ZReal>
-int launch_recover(rcf_ctx* ctx, const rcf_mesh* m, const ZReal* Z, int64_t ldz, double zs,
-                   const double* X, int64_t ldx, const double* lam, int nvec, double* Y,
-                   int64_t ldy) {
+template <>
+int launch_recover<float>(rcf_ctx* ctx, const rcf_mesh* m, const float* Z, int64_t ldz, double zs,
+                          const double* X, int64_t ldx, const double* lam, int nvec, double* Y, int64_t ldy) {
   if (nvec <= 0) return RCF_OK;
   const int64_t rows = 2 * m->nnodes;
-  recover_kernel<ZReal><<<dim3(blocks_for(rows), nvec), kThreads, 0, ctx->stream>>>(
-      m->d_mass, rows, Z, ldz, zs, X, ldx, lam, Y, ldy);
+  recover_kernel_f32<<<dim3(blocks_for(rows), nvec), kThreads, 0, ctx->stream>>>(
+      m->d_inv_mass32, rows, Z, ldz, float(zs), X, ldx, lam, Y, ldy);
   RCF_CHECK_LAUNCH(ctx);
   return RCF_OK;
 }
-template int launch_recover<float>(rcf_ctx*, const rcf_mesh*, const float*, int64_t, double,
-                                   const double*, int64_t, const double*, int, double*, int64_t);
-template int launch_recover<double>(rcf_ctx*, const rcf_mesh*, const double*, int64_t, double,
-                                    const double*, int64_t, const double*, int, double*, int64_t);
+template <>
+int launch_recover<double>(rcf_ctx* ctx, const rcf_mesh* m, const double* Z, int64_t ldz, double zs,
+                           const double* X, int64_t ldx, const double* lam, int nvec, double* Y, int64_t ldy) {
+  if (nvec <= 0) return RCF_OK;
+  const int64_t rows = 2 * m->nnodes;
+  recover_kernel_f64<<<dim3(blocks_for(rows), nvec), kThreads, 0, ctx->stream>>>(
+      m->d_inv_mass64, rows, Z, ldz, zs, X, ldx, lam, Y, ldy);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
 
 int launch_to_c64(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, int nvec, float* y,
                   int64_t ldy) {
