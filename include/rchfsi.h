@@ -131,6 +131,24 @@ int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec, const void
                   const void* Zkm1, const void* R, int64_t ld, int nvec, double alpha, double beta,
                   double gamma, const double* g, void* out);
 
+/* rcf_apply without any memory allocation (the paper has no counterpart).
+ * Same operation, arguments, layouts and errors as rcf_apply.  For callers
+ * that cannot let a library allocate device memory: a host whose GPU memory
+ * is already owned by its own pooling allocator, or a service loop that
+ * forbids allocation (and the device-wide synchronisation of cudaMalloc)
+ * after start-up.  The spin-orbit projector coefficients, which rcf_apply
+ * keeps in context scratch memory, live here in one fixed array of 6.29 MB
+ * inside the library's device image, present on every GPU that loads the
+ * library until the process exits.  Limit: natoms * nvec <= 16384 per call;
+ * larger calls return RCF_EINVAL with a message (split the vectors).  The
+ * first call on a device looks up the array's device address (once per
+ * device).  All calls share the one array: calls that may run at the same
+ * time on the GPU (different streams or contexts) race and must be
+ * serialised by the caller.  Nothing in the array needs clearing between
+ * calls: each call overwrites the coefficients it reads. */
+int rcf_apply_noalloc(rcf_ctx* ctx, const rcf_op* op, int form, const void* X, int64_t ldx,
+                      int nvec, void* Y, int64_t ldy, int prec);
+
 /* Number of kernels this context has launched so far (its own kernels; the
  * dense library routines of Rayleigh-Ritz are not counted). */
 int64_t rcf_launch_count(const rcf_ctx* ctx);

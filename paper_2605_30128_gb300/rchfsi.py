@@ -28,6 +28,7 @@ EXPORTS = [
     "rcf_potential_set", "rcf_projectors_set", "rcf_projectors_couplings", "rcf_projector_support",
     "rcf_apply", "rcf_lanczos_bounds", "rcf_residual", "rcf_filter", "rcf_rayleigh_ritz",
     "rcf_grad_bilinear", "rcf_adjoint_filter", "rcf_cheb_step", "rcf_launch_count",
+    "rcf_apply_noalloc",
 ]
 
 _lib = None
@@ -76,6 +77,7 @@ def lib() -> ctypes.CDLL:
         "rcf_adjoint_filter": (i32, [vp, vp, vp, i64, i32, vp, i32, vp, i32, i32, vp, i64, i32, vp, vp, vp]),
         "rcf_cheb_step": (i32, [vp, vp, i32, i32, vp, vp, vp, i64, i32, dbl, dbl, dbl, vp, vp]),
         "rcf_launch_count": (i64, [vp]),
+        "rcf_apply_noalloc": (i32, [vp, vp, i32, vp, i64, i32, vp, i64, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -314,3 +316,13 @@ def rcf_cheb_step(ctx, op, form: int, prec: int, Zk, Zkm1, R, alpha: float, beta
 
 def rcf_launch_count(ctx) -> int:
     return int(lib().rcf_launch_count(ctx))
+
+
+def rcf_apply_noalloc(ctx, op, form: int, X, Y, prec: int = RCF_FP64):
+    """rcf_apply that allocates nothing (fixed scratch inside the library; natoms * nvec <= 16384)."""
+    import torch
+    dt = torch.complex128 if prec == RCF_FP64 else torch.complex64
+    px, ldx = _dev(X, dt, "X")
+    py, ldy = _dev(Y, dt, "Y")
+    nvec = X.shape[0] if X.dim() == 2 else 1
+    _check(ctx, lib().rcf_apply_noalloc(ctx, op, form, px, ldx, nvec, py, ldy, prec))
