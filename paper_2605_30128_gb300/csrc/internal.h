@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/rchfsi.h"
+#include "rchfsi.h"
 
 namespace rcf {
 

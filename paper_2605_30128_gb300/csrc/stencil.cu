@@ -105,8 +105,22 @@ struct KTab {
   Real c[3][P + 1][P + 1];
 };
 
+// Tile shapes (multiples of P so that tiles start on element vertices) and blocks
+// per SM.  FP32: about 20 x 10 columns, two blocks per SM without spilling (the
+// best of the shapes timed on a GB300 for p = 5: 20x20/1, 20x10/2, 15x15/2,
+// 10x10/4), about 20 x 16 and one block for p >= 6; FP64 (ALU bound): about
+// 8 x 8, one block per SM.
+template <typename Real, int P>
+struct TileOf {
+  static constexpr bool f32 = sizeof(Real) == 4;
+  static constexpr bool small = P <= 5;   // two FP32 blocks per SM fit without spilling
+  static constexpr int TX = f32 ? P * ((20 + P - 1) / P) : P * ((8 + P - 1) / P);
+  static constexpr int TY = f32 ? P * (((small ? 10 : 16) + P - 1) / P) : P * ((8 + P - 1) / P);
+  static constexpr int MINB = (f32 && small) ? 2 : 1;
+};
+
 template <typename Real, int P, int TX, int TY, int NST>
-__global__ void __launch_bounds__(TX* TY, 1)
+__global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
     step_kernel(const StepArgs<Real> a, const KTab<Real, P> tab, const int Gx, const int Gy,
                 const int Gz) {
   // tab holds A * (x, y, z 1D operators); see launch_p.
@@ -303,28 +317,21 @@ __global__ void __launch_bounds__(TX* TY, 1)
 }
 
 template <typename Real, int P>
-struct TileOf {
-  // tile edge in nodes (a multiple of P): about 16 for FP32, 8 for FP64
-  static constexpr int base = sizeof(Real) == 4 ? 16 : 8;
-  static constexpr int T = P * ((base + P - 1) / P);
-};
-
-template <typename Real, int P>
 int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a) {
-  constexpr int T = TileOf<Real, P>::T;
+  constexpr int TX = TileOf<Real, P>::TX, TY = TileOf<Real, P>::TY;
   constexpr int NST = 4;   // three planes in flight per block
   // the kernel multiplies the operator by A through its tables
   KTab<Real, P> kt;
   for (int d = 0; d < 3; ++d)
     for (int i = 0; i <= P; ++i)
       for (int j = 0; j <= P; ++j) kt.c[d][i][j] = Real(double(a.A) * t.c[d][i][j]);
-  const int ntx = (m->G[0] + T - 1) / T, nty = (m->G[1] + T - 1) / T;
-  const size_t stage = size_t(T + P + 1) * (T + P + 1) + 3 * size_t(T) * T;
+  const int ntx = (m->G[0] + TX - 1) / TX, nty = (m->G[1] + TY - 1) / TY;
+  const size_t stage = size_t(TX + P + 1) * (TY + P + 1);
   const size_t smem = size_t(NST) * stage * sizeof(R4<Real>) + 2 * (P + 1) * (P + 1) * sizeof(Real);
-  auto kern = step_kernel<Real, P, T, T, NST>;
+  auto kern = step_kernel<Real, P, TX, TY, NST>;
   if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   dim3 grid(ntx * nty, a.nvec);
-  kern<<<grid, T * T, smem, ctx->stream>>>(a, kt, m->G[0], m->G[1], m->G[2]);
+  kern<<<grid, TX * TY, smem, ctx->stream>>>(a, kt, m->G[0], m->G[1], m->G[2]);
   RCF_CHECK_LAUNCH(ctx);
   return RCF_OK;
 }
