@@ -15,9 +15,10 @@
 // I = x + Gx (y + Gy z), each node a 4-tuple (re_up, im_up, re_dn, im_dn).
 // A block owns a TX x TY tile of (x, y) columns of one vector and marches
 // through all z planes.  Each plane (tile plus the x/y halo of one element
-// width), and the tile's potential, previous iterate and residual, are
-// staged in shared memory by cp.async through an NST-deep ring, so every
-// global load is issued NST-1 planes ahead of its use.  The z direction is
+// width) is staged in shared memory by cp.async through an NST-deep ring
+// (NST-1 planes in flight); the tile's own potential, previous iterate and
+// residual, which no other thread needs, go straight to registers one plane
+// ahead.  4-wide FP32 updates use packed FFMA2.  The z direction is
 // accumulated incrementally: when plane c of a 1D element arrives, its
 // contribution A Cz[cc][c] u_c is added to all P outputs of the element, and
 // the element's P planes are written when its closing vertex plane arrives.
@@ -45,6 +46,14 @@ template <typename Real>
 __device__ __forceinline__ void fma4(R4<Real>& acc, Real c, const R4<Real>& x) {
 #pragma unroll
   for (int i = 0; i < 4; ++i) acc.v[i] = fma(c, x.v[i], acc.v[i]);
+}
+// FP32: two packed FFMA2 (sm_100+) per 4-tuple
+template <>
+__device__ __forceinline__ void fma4<float>(R4<float>& acc, float c, const R4<float>& x) {
+  const float2 cc = make_float2(c, c);
+  const float2 lo = __ffma2_rn(cc, make_float2(x.v[0], x.v[1]), make_float2(acc.v[0], acc.v[1]));
+  const float2 hi = __ffma2_rn(cc, make_float2(x.v[2], x.v[3]), make_float2(acc.v[2], acc.v[3]));
+  acc.v[0] = lo.x; acc.v[1] = lo.y; acc.v[2] = hi.x; acc.v[3] = hi.y;
 }
 
 __device__ __forceinline__ R4<float> ldg4(const R4<float>* p) {
@@ -119,6 +128,12 @@ struct TileOf {
   static constexpr int MINB = (f32 && small) ? 2 : 1;
 };
 
+// shared-memory elements of one ring stage: the plane tile with its one-element x/y halo
+template <int P, int TX, int TY>
+__host__ __device__ constexpr int stage_elems() {
+  return (TX + P + 1) * (TY + P + 1);
+}
+
 template <typename Real, int P, int TX, int TY, int NST>
 __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
     step_kernel(const StepArgs<Real> a, const KTab<Real, P> tab, const int Gx, const int Gy,
@@ -129,7 +144,8 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
   constexpr int NT = TX * TY;
   constexpr int HALO = H * W;
   constexpr int KMAX = (HALO + NT - 1) / NT;
-  constexpr int STAGE = HALO + 3 * NT; // plane with halo, then own potential, prev, rv
+  constexpr int STAGE = stage_elems<P, TX, TY>();
+  static_assert(STAGE == HALO, "one stage holds the plane tile with its halo");
   using V4 = R4<Real>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   V4* S = reinterpret_cast<V4*>(smem_raw);                        // [NST][STAGE]
@@ -181,13 +197,17 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
       if (hs[k] >= 0) cp_async_r4(st + hs[k], src + hg[k]);
-    if (active) {
-      const int64_t I = col + int64_t(z) * plane;
-      cp_async_r4(st + HALO + tid, pot + I);
-      if (prev) cp_async_r4(st + HALO + NT + tid, prev + I);
-      if (rv) cp_async_r4(st + HALO + 2 * NT + tid, rv + I);
-    }
     cp_async_commit();
+  };
+  // this thread's potential, previous iterate and residual of one plane, one plane ahead.
+  // prev may alias out: each element is read here before this thread writes it.
+  V4 npot = zero4<Real>(), nprev = zero4<Real>(), nrv = zero4<Real>();
+  auto fetch_own = [&](int z) {
+    if (!active) return;
+    const int64_t I = col + int64_t(z) * plane;
+    npot = ldg4(pot + I);
+    if (prev) nprev = ldg4(prev + I);
+    if (rv) nrv = ldg4(rv + I);
   };
 
   // element -1 (planes Gz-P .. Gz-1) contributes row P of its 1D matrix to the vertex plane 0
@@ -203,6 +223,7 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
     else cp_async_commit();
   }
   int zload = NST - 1;
+  fetch_own(0);
 
   __syncthreads();  // tables visible
   const int ax = lx % P, by = ly % P;
@@ -246,6 +267,8 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
       ++zload;
       const V4* Pl = S + (z % NST) * STAGE;
       const V4 u = Pl[(ly + P) * W + lx + P];
+      const V4 cpot = npot, cprev = nprev, crv = nrv;
+      if (z + 1 < Gz) fetch_own(z + 1);
       // x and y terms (tables carry the factor A)
       V4 self = zero4<Real>();
       {
@@ -268,19 +291,11 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
       // A (potential) u + B u + C prev + g rv
       {
         V4 hp = zero4<Real>();
-        add_potential(hp, Pl[HALO + tid], u);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) self.v[i] = fma(A, hp.v[i], fma(B, u.v[i], self.v[i]));
-        if (prev) {
-          const V4 pv = Pl[HALO + NT + tid];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) self.v[i] = fma(C, pv.v[i], self.v[i]);
-        }
-        if (rv) {
-          const V4 rr = Pl[HALO + 2 * NT + tid];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) self.v[i] = fma(gv, rr.v[i], self.v[i]);
-        }
+        add_potential(hp, cpot, u);
+        fma4(self, A, hp);
+        fma4(self, B, u);
+        if (prev) fma4(self, C, cprev);
+        if (rv) fma4(self, gv, crv);
       }
       if (c == 0) {
         // the vertex plane closes element ez-1 (its local node P) and opens element ez
@@ -326,7 +341,7 @@ int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Re
     for (int i = 0; i <= P; ++i)
       for (int j = 0; j <= P; ++j) kt.c[d][i][j] = Real(double(a.A) * t.c[d][i][j]);
   const int ntx = (m->G[0] + TX - 1) / TX, nty = (m->G[1] + TY - 1) / TY;
-  const size_t stage = size_t(TX + P + 1) * (TY + P + 1);
+  const size_t stage = size_t(stage_elems<P, TX, TY>());
   const size_t smem = size_t(NST) * stage * sizeof(R4<Real>) + 2 * (P + 1) * (P + 1) * sizeof(Real);
   auto kern = step_kernel<Real, P, TX, TY, NST>;
   if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
