@@ -16,7 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librchfsi.so")
-SOURCES = ["api.cu", "stencil.cu", "nonlocal.cu", "vectors.cu", "filter.cu", "rr.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "stencil.cu", "stencil_tma.cu", "nonlocal.cu", "vectors.cu", "filter.cu", "rr.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -43,7 +44,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile (if needed) and return the path of librchfsi.so."""
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "internal.h"), os.path.join(ROOT, "include", "rchfsi.h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    headers.append(os.path.join(ROOT, "include", "rchfsi.h"))
     jobs = []
     objs = []
     for src in SOURCES:

@@ -195,6 +195,7 @@ extern "C" int rcf_create(rcf_ctx** out, int device, void* stream) {
     if (ctx->blas) cublasDestroy(ctx->blas);
     if (ctx->solver) cusolverDnDestroy(ctx->solver);
     if (ctx->d_pj) cudaFree(ctx->d_pj);
+    if (ctx->d_err) cudaFree(ctx->d_err);
     delete ctx;
     return st;
   };
@@ -207,6 +208,8 @@ extern "C" int rcf_create(rcf_ctx** out, int device, void* stream) {
   channel_projector_table(pj);
   if (cudaMalloc(&ctx->d_pj, sizeof(pj)) != cudaSuccess) { cudaGetLastError(); return bail(RCF_ENOMEM); }
   if (cudaMemcpy(ctx->d_pj, pj, sizeof(pj), cudaMemcpyHostToDevice) != cudaSuccess) return bail(RCF_ECUDA);
+  if (cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return bail(RCF_ENOMEM); }
+  if (cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess) return bail(RCF_ECUDA);
   *out = ctx;
   return RCF_OK;
 }
@@ -218,14 +221,29 @@ extern "C" int rcf_destroy(rcf_ctx* ctx) {
   if (ctx->blas) cublasDestroy(ctx->blas);
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   if (ctx->d_pj) cudaFree(ctx->d_pj);
+  if (ctx->d_err) cudaFree(ctx->d_err);
   delete ctx;
   return RCF_OK;
 }
 
+namespace rcf {
+int check_device_error(rcf_ctx* ctx) {
+  if (!ctx->d_err) return RCF_OK;
+  int h = 0;
+  RCF_CUDA(ctx, cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (h != 0) {
+    RCF_CUDA(ctx, cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    return fail(ctx, RCF_ETIMEOUT, "a device-side wait timed out (kernel returned early; results invalid)");
+  }
+  return RCF_OK;
+}
+}  // namespace rcf
+
 extern "C" int rcf_sync(rcf_ctx* ctx) {
   if (!ctx) return RCF_EINVAL;
   RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  return RCF_OK;
+  return check_device_error(ctx);
 }
 
 extern "C" int rcf_mesh_create(rcf_ctx* ctx, const int ncell[3], const double side[3], int p, rcf_mesh** out) {

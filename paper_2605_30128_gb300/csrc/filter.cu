@@ -449,7 +449,7 @@ extern "C" int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64
     // the per-block coefficient table is a host vector copied asynchronously
     RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   }
-  return RCF_OK;
+  return check_device_error(ctx);
 }
 
 extern "C" int rcf_lanczos_bounds(rcf_ctx* ctx, const rcf_op* op, int nsteps, const double* v0,

@@ -34,6 +34,7 @@ struct rcf_ctx {
   std::string last_error;
   double* d_pj = nullptr;   // spin-orbit channel projectors P_{1/2}, P_{3/2} (6x6 complex each)
   int64_t launches = 0;     // kernels launched by this library on this context
+  int* d_err = nullptr;     // device error word: set by a kernel whose bounded wait timed out
   // grow-only scratch buffers, one per slot
   std::vector<void*> ws_ptr;
   std::vector<size_t> ws_size;
@@ -149,6 +150,11 @@ void build_tables(const rcf_mesh* m, int kind, Tables* t);
 
 template <typename Real>
 int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a);
+// FP32 step with TMA plane loads (stencil_tma.cu); *used = false when it does not apply
+// (degree, tile divisibility, alignment, tensor-map encoding) and the caller falls back.
+int launch_step_tma(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<float>& a, bool* used);
+// RCF_ETIMEOUT (and clear the word) if a kernel recorded a timed-out wait; synchronises
+int check_device_error(rcf_ctx* ctx);
 
 // ---------------------------------------------------------------------------
 // nonlocal projectors (nonlocal.cu)

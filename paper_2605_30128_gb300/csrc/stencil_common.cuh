@@ -1,0 +1,111 @@
+// Device helpers shared by the step kernels (stencil.cu, stencil_tma.cu): 4-tuples of
+// a node's spinor values (re_up, im_up, re_dn, im_dn), packed FMAs, loads, the 2x2
+// spinor potential, the 1D coefficient tables and the tile shapes.
+#pragma once
+
+#include "internal.h"
+
+namespace rcf {
+namespace {
+
+template <typename Real>
+struct alignas(4 * sizeof(Real)) R4 {
+  Real v[4];
+};
+
+template <typename Real>
+__device__ __forceinline__ R4<Real> zero4() {
+  R4<Real> r;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r.v[i] = Real(0);
+  return r;
+}
+
+template <typename Real>
+__device__ __forceinline__ void fma4(R4<Real>& acc, Real c, const R4<Real>& x) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc.v[i] = fma(c, x.v[i], acc.v[i]);
+}
+// FP32: two packed FFMA2 (sm_100+) per 4-tuple
+template <>
+__device__ __forceinline__ void fma4<float>(R4<float>& acc, float c, const R4<float>& x) {
+  const float2 cc = make_float2(c, c);
+  const float2 lo = __ffma2_rn(cc, make_float2(x.v[0], x.v[1]), make_float2(acc.v[0], acc.v[1]));
+  const float2 hi = __ffma2_rn(cc, make_float2(x.v[2], x.v[3]), make_float2(acc.v[2], acc.v[3]));
+  acc.v[0] = lo.x; acc.v[1] = lo.y; acc.v[2] = hi.x; acc.v[3] = hi.y;
+}
+
+__device__ __forceinline__ R4<float> ldg4(const R4<float>* p) {
+  float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  R4<float> r;
+  r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  return r;
+}
+__device__ __forceinline__ R4<double> ldg4(const R4<double>* p) {
+  double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  R4<double> r;
+  r.v[0] = a.x; r.v[1] = a.y; r.v[2] = b.x; r.v[3] = b.y;
+  return r;
+}
+// plain (coherent) load for buffers that the same kernel may write (prev aliases out)
+template <typename Real>
+__device__ __forceinline__ R4<Real> ld4(const R4<Real>* p) {
+  return *p;
+}
+template <typename Real>
+__device__ __forceinline__ void st4(R4<Real>* p, const R4<Real>& x) {
+  *p = x;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+template <typename Real>
+__device__ __forceinline__ void cp_async_r4(R4<Real>* dst, const R4<Real>* src) {
+#pragma unroll
+  for (int i = 0; i < int(sizeof(R4<Real>) / 16); ++i)
+    cp_async16(reinterpret_cast<char*>(dst) + 16 * i, reinterpret_cast<const char*>(src) + 16 * i);
+}
+
+// 2x2 spinor potential (Eq. hloc): [[pv + bz, bx - i by], [bx + i by, pv - bz]] u
+template <typename Real>
+__device__ __forceinline__ void add_potential(R4<Real>& acc, const R4<Real>& pot, const R4<Real>& u) {
+  const Real pv = pot.v[0], bx = pot.v[1], by = pot.v[2], bz = pot.v[3];
+  const Real ur = u.v[0], ui = u.v[1], dr = u.v[2], di = u.v[3];
+  // up row
+  acc.v[0] += (pv + bz) * ur + bx * dr + by * di;
+  acc.v[1] += (pv + bz) * ui + bx * di - by * dr;
+  // down row
+  acc.v[2] += bx * ur - by * ui + (pv - bz) * dr;
+  acc.v[3] += bx * ui + by * ur + (pv - bz) * di;
+}
+
+template <typename Real, int P>
+struct KTab {
+  Real c[3][P + 1][P + 1];
+};
+
+// Tile shapes (multiples of P so that tiles start on element vertices) and blocks
+// per SM.  FP32: about 20 x 10 columns, two blocks per SM without spilling (the
+// best of the shapes timed on a GB300 for p = 5: 20x20/1, 20x10/2, 15x15/2,
+// 10x10/4), about 20 x 16 and one block for p >= 6; FP64 (ALU bound): about
+// 8 x 8, one block per SM.
+template <typename Real, int P>
+struct TileOf {
+  static constexpr bool f32 = sizeof(Real) == 4;
+  static constexpr bool small = P <= 5;   // two FP32 blocks per SM fit without spilling
+  static constexpr int TX = f32 ? P * ((20 + P - 1) / P) : P * ((8 + P - 1) / P);
+  static constexpr int TY = f32 ? P * (((small ? 10 : 16) + P - 1) / P) : P * ((8 + P - 1) / P);
+  static constexpr int MINB = (f32 && small) ? 2 : 1;
+};
+
+}  // namespace
+}  // namespace rcf

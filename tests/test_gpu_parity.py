@@ -22,6 +22,11 @@ MESHES = [
     ((4, 3, 2), (8.0, 6.0, 4.0), 6),     # p = 6, Gx = 24 > 18
     ((1, 2, 3), (2.0, 4.0, 6.0), 2),     # one cell along x: a node is its own periodic image
     ((9, 2, 1), (9.0, 2.0, 1.0), 1),     # p = 1
+    # meshes that the FP32 tiles divide, so the TMA kernel runs: one tile per plane (its
+    # strips wrap onto itself) and several tiles; p = 5 (20 x 10 tiles) and p = 4 (20 x 12)
+    ((4, 2, 2), (8.0, 4.0, 4.0), 5),
+    ((8, 4, 2), (16.0, 8.0, 4.0), 5),
+    ((5, 3, 2), (10.0, 6.0, 4.0), 4),
 ]
 
 
