@@ -60,6 +60,14 @@ typedef enum { RCF_CHFSI = 0, RCF_RCHFSI = 1 } rcf_mode;
 /* Operator form for rcf_apply: H, D^{-1} H or H D^{-1}. */
 typedef enum { RCF_FORM_H = 0, RCF_FORM_DINV_H = 1, RCF_FORM_H_DINV = 2 } rcf_form;
 
+/* FP32 step-kernel implementation (library-specific; the paper has no counterpart).
+ * RCF_STEP_CPASYNC (default): per-thread cp.async staging of each z plane with one
+ * block barrier per plane.  RCF_STEP_TMA: one producer thread issues five
+ * tensor-memory-accelerator boxes per plane into an mbarrier ring (degrees 4..6,
+ * meshes whose node counts in x and y the tile divides; other cases use the
+ * default).  Both compute the same sums in the same order. */
+typedef enum { RCF_STEP_CPASYNC = 0, RCF_STEP_TMA = 1 } rcf_step_kernel;
+
 /* ---- context ---------------------------------------------------------- */
 
 /* Create a context on CUDA device `device`, enqueueing all work on `stream`
@@ -152,6 +160,10 @@ int rcf_apply_noalloc(rcf_ctx* ctx, const rcf_op* op, int form, const void* X, i
 /* Number of kernels this context has launched so far (its own kernels; the
  * dense library routines of Rayleigh-Ritz are not counted). */
 int64_t rcf_launch_count(const rcf_ctx* ctx);
+
+/* Select the FP32 step kernel of this context (rcf_step_kernel).  Returns
+ * RCF_EINVAL for an unknown kind.  Takes effect at the next launch. */
+int rcf_set_step_kernel(rcf_ctx* ctx, int kind);
 
 /* ---- filter bounds (Section III-B-2; Lanczos as in Section III-C-1) --- */
 

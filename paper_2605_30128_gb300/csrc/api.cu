@@ -214,6 +214,13 @@ extern "C" int rcf_create(rcf_ctx** out, int device, void* stream) {
   return RCF_OK;
 }
 
+extern "C" int rcf_set_step_kernel(rcf_ctx* ctx, int kind) {
+  if (!ctx) return RCF_EINVAL;
+  if (kind != RCF_STEP_CPASYNC && kind != RCF_STEP_TMA) return fail(ctx, RCF_EINVAL, "unknown step kernel %d", kind);
+  ctx->step_kernel = kind;
+  return RCF_OK;
+}
+
 extern "C" int rcf_destroy(rcf_ctx* ctx) {
   if (!ctx) return RCF_OK;
   cudaStreamSynchronize(ctx->stream);

@@ -35,6 +35,7 @@ struct rcf_ctx {
   double* d_pj = nullptr;   // spin-orbit channel projectors P_{1/2}, P_{3/2} (6x6 complex each)
   int64_t launches = 0;     // kernels launched by this library on this context
   int* d_err = nullptr;     // device error word: set by a kernel whose bounded wait timed out
+  int step_kernel = RCF_STEP_CPASYNC;   // FP32 step kernel (rcf_set_step_kernel)
   // grow-only scratch buffers, one per slot
   std::vector<void*> ws_ptr;
   std::vector<size_t> ws_size;

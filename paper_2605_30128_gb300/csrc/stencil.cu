@@ -277,9 +277,11 @@ template <typename Real>
 int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a) {
   if (a.nvec <= 0) return RCF_OK;
   if constexpr (sizeof(Real) == 4) {
-    bool used = false;
-    RCF_TRY(launch_step_tma(ctx, m, t, a, &used));
-    if (used) return RCF_OK;
+    if (ctx->step_kernel == RCF_STEP_TMA) {
+      bool used = false;
+      RCF_TRY(launch_step_tma(ctx, m, t, a, &used));
+      if (used) return RCF_OK;
+    }
   }
   switch (m->p) {
     case 1: return launch_p<Real, 1>(ctx, m, t, a);

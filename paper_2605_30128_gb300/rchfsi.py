@@ -20,6 +20,7 @@ RCF_OK, RCF_EINVAL, RCF_ENOMEM, RCF_ECUDA, RCF_ENOTSPD, RCF_ETIMEOUT, RCF_ENOTSU
 RCF_FP64, RCF_FP32 = 0, 1
 RCF_CHFSI, RCF_RCHFSI = 0, 1
 RCF_FORM_H, RCF_FORM_DINV_H, RCF_FORM_H_DINV = 0, 1, 2
+RCF_STEP_CPASYNC, RCF_STEP_TMA = 0, 1
 
 EXPORTS = [
     "rcf_create", "rcf_destroy", "rcf_status_string", "rcf_last_error", "rcf_sync",
@@ -28,7 +29,7 @@ EXPORTS = [
     "rcf_potential_set", "rcf_projectors_set", "rcf_projectors_couplings", "rcf_projector_support",
     "rcf_apply", "rcf_lanczos_bounds", "rcf_residual", "rcf_filter", "rcf_rayleigh_ritz",
     "rcf_grad_bilinear", "rcf_adjoint_filter", "rcf_cheb_step", "rcf_launch_count",
-    "rcf_apply_noalloc",
+    "rcf_apply_noalloc", "rcf_set_step_kernel",
 ]
 
 _lib = None
@@ -78,6 +79,7 @@ def lib() -> ctypes.CDLL:
         "rcf_cheb_step": (i32, [vp, vp, i32, i32, vp, vp, vp, i64, i32, dbl, dbl, dbl, vp, vp]),
         "rcf_launch_count": (i64, [vp]),
         "rcf_apply_noalloc": (i32, [vp, vp, i32, vp, i64, i32, vp, i64, i32]),
+        "rcf_set_step_kernel": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -316,6 +318,11 @@ def rcf_cheb_step(ctx, op, form: int, prec: int, Zk, Zkm1, R, alpha: float, beta
 
 def rcf_launch_count(ctx) -> int:
     return int(lib().rcf_launch_count(ctx))
+
+
+def rcf_set_step_kernel(ctx, kind: int) -> None:
+    """FP32 step kernel of this context: RCF_STEP_CPASYNC (default) or RCF_STEP_TMA."""
+    _check(ctx, lib().rcf_set_step_kernel(ctx, int(kind)))
 
 
 def rcf_apply_noalloc(ctx, op, form: int, X, Y, prec: int = RCF_FP64):

@@ -176,3 +176,6 @@ def test_invalid_arguments_are_rejected(cfg1):
         R.rcf_filter(cfg1.g.ctx, cfg1.g.op, Xd, cfg1.lam, 0, cfg1.bounds, 1, 0, 0, Yd)   # degree 0
     # zero vectors is a no-op
     R.rcf_filter(cfg1.g.ctx, cfg1.g.op, Xd[:0], cfg1.lam[:0], 5, cfg1.bounds, 1, 0, 0, Yd[:0])
+    with pytest.raises(R.RcfError) as e:
+        R.rcf_set_step_kernel(cfg1.g.ctx, 7)                                             # unknown kernel
+    assert e.value.status == R.RCF_EINVAL

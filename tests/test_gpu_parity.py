@@ -22,18 +22,22 @@ MESHES = [
     ((4, 3, 2), (8.0, 6.0, 4.0), 6),     # p = 6, Gx = 24 > 18
     ((1, 2, 3), (2.0, 4.0, 6.0), 2),     # one cell along x: a node is its own periodic image
     ((9, 2, 1), (9.0, 2.0, 1.0), 1),     # p = 1
-    # meshes that the FP32 tiles divide, so the TMA kernel runs: one tile per plane (its
-    # strips wrap onto itself) and several tiles; p = 5 (20 x 10 tiles) and p = 4 (20 x 12)
-    ((4, 2, 2), (8.0, 4.0, 4.0), 5),
-    ((8, 4, 2), (16.0, 8.0, 4.0), 5),
-    ((5, 3, 2), (10.0, 6.0, 4.0), 4),
+    # meshes that the FP32 tiles divide, run with the TMA step kernel selected: one tile
+    # per plane (its strips wrap onto itself) and several tiles; p = 5 (20 x 10 tiles)
+    # and p = 4 (20 x 12)
+    ((4, 2, 2), (8.0, 4.0, 4.0), 5, "tma"),
+    ((8, 4, 2), (16.0, 8.0, 4.0), 5, "tma"),
+    ((5, 3, 2), (10.0, 6.0, 4.0), 4, "tma"),
 ]
 
 
-@pytest.fixture(scope="module", params=MESHES, ids=lambda m: f"n{m[0]}-p{m[2]}")
+@pytest.fixture(scope="module", params=MESHES, ids=lambda m: f"n{m[0]}-p{m[2]}" + ("-tma" if len(m) > 3 else ""))
 def pair(request):
-    n, L, p = request.param
+    from paper_2605_30128_gb300 import rchfsi as R
+    n, L, p = request.param[:3]
     pr = Pair(n, L, p, natoms=2)
+    if len(request.param) > 3:
+        R.rcf_set_step_kernel(pr.g.ctx, R.RCF_STEP_TMA)
     yield pr
     pr.close()
 
