@@ -51,8 +51,13 @@ typedef enum {
   RCF_ENOTSUP = 6    /* combination not built (e.g. degree p > 8) */
 } rcf_status;
 
-/* Arithmetic of the filter's Hamiltonian-multivector products. */
-typedef enum { RCF_FP64 = 0, RCF_FP32 = 1 } rcf_precision;
+/* Arithmetic of the filter's Hamiltonian-multivector products.  RCF_FP32_DF
+ * (R-ChFSI only): FP32 recurrence as RCF_FP32, with the residual R evaluated in
+ * double-float arithmetic (pairs of floats with exact products and error-free
+ * sums: about 2^-46 relative accuracy, against 2^-52 for FP64) instead of FP64,
+ * because this GPU runs FP64 at a small fraction of its FP32 rate.  The paper
+ * keeps R in FP64 (Section III-C); this variant is the library's. */
+typedef enum { RCF_FP64 = 0, RCF_FP32 = 1, RCF_FP32_DF = 2 } rcf_precision;
 
 /* Filter form: plain ChFSI (Eq. ChFSIrecurrence) or R-ChFSI (Eq. rChFSIrecurrence). */
 typedef enum { RCF_CHFSI = 0, RCF_RCHFSI = 1 } rcf_mode;
@@ -182,11 +187,20 @@ int rcf_lanczos_bounds(rcf_ctx* ctx, const rcf_op* op, int nsteps, const double*
 int rcf_residual(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
                  const double* ritz, double* R, int64_t ldr, double* colnorm);
 
+/* The same residual in double-float arithmetic (the residual of RCF_FP32_DF;
+ * no counterpart in the paper): Rh (c64) = the FP32 rounding of R, Rl (c64,
+ * may be NULL) = R - Rh rounded to FP32, so Rh + Rl carries R to about 2^-46
+ * relative to the sum of the magnitudes of its terms.  Rh and Rl share ldr and
+ * must not overlap each other or X.  Synchronises. */
+int rcf_residual_df(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
+                    const double* ritz, float* Rh, float* Rl, int64_t ldr);
+
 /* ---- the filter (Eq. ChFSIrecurrence / Eq. rChFSIrecurrence) ---------- */
 
 /* Y = filtered block of X, degree q = `degree` >= 1, bounds = {lambda_min,
  * lambda_T, lambda_max} (host; need lambda_min < lambda_T < lambda_max).
- * mode RCF_RCHFSI: R = H X - M X Lambda (FP64), Z_0 = 0, Z_1 = sigma_1 R / e,
+ * mode RCF_RCHFSI: R = H X - M X Lambda (FP64; double-float for
+ * RCF_FP32_DF), Z_0 = 0, Z_1 = sigma_1 R / e,
  * the residual recurrence in `prec`, Lambda_k propagated in FP64, recovery
  * Y = D^{-1} Z_q + X Lambda_q in FP64.  mode RCF_CHFSI: Eq. ChFSIrecurrence
  * with M^{-1} = D^{-1}; ritz may be NULL.  Vectors are processed in band

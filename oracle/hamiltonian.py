@@ -147,12 +147,19 @@ class Hamiltonian:
             Y[pr["rows"]] += pr["P"] @ (pr["Delta"] @ C)
         return Y
 
-    def apply_rows(self, X: np.ndarray, nodes) -> np.ndarray:
+    def apply_rows(self, X: np.ndarray, nodes, magnitudes: bool = False) -> np.ndarray:
         """Rows {2I, 2I+1 : I in nodes} of H X, each computed from the element matrices of the
-        cells that contain I (no global assembly); shape (2 len(nodes), nvec)."""
+        cells that contain I (no global assembly); shape (2 len(nodes), nvec).
+
+        magnitudes=True returns instead the same sums taken over the moduli of every factor
+        (|K^e| |X|, |potential block| |X|, |P| |Delta| |P^T| |X|): an upper bound of the sum
+        of the magnitudes of the terms of each entry, the scale of its rounding error."""
         mesh = self.mesh
         Ke = mesh.element_kinetic()
         X = np.asarray(X).reshape(self.N, -1)
+        if magnitudes:
+            X = np.abs(X)
+            Ke = np.abs(Ke)
         out = np.zeros((2 * len(nodes), X.shape[1]), dtype=np.complex128)
         for r, I in enumerate(nodes):
             cells, locs = np.nonzero(mesh.conn == I)
@@ -164,14 +171,15 @@ class Hamiltonian:
                 for be in range(2):
                     blk = (self.pv[I] if al == be else 0.0) + sum(self.pb[d][I] * PAULI[d][al, be]
                                                                 for d in range(3))
-                    out[2 * r + al] += blk * X[2 * I + be]
+                    out[2 * r + al] += (abs(blk) if magnitudes else blk) * X[2 * I + be]
         for pr in self.projectors:
-            C = pr["Delta"] @ (pr["P"].T @ X[pr["rows"]])
+            P, D = (np.abs(pr["P"]), np.abs(pr["Delta"])) if magnitudes else (pr["P"], pr["Delta"])
+            C = D @ (P.T @ X[pr["rows"]])
             pos = {int(I): k for k, I in enumerate(pr["support"])}
             for r, I in enumerate(nodes):
                 k = pos.get(int(I))
                 if k is not None:
-                    out[2 * r:2 * r + 2] += pr["P"][2 * k:2 * k + 2] @ C
+                    out[2 * r:2 * r + 2] += P[2 * k:2 * k + 2] @ C
         return out
 
     def dense(self) -> np.ndarray:

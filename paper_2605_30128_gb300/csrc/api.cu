@@ -148,6 +148,7 @@ int upload(rcf_ctx* ctx, T** dst, const T* src, size_t n) {
 void free_proj(ProjAtoms* pa) {
   cudaFree(pa->d_offsets); cudaFree(pa->d_node); cudaFree(pa->d_atom);
   cudaFree(pa->d_beta64); cudaFree(pa->d_beta32); cudaFree(pa->d_delta64); cudaFree(pa->d_delta32);
+  cudaFree(pa->d_nodemap); cudaFree(pa->d_uoff); cudaFree(pa->d_uent); cudaFree(pa->d_betadf);
   *pa = ProjAtoms();
 }
 
@@ -376,6 +377,7 @@ extern "C" int rcf_op_destroy(rcf_op* op) {
   if (op->ctx) cudaStreamSynchronize(op->ctx->stream);
   cudaFree(op->d_pot64);
   cudaFree(op->d_pot32);
+  cudaFree(op->d_potdf);
   free_proj(&op->proj);
   delete op;
   return RCF_OK;
@@ -414,8 +416,20 @@ extern "C" int rcf_potential_set(rcf_op* op, const double* V, const double* B, i
   for (double x : pot)
     if (!std::isfinite(x)) return fail(ctx, RCF_EINVAL, "potential contains a non-finite value");
   std::vector<float> pot32(pot.begin(), pot.end());
+  // double-float copy for the residual: (pv+bz, pv-bz, bx, by) / M_I, hi then lo
+  std::vector<float> potdf(8 * size_t(m->nnodes));
+  for (int64_t I = 0; I < m->nnodes; ++I) {
+    const double* q = &pot[4 * I];
+    const double c[4] = {q[0] + q[3], q[0] - q[3], q[1], q[2]};
+    for (int k = 0; k < 4; ++k) {
+      const float h = float(c[k]);
+      potdf[8 * I + k] = h;
+      potdf[8 * I + 4 + k] = float(c[k] - double(h));
+    }
+  }
   RCF_TRY(upload(ctx, &op->d_pot64, pot.data(), pot.size()));
   RCF_TRY(upload(ctx, &op->d_pot32, pot32.data(), pot32.size()));
+  RCF_TRY(upload(ctx, &op->d_potdf, potdf.data(), potdf.size()));
   return RCF_OK;
 }
 
@@ -483,6 +497,32 @@ extern "C" int rcf_projectors_set(rcf_op* op, int natoms, const double* pos, con
   RCF_TRY(upload(ctx, &pa.d_beta32, b32.data(), b32.size()));
   RCF_TRY(upload(ctx, &pa.d_delta64, pa.delta.data(), pa.delta.size()));
   RCF_TRY(upload(ctx, &pa.d_delta32, d32.data(), d32.size()));
+  // union of the supports: entry ids grouped by node, node -> union index
+  {
+    std::vector<int> order(pa.nent);
+    for (int64_t e = 0; e < pa.nent; ++e) order[e] = int(e);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return pa.node[x] < pa.node[y]; });
+    std::vector<int> nodemap(m->nnodes, -1), uoff(1, 0);
+    for (int64_t k = 0; k < pa.nent; ++k) {
+      const int I = pa.node[order[k]];
+      if (k == 0 || pa.node[order[k - 1]] != I) {
+        if (k > 0) uoff.push_back(int(k));
+        nodemap[I] = int(uoff.size()) - 1;
+      }
+    }
+    if (pa.nent > 0) uoff.push_back(int(pa.nent));
+    pa.nunion = int(uoff.size()) - 1;
+    std::vector<float> bdf(12 * size_t(pa.nent));
+    for (size_t i = 0; i < 6 * size_t(pa.nent); ++i) {
+      const float h = float(pa.beta[i]);
+      bdf[2 * i] = h;
+      bdf[2 * i + 1] = float(pa.beta[i] - double(h));
+    }
+    RCF_TRY(upload(ctx, &pa.d_nodemap, nodemap.data(), nodemap.size()));
+    RCF_TRY(upload(ctx, &pa.d_uoff, uoff.data(), uoff.size()));
+    RCF_TRY(upload(ctx, &pa.d_uent, order.data(), order.size()));
+    RCF_TRY(upload(ctx, &pa.d_betadf, bdf.data(), bdf.size()));
+  }
   op->proj = pa;
   return RCF_OK;
 }

@@ -214,9 +214,11 @@ int rchfsi_step(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int k, const Rea
   return apply_full<Real>(ctx, op, RCF_FORM_H_DINV, a);
 }
 
+// df: the residual in double-float arithmetic, written straight to its FP32 rounding
+// (FP32 recurrence, q >= 2); otherwise in FP64 and rounded by a separate pass.
 template <typename Real>
 int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
-                 int nvec, const double* lam_h, double* Y, int64_t ldy) {
+                 int nvec, const double* lam_h, double* Y, int64_t ldy, bool df = false) {
   const rcf_mesh* m = op->mesh;
   const int64_t rows = 2 * m->nnodes;
   const int64_t ld = rows;   // internal buffers: ld = 2M
@@ -234,11 +236,14 @@ int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const do
   RCF_TRY(workspace(ctx, WS_COEF, sizeof(double) * tab.size(), reinterpret_cast<void**>(&tab_d)));
   RCF_CUDA(ctx, cudaMemcpyAsync(tab_d, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
 
-  double* R64 = nullptr;
-  RCF_TRY(workspace(ctx, WS_R64, sizeof(double) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R64)));
-  RCF_TRY(residual_impl(ctx, op, X, ldx, nvec, tab_d, R64, ld));
   const double s = ch.sigma[1] / ch.e;
   const double* lamq_d = tab_d + size_t(q) * nvec;
+  df = df && sizeof(Real) == sizeof(float) && q >= 2;
+  double* R64 = nullptr;
+  if (!df) {
+    RCF_TRY(workspace(ctx, WS_R64, sizeof(double) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R64)));
+    RCF_TRY(residual_impl(ctx, op, X, ldx, nvec, tab_d, R64, ld));
+  }
   if (q == 1) {
     RCF_TRY(launch_recover<double>(ctx, m, R64, ld, s, X, ldx, lamq_d, nvec, Y, ldy));
   } else {
@@ -248,7 +253,8 @@ int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const do
     } else {
       float* R32 = nullptr;
       RCF_TRY(workspace(ctx, WS_R32, sizeof(float) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R32)));
-      RCF_TRY(launch_to_c64(ctx, rows, R64, ld, nvec, R32, ld));
+      if (df) RCF_TRY(launch_residual_df(ctx, op, X, ldx, nvec, tab_d, R32, nullptr, ld));
+      else RCF_TRY(launch_to_c64(ctx, rows, R64, ld, nvec, R32, ld));
       R = reinterpret_cast<const Real*>(R32);
     }
     Real *ZA = nullptr, *ZB = nullptr;
@@ -421,6 +427,30 @@ extern "C" int rcf_residual(rcf_ctx* ctx, const rcf_op* op, const double* X, int
   return RCF_OK;
 }
 
+extern "C" int rcf_residual_df(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
+                               const double* ritz, float* Rh, float* Rl, int64_t ldr) {
+  if (!ctx || !op) return RCF_EINVAL;
+  RCF_TRY(check_block(ctx, op, X, ldx, nvec, 8, "X"));
+  if (nvec == 0) return RCF_OK;
+  if (!ritz) return fail(ctx, RCF_EINVAL, "ritz is NULL");
+  RCF_TRY(check_block(ctx, op, Rh, ldr, nvec, 4, "Rh"));
+  if (Rl) {
+    RCF_TRY(check_block(ctx, op, Rl, ldr, nvec, 4, "Rl"));
+    if (overlaps(Rh, ldr, Rl, ldr, nvec, 8)) return fail(ctx, RCF_EINVAL, "Rl overlaps Rh");
+  }
+  if (overlaps(X, ldx, Rh, ldr, nvec, 16) || (Rl && overlaps(X, ldx, Rl, ldr, nvec, 16)))
+    return fail(ctx, RCF_EINVAL, "R overlaps X");
+  std::vector<double> neg(nvec);
+  for (int v = 0; v < nvec; ++v) neg[v] = -ritz[v];
+  double* neg_d = nullptr;
+  RCF_TRY(workspace(ctx, WS_COEF, sizeof(double) * nvec, reinterpret_cast<void**>(&neg_d)));
+  RCF_CUDA(ctx, cudaMemcpyAsync(neg_d, neg.data(), sizeof(double) * nvec, cudaMemcpyHostToDevice, ctx->stream));
+  RCF_TRY(launch_residual_df(ctx, op, X, ldx, nvec, neg_d, Rh, Rl, ldr));
+  // neg is a host stack buffer read by an async copy
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RCF_OK;
+}
+
 extern "C" int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
                           const double* ritz, int degree, const double bounds[3], int mode, int prec,
                           int block, double* Y, int64_t ldy) {
@@ -429,7 +459,10 @@ extern "C" int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64
   RCF_TRY(check_block(ctx, op, Y, ldy, nvec, 8, "Y"));
   if (overlaps(X, ldx, Y, ldy, nvec, 16)) return fail(ctx, RCF_EINVAL, "Y overlaps X");
   if (mode != RCF_CHFSI && mode != RCF_RCHFSI) return fail(ctx, RCF_EINVAL, "unknown mode %d", mode);
-  if (prec != RCF_FP64 && prec != RCF_FP32) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  if (prec != RCF_FP64 && prec != RCF_FP32 && prec != RCF_FP32_DF)
+    return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  if (prec == RCF_FP32_DF && mode != RCF_RCHFSI)
+    return fail(ctx, RCF_EINVAL, "RCF_FP32_DF applies to R-ChFSI only");
   if (mode == RCF_RCHFSI && !ritz && nvec > 0) return fail(ctx, RCF_EINVAL, "ritz is NULL");
   Cheb ch;
   RCF_TRY(cheb_scalars(ctx, bounds, degree, &ch));
@@ -441,7 +474,7 @@ extern "C" int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64
     double* Yb = Y + 2 * int64_t(b0) * ldy;
     if (mode == RCF_RCHFSI) {
       if (prec == RCF_FP64) RCF_TRY((rchfsi_block<double>(ctx, op, ch, degree, Xb, ldx, n, ritz + b0, Yb, ldy)));
-      else RCF_TRY((rchfsi_block<float>(ctx, op, ch, degree, Xb, ldx, n, ritz + b0, Yb, ldy)));
+      else RCF_TRY((rchfsi_block<float>(ctx, op, ch, degree, Xb, ldx, n, ritz + b0, Yb, ldy, prec == RCF_FP32_DF)));
     } else {
       if (prec == RCF_FP64) RCF_TRY(chfsi_block64(ctx, op, ch, degree, Xb, ldx, n, Yb, ldy));
       else RCF_TRY(chfsi_block32(ctx, op, ch, degree, Xb, ldx, n, Yb, ldy));

@@ -5,6 +5,7 @@
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <string>
@@ -77,6 +78,12 @@ struct ProjAtoms {
   double* d_delta64 = nullptr;   // [natoms][144] complex
   float* d_delta32 = nullptr;
   int64_t nent = 0;
+  // union of the supports, for the double-float residual: entries grouped by node
+  int nunion = 0;
+  int* d_nodemap = nullptr;      // [nnodes] union index or -1
+  int* d_uoff = nullptr;         // [nunion + 1]
+  int* d_uent = nullptr;         // [nent] entry ids, grouped by node
+  float* d_betadf = nullptr;     // [nent][6][2] beta (hi, lo)
 };
 
 struct rcf_op {
@@ -84,6 +91,7 @@ struct rcf_op {
   const rcf_mesh* mesh = nullptr;
   double* d_pot64 = nullptr;   // [nnodes][4] (pv, pbx, pby, pbz) / M_I
   float* d_pot32 = nullptr;
+  float* d_potdf = nullptr;    // [nnodes][8] (pv+bz, pv-bz, bx, by) / M_I: hi[4], lo[4]
   ProjAtoms proj;
 };
 
@@ -118,7 +126,7 @@ int workspace(rcf_ctx* ctx, int slot, size_t bytes, void** out);
 enum WsSlot {
   WS_R64 = 0, WS_R32, WS_ZA, WS_ZB, WS_COEF, WS_NLC, WS_NLC2, WS_LANCZOS, WS_RR_W, WS_RR_S,
   WS_RR_T, WS_RR_INFO, WS_RR_WORK, WS_GRAD, WS_CKPT, WS_ADJ_A, WS_ADJ_B, WS_ADJ_C, WS_ADJ_U,
-  WS_NORM, WS_COUNT
+  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_COUNT
 };
 
 // ---------------------------------------------------------------------------
@@ -156,6 +164,17 @@ int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs
 int launch_step_tma(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<float>& a, bool* used);
 // RCF_ETIMEOUT (and clear the word) if a kernel recorded a timed-out wait; synchronises
 int check_device_error(rcf_ctx* ctx);
+
+// ---------------------------------------------------------------------------
+// double-float residual (residual_df.cu)
+// ---------------------------------------------------------------------------
+// Rh = RN32(R), Rl = R - Rh (if not null), R = H X - M X diag(lambda) evaluated in
+// double-float arithmetic (local part, spin-orbit projectors included); neglam_d =
+// -lambda (device, FP64).  X c128 [nvec][ldx], Rh/Rl c64 [nvec][ldr].
+int launch_residual_df(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
+                       const double* neglam_d, float* Rh, float* Rl, int64_t ldr);
+// hi[i], lo[i] = double-float split of x[i] (integer operations only)
+int launch_split_f64(rcf_ctx* ctx, int64_t n, const double* x, float* hi, float* lo);
 
 // ---------------------------------------------------------------------------
 // nonlocal projectors (nonlocal.cu)

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librchfsi.so")
 
 RCF_OK, RCF_EINVAL, RCF_ENOMEM, RCF_ECUDA, RCF_ENOTSPD, RCF_ETIMEOUT, RCF_ENOTSUP = range(7)
-RCF_FP64, RCF_FP32 = 0, 1
+RCF_FP64, RCF_FP32, RCF_FP32_DF = 0, 1, 2
 RCF_CHFSI, RCF_RCHFSI = 0, 1
 RCF_FORM_H, RCF_FORM_DINV_H, RCF_FORM_H_DINV = 0, 1, 2
 RCF_STEP_CPASYNC, RCF_STEP_TMA = 0, 1
@@ -29,7 +29,7 @@ EXPORTS = [
     "rcf_potential_set", "rcf_projectors_set", "rcf_projectors_couplings", "rcf_projector_support",
     "rcf_apply", "rcf_lanczos_bounds", "rcf_residual", "rcf_filter", "rcf_rayleigh_ritz",
     "rcf_grad_bilinear", "rcf_adjoint_filter", "rcf_cheb_step", "rcf_launch_count",
-    "rcf_apply_noalloc", "rcf_set_step_kernel",
+    "rcf_apply_noalloc", "rcf_set_step_kernel", "rcf_residual_df",
 ]
 
 _lib = None
@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
         "rcf_launch_count": (i64, [vp]),
         "rcf_apply_noalloc": (i32, [vp, vp, i32, vp, i64, i32, vp, i64, i32]),
         "rcf_set_step_kernel": (i32, [vp, i32]),
+        "rcf_residual_df": (i32, [vp, vp, vp, i64, i32, vp, vp, vp, i64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -257,6 +258,21 @@ def rcf_residual(ctx, op, X, ritz, R=None, colnorm=None):
     pr, ldr = (None, 0) if R is None else _dev(R, torch.complex128, "R")
     pc = None if colnorm is None else ctypes.c_void_p(colnorm.data_ptr())
     _check(ctx, lib().rcf_residual(ctx, op, px, ldx, X.shape[0], _np_ptr(rz), pr, ldr, pc))
+
+
+def rcf_residual_df(ctx, op, X, ritz, Rh, Rl=None):
+    """Double-float residual: Rh (complex64) = FP32 rounding of H X - M X diag(ritz), Rl the
+    remainder (complex64, optional; same leading dimension as Rh)."""
+    import torch
+    px, ldx = _dev(X, torch.complex128, "X")
+    rz = np.ascontiguousarray(ritz, dtype=np.float64)
+    ph, ldr = _dev(Rh, torch.complex64, "Rh")
+    pl = None
+    if Rl is not None:
+        pl, ldl = _dev(Rl, torch.complex64, "Rl")
+        if ldl != ldr:
+            raise ValueError("Rh and Rl must share the leading dimension")
+    _check(ctx, lib().rcf_residual_df(ctx, op, px, ldx, X.shape[0], _np_ptr(rz), ph, pl, ldr))
 
 
 def rcf_filter(ctx, op, X, ritz, degree: int, bounds, mode: int, prec: int, block: int, Y):

@@ -80,18 +80,21 @@ def test_rchfsi_fp32_error_scales_with_residual(cfg1):
     bounds = (float(lam_c.min()), float(lam_c.max()), cfg1.hi)
     noise = workloads.complex_normal(77, Xc.shape)
     nw = 28   # the wanted columns; the buffer columns above keep an O(1e-3) residual
-    errs32, errs_ch = [], []
+    errs32, errs_df, errs_ch = [], [], []
     for delta in (1e-3, 1e-6):
         X = Xc + delta * noise / np.linalg.norm(noise) * np.linalg.norm(Xc)
         ref = rchfsi_filter(H, X, lam_c, *bounds, 10)
         y32 = _gpu_filter(cfg1, X, lam_c, bounds, 10, R.RCF_RCHFSI, R.RCF_FP32)
+        ydf = _gpu_filter(cfg1, X, lam_c, bounds, 10, R.RCF_RCHFSI, R.RCF_FP32_DF)
         c32 = _gpu_filter(cfg1, X, lam_c, bounds, 10, R.RCF_CHFSI, R.RCF_FP32)
         # the filters act column by column, so the wanted columns can be checked alone
         errs32.append(rel(y32[:, :nw], ref[:, :nw]))
+        errs_df.append(rel(ydf[:, :nw], ref[:, :nw]))
         errs_ch.append(rel(c32[:, :nw], ref[:, :nw]))
-    assert errs32[0] < 1e-6
-    assert errs32[1] < errs32[0] * 1e-2          # residual-proportional
-    assert errs32[1] < 1e-9
+    for errs in (errs32, errs_df):
+        assert errs[0] < 1e-6
+        assert errs[1] < errs[0] * 1e-2          # residual-proportional
+        assert errs[1] < 1e-9
     assert errs_ch[1] > 1e2 * errs32[1]          # plain FP32 ChFSI keeps its eps_32 floor
 
 
@@ -141,7 +144,8 @@ def test_eigensolver_loop_reaches_oracle_eigenvalues(cfg1):
     H, nw = cfg1.H, 28
     X0 = workloads.complex_normal(cfg1.w.seed + 100, (H.N, cfg1.w.nvec))
     _, ref, _ = rchfsi_eigensolver(H, X0, q=10, lmax=cfg1.hi, tol=1e-10, max_cycles=120, nwanted=nw)
-    for mode, prec in ((R.RCF_CHFSI, R.RCF_FP64), (R.RCF_RCHFSI, R.RCF_FP64), (R.RCF_RCHFSI, R.RCF_FP32)):
+    for mode, prec in ((R.RCF_CHFSI, R.RCF_FP64), (R.RCF_RCHFSI, R.RCF_FP64), (R.RCF_RCHFSI, R.RCF_FP32),
+                       (R.RCF_RCHFSI, R.RCF_FP32_DF)):
         lam, hist = _gpu_loop(cfg1, X0, 10, cfg1.hi, 1e-9, 150, mode, prec, nw)
         assert hist[-1] < 1e-9, (mode, prec, hist[-5:])
         assert np.max(np.abs(lam[:nw] - ref[:nw])) < 1e-7, (mode, prec)
@@ -176,6 +180,9 @@ def test_invalid_arguments_are_rejected(cfg1):
         R.rcf_filter(cfg1.g.ctx, cfg1.g.op, Xd, cfg1.lam, 0, cfg1.bounds, 1, 0, 0, Yd)   # degree 0
     # zero vectors is a no-op
     R.rcf_filter(cfg1.g.ctx, cfg1.g.op, Xd[:0], cfg1.lam[:0], 5, cfg1.bounds, 1, 0, 0, Yd[:0])
+    with pytest.raises(R.RcfError) as e:
+        R.rcf_filter(cfg1.g.ctx, cfg1.g.op, Xd, cfg1.lam, 5, cfg1.bounds, R.RCF_CHFSI, R.RCF_FP32_DF, 0, Yd)
+    assert e.value.status == R.RCF_EINVAL                                               # no residual in ChFSI
     with pytest.raises(R.RcfError) as e:
         R.rcf_set_step_kernel(cfg1.g.ctx, 7)                                             # unknown kernel
     assert e.value.status == R.RCF_EINVAL

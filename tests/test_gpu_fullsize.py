@@ -123,3 +123,47 @@ def test_filter_mixed_full_block_columns(full):
     dz = ref - Xc * Lq[None, :]                  # D^{-1} Z_q: the part computed in FP32
     err = Y[COLS].cpu().numpy().T - ref
     assert np.linalg.norm(err) < 1e-5 * np.linalg.norm(dz)
+
+
+def test_residual_df_sampled_rows_all_columns(full):
+    """Double-float residual on all 256 columns at the benchmark size: 48 sampled rows per
+    column against the oracle's rows of H X - M X Lambda, within 2^-40 of the magnitudes of
+    the terms (the bound derived in test_gpu_residual_df)."""
+    import torch
+    from paper_2605_30128_gb300 import rchfsi as R
+    H, g, X = full["H"], full["g"], full["X"]
+    lam = full["ritz"]
+    rng = np.random.default_rng(4)
+    nodes = list(rng.integers(0, H.nnodes, 40))
+    for pr in H.projectors[:4]:
+        nodes.append(int(pr["support"][len(pr["support"]) // 2]))
+    nodes += [0, H.nnodes - 1, 99, 100 * 100 * 99]
+    rows = np.array([[2 * I, 2 * I + 1] for I in nodes]).ravel()
+    Xh = X.cpu().numpy().T
+    ref = H.apply_rows(Xh, nodes) - H.Mdiag[rows, None] * Xh[rows] * lam[None, :]
+    S = H.apply_rows(Xh, nodes, magnitudes=True) + H.Mdiag[rows, None] * np.abs(Xh[rows]) * np.abs(lam)[None, :]
+    Rh = torch.empty(X.shape, dtype=torch.complex64, device="cuda")
+    Rl = torch.empty_like(Rh)
+    R.rcf_residual_df(g.ctx, g.op, X, lam, Rh, Rl)
+    idx = torch.from_numpy(rows).cuda()
+    got = Rh[:, idx].cpu().numpy().T.astype(np.complex128) + Rl[:, idx].cpu().numpy().T.astype(np.complex128)
+    for part in (np.real, np.imag):
+        assert np.all(np.abs(part(got) - part(ref)) <= 2.0 ** -40 * S)
+
+
+def test_filter_mixed_df_full_block_columns(full):
+    """FP32 R-ChFSI with the double-float residual on the full block: same bound as the
+    FP32 filter with the FP64 residual."""
+    import torch
+    from oracle import rchfsi_filter, ritz_filter_values
+    from paper_2605_30128_gb300 import rchfsi as R
+    w, H, g, X = full["w"], full["H"], full["g"], full["X"]
+    Y = torch.empty_like(X)
+    R.rcf_filter(g.ctx, g.op, X, full["ritz"], w.degree, full["bounds"], R.RCF_RCHFSI, R.RCF_FP32_DF, w.block, Y)
+    Xc = X[COLS].cpu().numpy().T
+    lam = full["ritz"][COLS]
+    ref = rchfsi_filter(H, Xc, lam, *full["bounds"], w.degree)
+    Lq = ritz_filter_values(lam, *full["bounds"], w.degree)[w.degree]
+    dz = ref - Xc * Lq[None, :]
+    err = Y[COLS].cpu().numpy().T - ref
+    assert np.linalg.norm(err) < 1e-5 * np.linalg.norm(dz)

@@ -27,6 +27,26 @@ def test_hermitian_and_mass_positive():
     assert np.max(np.abs(off)) > 1e-6
 
 
+def test_apply_rows_matches_assembled_operator():
+    """Row-wise product from the element matrices (used at sizes where assembly is too big)
+    equals the assembled sparse H plus projectors; the term-magnitude variant bounds |H| |X|
+    (assembled entrywise moduli) from above, and |H X| from above in turn."""
+    import workloads
+    H, *_ = build_oracle(small_workload(ncell=(2, 3, 2), side=(6.0, 7.0, 5.0), p=3))
+    X = workloads.complex_normal(3, (H.N, 4))
+    nodes = [0, 5, H.nnodes // 2, H.nnodes - 1] + [int(pr["support"][0]) for pr in H.projectors]
+    rows = np.array([[2 * I, 2 * I + 1] for I in nodes]).ravel()
+    full = H.apply(X)
+    np.testing.assert_allclose(H.apply_rows(X, nodes), full[rows], rtol=0, atol=1e-13 * np.abs(full).max())
+    S = H.apply_rows(X, nodes, magnitudes=True)
+    A = np.abs(H.dense())[rows] @ np.abs(X)
+    assert np.all(S >= A * (1 - 1e-13))
+    assert np.all(A >= np.abs(full[rows]) * (1 - 1e-13))
+    # moduli only: the bound does not depend on the phases of X
+    ph = np.exp(1j * np.random.default_rng(0).uniform(0, 2 * np.pi, X.shape))
+    np.testing.assert_allclose(H.apply_rows(X * ph, nodes, magnitudes=True), S, rtol=1e-14)
+
+
 def test_kramers_degeneracy_without_B():
     H, *_ = build_oracle(small_workload(), with_b=False)
     lam = sla.eigh(H.dense(), np.diag(H.Mdiag), eigvals_only=True)
