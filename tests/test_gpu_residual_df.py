@@ -63,7 +63,9 @@ def _run(pair, X, lam, ld_pad=0):
     return rh, rl
 
 
-def _check(H, X, lam, rh, rl):
+def _check(H, X, lam, rh, rl, exact_frac=0.999):
+    """Rh + Rl within 2^-40 A of R; Rh within one FP32 ulp plus that error of fl32(R), and
+    (where R is not much smaller than A) equal to fl32(R) for a fraction exact_frac."""
     ref = H.apply(X) - H.Mdiag[:, None] * X * lam[None, :]
     A = magnitude_bound(H, X, lam)
     got = rh.astype(np.complex128) + rl.astype(np.complex128)
@@ -72,8 +74,9 @@ def _check(H, X, lam, rh, rl):
         assert np.all(err <= 2.0 ** -40 * A + 1e-300), float(np.max(err / A))
         f32 = part(ref).astype(np.float32)
         h = part(rh)
-        assert np.all(np.abs(h.astype(np.float64) - f32) <= np.spacing(np.abs(f32)))
-        assert np.mean(h == f32) >= 0.999
+        assert np.all(np.abs(h.astype(np.float64) - f32) <= np.spacing(np.abs(f32)) + 2.0 ** -40 * A)
+        if exact_frac is not None:
+            assert np.mean(h == f32) >= exact_frac
 
 
 def test_residual_df_matches_oracle(pair):
@@ -95,7 +98,8 @@ def test_residual_df_near_eigenvectors(pair):
     X = V[:, :4] + 1e-7 * workloads.complex_normal(8, (H.N, 4))
     lam = w[:4]
     rh, rl = _run(pair, X, lam, ld_pad=6)
-    _check(H, X, lam, rh, rl)
+    # R is ~1e-7 of the terms here, so its FP32 ulp can be below the double-float error
+    _check(H, X, lam, rh, rl, exact_frac=None)
 
 
 def test_residual_df_strided_and_empty(pair):
