@@ -30,13 +30,17 @@ int check_block(rcf_ctx* ctx, const rcf_op* op, const void* p, int64_t ld, int n
   return RCF_OK;
 }
 
-bool overlaps(const void* a, int64_t lda, const void* b, int64_t ldb, int nvec, size_t cplx) {
+// do two multivectors (nvec columns of ld complex elements of size_a / size_b bytes) overlap
+bool overlaps(const void* a, int64_t lda, size_t size_a, const void* b, int64_t ldb, size_t size_b, int nvec) {
   if (!a || !b || nvec == 0) return false;
   const char* a0 = static_cast<const char*>(a);
   const char* b0 = static_cast<const char*>(b);
-  const char* a1 = a0 + size_t(lda) * nvec * cplx;
-  const char* b1 = b0 + size_t(ldb) * nvec * cplx;
+  const char* a1 = a0 + size_t(lda) * nvec * size_a;
+  const char* b1 = b0 + size_t(ldb) * nvec * size_b;
   return a0 < b1 && b0 < a1;
+}
+bool overlaps(const void* a, int64_t lda, const void* b, int64_t ldb, int nvec, size_t cplx) {
+  return overlaps(a, lda, cplx, b, ldb, cplx, nvec);
 }
 
 // Chebyshev scalars (Eq. ChFSIrecurrence): c, e, sigma[1..q]
@@ -438,7 +442,7 @@ extern "C" int rcf_residual_df(rcf_ctx* ctx, const rcf_op* op, const double* X, 
     RCF_TRY(check_block(ctx, op, Rl, ldr, nvec, 4, "Rl"));
     if (overlaps(Rh, ldr, Rl, ldr, nvec, 8)) return fail(ctx, RCF_EINVAL, "Rl overlaps Rh");
   }
-  if (overlaps(X, ldx, Rh, ldr, nvec, 16) || (Rl && overlaps(X, ldx, Rl, ldr, nvec, 16)))
+  if (overlaps(X, ldx, 16, Rh, ldr, 8, nvec) || (Rl && overlaps(X, ldx, 16, Rl, ldr, 8, nvec)))
     return fail(ctx, RCF_EINVAL, "R overlaps X");
   std::vector<double> neg(nvec);
   for (int v = 0; v < nvec; ++v) neg[v] = -ritz[v];

@@ -198,7 +198,7 @@ constexpr size_t df_smem_bytes() {
   return size_t(NST) * HALO * sizeof(D4)            // raw FP64 planes
          + size_t(NST) * 4 * NT * sizeof(float4)    // tile potential and nonlocal terms (hi, lo)
          + size_t(2) * 2 * HALO * sizeof(float4)    // converted planes (hi, lo), double buffered
-         + size_t(2) * (P + 1) * (P + 1) * sizeof(Coef);
+         + size_t(3) * (P + 1) * (P + 1) * sizeof(Coef);
 }
 
 template <int P, int TX, int TY, int NST>
@@ -214,10 +214,11 @@ __global__ void __launch_bounds__(TX* TY, DFTile<P>::MINB)
   float4* TT = reinterpret_cast<float4*>(RAW + NST * HALO);        // [NST][4][NT]: pot h, pot l, nl h, nl l
   float4* SH = TT + NST * 4 * NT;                                  // [2][HALO]
   float4* SL = SH + 2 * HALO;                                      // [2][HALO]
-  Coef* CT = reinterpret_cast<Coef*>(SL + 2 * HALO);               // [2][P+1][P+1]
+  Coef* CT = reinterpret_cast<Coef*>(SL + 2 * HALO);               // [3][P+1][P+1]: x, y, z
+  const Coef* CZ = CT + 2 * (P + 1) * (P + 1);
 
   const int tid = threadIdx.x;
-  for (int i = tid; i < 2 * (P + 1) * (P + 1); i += NT) CT[i] = (&tb.c[0][0][0])[i];
+  for (int i = tid; i < 3 * (P + 1) * (P + 1); i += NT) CT[i] = (&tb.c[0][0][0])[i];
 
   const int lx = tid % TX, ly = tid / TX;
   const int ntx = (Gx + TX - 1) / TX;
@@ -331,96 +332,100 @@ __global__ void __launch_bounds__(TX* TY, DFTile<P>::MINB)
     }
   };
 
-  for (int ez = 0; ez < nz; ++ez) {
+  // planes in order; c = local index of the plane in its z element.  The loop is not
+  // unrolled (the body is large); the branches on c are uniform across the block.
+  int c = 0, ez = 0;
+  for (int z = 0; z < Gz; ++z) {
+    const int s = z % NST;
+    cp_async_wait<NST - 2>();
+    // convert this thread's copies of plane z into the (hi, lo) plane z & 1
+    {
+      const D4* st = RAW + s * HALO;
+      float4* dh = SH + (z & 1) * HALO;
+      float4* dl = SL + (z & 1) * HALO;
 #pragma unroll
-    for (int c = 0; c < P; ++c) {
-      const int z = ez * P + c;
-      const int s = z % NST;
-      cp_async_wait<NST - 2>();
-      // convert this thread's copies of plane z into the (hi, lo) plane z & 1
-      {
-        const D4* st = RAW + s * HALO;
-        float4* dh = SH + (z & 1) * HALO;
-        float4* dl = SL + (z & 1) * HALO;
-#pragma unroll
-        for (int k = 0; k < KMAX; ++k)
-          if (hs[k] >= 0) {
-            float4 h, l;
-            split4(st[hs[k]], h, l);
-            dh[hs[k]] = h;
-            dl[hs[k]] = l;
-          }
-      }
-      __syncthreads();
-      if (zload < Gz) {
-        issue_plane(zload, zload % NST);
-        load_nm(zload + 1);
-      } else {
-        cp_async_commit();
-      }
-      ++zload;
+      for (int k = 0; k < KMAX; ++k)
+        if (hs[k] >= 0) {
+          float4 h, l;
+          split4(st[hs[k]], h, l);
+          dh[hs[k]] = h;
+          dl[hs[k]] = l;
+        }
+    }
+    __syncthreads();
+    if (zload < Gz) {
+      issue_plane(zload, zload % NST);
+      load_nm(zload + 1);
+    } else {
+      cp_async_commit();
+    }
+    ++zload;
 
-      const float4* Ph = SH + (z & 1) * HALO;
-      const float4* Pl = SL + (z & 1) * HALO;
-      auto node = [&](int k) { return df4_of(Ph[k], Pl[k]); };
-      const DF4 u = node((ly + P) * W + lx + P);
-      DF4 self = zero4df();
-      {
-        const int row = (ly + P) * W;
-        const int cb = lx - ax + P;
+    const float4* Ph = SH + (z & 1) * HALO;
+    const float4* Pl = SL + (z & 1) * HALO;
+    auto node = [&](int k) { return df4_of(Ph[k], Pl[k]); };
+    const DF4 u = node((ly + P) * W + lx + P);
+    DF4 self = zero4df();
+    {
+      const int row = (ly + P) * W;
+      const int cb = lx - ax + P;
 #pragma unroll
-        for (int q = 0; q <= P; ++q) tap4(self, cxr[q], node(row + cb + q));
-        if (ax == 0) {
+      for (int q = 0; q <= P; ++q) tap4(self, cxr[q], node(row + cb + q));
+      if (ax == 0) {
 #pragma unroll
-          for (int q = 0; q <= P; ++q) tap4(self, cxv[q], node(row + cb - P + q));
-        }
-        const int rb = ly - by + P;
-#pragma unroll
-        for (int q = 0; q <= P; ++q) tap4(self, cyr[q], node((rb + q) * W + lx + P));
-        if (by == 0) {
-#pragma unroll
-          for (int q = 0; q <= P; ++q) tap4(self, cyv[q], node((rb - P + q) * W + lx + P));
-        }
+        for (int q = 0; q <= P; ++q) tap4(self, cxv[q], node(row + cb - P + q));
       }
-      // spinor potential and -lambda: [[pv+bz-l, bx-i by], [bx+i by, pv-bz-l]] u
-      {
-        const float4* t = TT + s * 4 * NT;
-        const float4 ph = t[0 * NT + tid], pl = t[1 * NT + tid];
-        const float2 dA = dfadd1(make_float2(ph.x, pl.x), make_float2(nlam.h.x, nlam.l.x));
-        const float2 dD = dfadd1(make_float2(ph.y, pl.y), make_float2(nlam.h.x, nlam.l.x));
-        const Coef cA = coef1(dA.x, dA.y), cD = coef1(dD.x, dD.y), cBx = coef1(ph.z, pl.z);
-        const Coef cBy = coef2(make_float2(ph.w, -ph.w), make_float2(pl.w, -pl.w));    // ( by, -by)
-        const Coef cnBy = coef2(make_float2(-ph.w, ph.w), make_float2(-pl.w, pl.w));   // (-by,  by)
-        tap(self.a, cA, u.a);
-        tap(self.a, cBx, u.b);
-        tap(self.a, cBy, swap2(u.b));
-        tap(self.b, cBx, u.a);
-        tap(self.b, cnBy, swap2(u.a));
-        tap(self.b, cD, u.b);
-        if (supp & (1u << (z & 31))) dfadd4(self, df4_of(t[2 * NT + tid], t[3 * NT + tid]));
-      }
-      if (c == 0) {
-        tap4(accn, tb.c[2][P][P], u);
-        if (ez > 0) {
+      const int rb = ly - by + P;
 #pragma unroll
-          for (int cc = 0; cc < P; ++cc) tap4(acc[cc], tb.c[2][cc][P], u);
-          emit(ez - 1);
-        }
-        acc[0] = accn;
-        dfadd4(acc[0], self);
+      for (int q = 0; q <= P; ++q) tap4(self, cyr[q], node((rb + q) * W + lx + P));
+      if (by == 0) {
 #pragma unroll
-        for (int cc = 1; cc < P; ++cc) acc[cc] = zero4df();
-#pragma unroll
-        for (int cc = 0; cc < P; ++cc) tap4(acc[cc], tb.c[2][cc][0], u);
-        accn = zero4df();
-        tap4(accn, tb.c[2][P][0], u);
-      } else {
-        dfadd4(acc[c], self);
-#pragma unroll
-        for (int cc = 0; cc < P; ++cc) tap4(acc[cc], tb.c[2][cc][c], u);
-        tap4(accn, tb.c[2][P][c], u);
+        for (int q = 0; q <= P; ++q) tap4(self, cyv[q], node((rb - P + q) * W + lx + P));
       }
     }
+    // spinor potential and -lambda: [[pv+bz-l, bx-i by], [bx+i by, pv-bz-l]] u
+    {
+      const float4* t = TT + s * 4 * NT;
+      const float4 ph = t[0 * NT + tid], pl = t[1 * NT + tid];
+      const float2 dA = dfadd1(make_float2(ph.x, pl.x), make_float2(nlam.h.x, nlam.l.x));
+      const float2 dD = dfadd1(make_float2(ph.y, pl.y), make_float2(nlam.h.x, nlam.l.x));
+      const Coef cA = coef1(dA.x, dA.y), cD = coef1(dD.x, dD.y), cBx = coef1(ph.z, pl.z);
+      const Coef cBy = coef2(make_float2(ph.w, -ph.w), make_float2(pl.w, -pl.w));    // ( by, -by)
+      const Coef cnBy = coef2(make_float2(-ph.w, ph.w), make_float2(-pl.w, pl.w));   // (-by,  by)
+      tap(self.a, cA, u.a);
+      tap(self.a, cBx, u.b);
+      tap(self.a, cBy, swap2(u.b));
+      tap(self.b, cBx, u.a);
+      tap(self.b, cnBy, swap2(u.a));
+      tap(self.b, cD, u.b);
+      if (supp & (1u << (z & 31))) dfadd4(self, df4_of(t[2 * NT + tid], t[3 * NT + tid]));
+    }
+    if (c == 0) {
+      // the vertex plane closes element ez-1 (its local node P) and opens element ez
+      tap4(accn, tb.c[2][P][P], u);
+      if (ez > 0) {
+#pragma unroll
+        for (int cc = 0; cc < P; ++cc) tap4(acc[cc], tb.c[2][cc][P], u);
+        emit(ez - 1);
+      }
+      acc[0] = accn;
+      dfadd4(acc[0], self);
+#pragma unroll
+      for (int cc = 1; cc < P; ++cc) acc[cc] = zero4df();
+#pragma unroll
+      for (int cc = 0; cc < P; ++cc) tap4(acc[cc], tb.c[2][cc][0], u);
+      accn = zero4df();
+      tap4(accn, tb.c[2][P][0], u);
+    } else {
+      const Coef* cz = CZ + c;   // column c of the z operator: cz[cc * (P + 1)] = C_z[cc][c]
+#pragma unroll
+      for (int cc = 1; cc < P; ++cc)
+        if (cc == c) dfadd4(acc[cc], self);
+#pragma unroll
+      for (int cc = 0; cc < P; ++cc) tap4(acc[cc], cz[cc * (P + 1)], u);
+      tap4(accn, cz[P * (P + 1)], u);
+    }
+    if (++c == P) { c = 0; ++ez; }
   }
   // the last element closes on plane Gz = 0 (periodic)
   if (active) {

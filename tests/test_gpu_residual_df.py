@@ -115,3 +115,26 @@ def test_residual_df_strided_and_empty(pair):
     ref = H.apply(X) - H.Mdiag[:, None] * X * lam[None, :]
     assert np.max(np.abs(Rh.cpu().numpy().T - ref)) <= 2 ** -23 * np.max(np.abs(ref))
     R.rcf_residual_df(pair.g.ctx, pair.g.op, big[:0, :H.N], lam[:0], Rh[:0])  # no vectors: no-op
+
+
+def test_residual_df_adjacent_buffers_accepted_overlap_rejected(pair):
+    """X (complex128) directly after Rh (complex64) in one allocation is legal; X overlapping
+    Rh is rejected."""
+    import torch
+    from paper_2605_30128_gb300 import rchfsi as R
+    H = pair.H
+    nv = 2
+    X = workloads.complex_normal(10, (H.N, nv))
+    lam = np.array([0.3, -0.2])
+    nb_r, nb_x = nv * H.N * 8, nv * H.N * 16
+    buf = torch.zeros(nb_r + nb_x, dtype=torch.uint8, device="cuda")
+    Rh = buf[:nb_r].view(torch.complex64).view(nv, H.N)
+    Xd = buf[nb_r:].view(torch.complex128).view(nv, H.N)
+    Xd.copy_(to_dev(X))
+    R.rcf_residual_df(pair.g.ctx, pair.g.op, Xd, lam, Rh)
+    ref = H.apply(X) - H.Mdiag[:, None] * X * lam[None, :]
+    assert np.max(np.abs(Rh.cpu().numpy().T - ref)) <= 2 ** -23 * np.max(np.abs(ref))
+    Rbad = buf[nb_r - 8 * H.N:2 * nb_r - 8 * H.N].view(torch.complex64).view(nv, H.N)   # ends inside X
+    with pytest.raises(R.RcfError) as e:
+        R.rcf_residual_df(pair.g.ctx, pair.g.op, Xd, lam, Rbad)
+    assert e.value.status == R.RCF_EINVAL
