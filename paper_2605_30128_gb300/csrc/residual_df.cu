@@ -20,7 +20,10 @@
 // Kernel organisation follows the FP32 step kernel (z-marching TX x TY column tiles,
 // a cp.async ring of halo planes, incremental z accumulation), with raw FP64 planes
 // in the ring, converted once per plane into a double-buffered (hi, lo) plane, and the
-// tile's potential and nonlocal terms staged through the same ring.
+// tile's potential and nonlocal terms staged through the same ring.  Threads are
+// grouped by node class (tile_position) so that the element-vertex branches are
+// uniform within warps: this kernel is ALU bound, and a divergent vertex branch costs
+// every lane of the warp.
 #include "internal.h"
 #include "stencil_common.cuh"
 
@@ -220,7 +223,8 @@ __global__ void __launch_bounds__(TX* TY, DFTile<P>::MINB)
   const int tid = threadIdx.x;
   for (int i = tid; i < 3 * (P + 1) * (P + 1); i += NT) CT[i] = (&tb.c[0][0][0])[i];
 
-  const int lx = tid % TX, ly = tid / TX;
+  int lx, ly;
+  tile_position<P, TX, TY>(tid, lx, ly);
   const int ntx = (Gx + TX - 1) / TX;
   const int x0 = (blockIdx.x % ntx) * TX;
   const int y0 = (blockIdx.x / ntx) * TY;

@@ -88,6 +88,40 @@ __device__ __forceinline__ void add_potential(R4<Real>& acc, const R4<Real>& pot
   acc.v[3] += bx * ui + by * ur + (pv - bz) * di;
 }
 
+// Thread -> node of a TX x TY tile (TX, TY multiples of P), grouped by node class so that
+// the element-vertex branches are uniform within most warps: first the nodes interior in
+// both x and y, then x-vertex nodes, then y-vertex nodes, then nodes that are vertices in
+// both (row-major within each class).  A vertex node's 1D row spans two elements (2P + 2
+// taps instead of P + 1); in row-major order every warp holds vertex lanes and all its
+// lanes pay for them.
+template <int P, int TX, int TY>
+__device__ __forceinline__ void tile_position(int tid, int& lx, int& ly) {
+  if (P == 1) {
+    lx = tid % TX;
+    ly = tid / TX;
+    return;
+  }
+  constexpr int nxv = TX / P, nxi = TX - nxv, nyv = TY / P, nyi = TY - nyv;
+  constexpr int n0 = nxi * nyi, n1 = n0 + nxv * nyi, n2 = n1 + nxi * nyv;
+  auto interior = [](int i) { return (i / (P - 1)) * P + 1 + i % (P - 1); };
+  if (tid < n0) {
+    lx = interior(tid % nxi);
+    ly = interior(tid / nxi);
+  } else if (tid < n1) {
+    const int i = tid - n0;
+    lx = (i % nxv) * P;
+    ly = interior(i / nxv);
+  } else if (tid < n2) {
+    const int i = tid - n1;
+    lx = interior(i % nxi);
+    ly = (i / nxi) * P;
+  } else {
+    const int i = tid - n2;
+    lx = (i % nxv) * P;
+    ly = (i / nxv) * P;
+  }
+}
+
 template <typename Real, int P>
 struct KTab {
   Real c[3][P + 1][P + 1];
