@@ -4,9 +4,11 @@
 Workload (default): periodic 20^3 cells, p = 5 (100^3 nodes, 2,000,000 complex
 spinor DoF), 32 atoms with spin-orbit projectors, 1024 spinor vectors filtered
 in band blocks of 256 at degree 40.  The recurrence runs in complex64 (FP32
-stencil products); X, the residual and the recovery are complex128.  A step is
-one rcf_filter call over all 1024 vectors: X -> Y_q including the FP64
-residual and the recovery.  Units per step = 2M * nvec * degree.
+stencil products); X and the recovery are complex128; the residual is evaluated
+in double-float arithmetic (RCF_FP32_DF: FP64-class accuracy on the FP32 pipes).
+A step is one rcf_filter call over all 1024 vectors: X -> Y_q including the
+residual and the recovery.  Units per step = 2M * nvec * degree.  The same
+filter with the residual in native FP64 (RCF_FP32) is reported beside it.
 
 Also reported on the same JSON line: the dominant kernel (the FP32 recurrence
 step) against the measured HBM copy bandwidth, the FP64 ChFSI filter on the
@@ -266,8 +268,8 @@ def run_ours(args):
     ritz = np.linspace(lo, lT, nvec, endpoint=False)
     bounds = (lo - 1e-3 * abs(lo), lT, hi)
 
-    def step():
-        R.rcf_filter(ctx, op, X, ritz, q, bounds, R.RCF_RCHFSI, R.RCF_FP32, w.block, Y)
+    def step(prec=R.RCF_FP32_DF):
+        R.rcf_filter(ctx, op, X, ritz, q, bounds, R.RCF_RCHFSI, prec, w.block, Y)
 
     for _ in range(args.warmup):
         step()
@@ -290,17 +292,31 @@ def run_ours(args):
     units = float(N) * nvec * q
     value = units * ws / (ms * 1e-3)
 
+    # the same filter with the residual in native FP64
+    step(R.RCF_FP32)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ev0.record(stream)
+    for _ in range(max(1, args.steps - 1)):
+        step(R.RCF_FP32)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = max_over_ranks(ws, ev0.elapsed_time(ev1) / max(1, args.steps - 1))
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": describe(w),
-                   "precision": "recurrence and stencil products complex64 (FP32); X, residual, recovery complex128",
+                   "precision": "recurrence and stencil products complex64 (FP32); X and recovery complex128; "
+                                "residual in double-float arithmetic (pairs of FP32, FP64-class), rounded to complex64",
                    "l2": "inputs larger than L2 (X and Y are %.1f GB each)" % (X.numel() * 16 / 1e9),
                    "parallelism": "band partitioning, one GPU per column group (no filter communication)"
                                   if ws > 1 else "single GPU"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
+        "variants": {"fp64_residual": {"value": units * ws / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                                       "precision": "as above with the residual in native FP64 (RCF_FP32)"}},
     }
 
     # ---- dominant kernel: one FP32 recurrence step on a block, timed alone ----
@@ -330,6 +346,23 @@ def run_ours(args):
     step_ms = ev0.elapsed_time(ev1) / nrep
     R.rcf_op_destroy(op1)
     del Zk, Zm, Rr
+    # the residual of one block: double-float (the headline path) and native FP64
+    Rh = torch.empty((blk, N), dtype=torch.complex64, device=dev)
+    R.rcf_residual_df(ctx, op, X[:blk], ritz[:blk], Rh)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    R.rcf_residual_df(ctx, op, X[:blk], ritz[:blk], Rh)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    res_df_ms = ev0.elapsed_time(ev1)
+    del Rh
+    R64 = torch.empty((blk, N), dtype=torch.complex128, device=dev)
+    ev0.record(stream)
+    R.rcf_residual(ctx, op, X[:blk], ritz[:blk], R64)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    res64_ms = ev0.elapsed_time(ev1)
+    del R64
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
     peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -341,6 +374,8 @@ def run_ours(args):
                         "kernel_ms": k_ms, "algorithmic_bytes": BYTES_PER_UNIT * N * blk,
                         "peak_source": "measured" if peaks else "fallback",
                         "step_with_projectors_ms": step_ms}
+    line["residual"] = {"double_float_ms": res_df_ms, "fp64_ms": res64_ms, "vectors": blk,
+                        "note": "R = H X - M X Lambda of one block, spin-orbit terms included"}
 
     if not args.no_extras:
         # ---- FP64 ChFSI on one block, same mesh and degree ----
@@ -356,7 +391,7 @@ def run_ours(args):
         f64_val = float(N) * blk * q / (f64_ms * 1e-3)
         # the mixed filter on the same single block, for a like-for-like ratio
         ev0.record(stream)
-        R.rcf_filter(ctx, op, Xb, ritz[:blk], q, bounds, R.RCF_RCHFSI, R.RCF_FP32, blk, Yb)
+        R.rcf_filter(ctx, op, Xb, ritz[:blk], q, bounds, R.RCF_RCHFSI, R.RCF_FP32_DF, blk, Yb)
         ev1.record(stream)
         torch.cuda.synchronize()
         mix_ms = ev0.elapsed_time(ev1)
@@ -380,7 +415,7 @@ def run_ours(args):
         ev0.record(stream)
         for _ in range(max(1, args.steps)):
             X[:ne].copy_(Xh, non_blocking=True)
-            R.rcf_filter(ctx, op, X[:ne], ritz[:ne], q, bounds, R.RCF_RCHFSI, R.RCF_FP32, w.block, Y[:ne])
+            R.rcf_filter(ctx, op, X[:ne], ritz[:ne], q, bounds, R.RCF_RCHFSI, R.RCF_FP32_DF, w.block, Y[:ne])
             Yh.copy_(Y[:ne], non_blocking=True)
         ev1.record(stream)
         torch.cuda.synchronize()

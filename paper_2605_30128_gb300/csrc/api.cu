@@ -148,7 +148,8 @@ int upload(rcf_ctx* ctx, T** dst, const T* src, size_t n) {
 void free_proj(ProjAtoms* pa) {
   cudaFree(pa->d_offsets); cudaFree(pa->d_node); cudaFree(pa->d_atom);
   cudaFree(pa->d_beta64); cudaFree(pa->d_beta32); cudaFree(pa->d_delta64); cudaFree(pa->d_delta32);
-  cudaFree(pa->d_nodemap); cudaFree(pa->d_uoff); cudaFree(pa->d_uent); cudaFree(pa->d_betadf);
+  cudaFree(pa->d_nodemap); cudaFree(pa->d_unode); cudaFree(pa->d_uoff); cudaFree(pa->d_uent);
+  cudaFree(pa->d_betadf);
   *pa = ProjAtoms();
 }
 
@@ -502,12 +503,13 @@ extern "C" int rcf_projectors_set(rcf_op* op, int natoms, const double* pos, con
     std::vector<int> order(pa.nent);
     for (int64_t e = 0; e < pa.nent; ++e) order[e] = int(e);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return pa.node[x] < pa.node[y]; });
-    std::vector<int> nodemap(m->nnodes, -1), uoff(1, 0);
+    std::vector<int> nodemap(m->nnodes, -1), uoff(1, 0), unode;
     for (int64_t k = 0; k < pa.nent; ++k) {
       const int I = pa.node[order[k]];
       if (k == 0 || pa.node[order[k - 1]] != I) {
         if (k > 0) uoff.push_back(int(k));
         nodemap[I] = int(uoff.size()) - 1;
+        unode.push_back(I);
       }
     }
     if (pa.nent > 0) uoff.push_back(int(pa.nent));
@@ -519,6 +521,7 @@ extern "C" int rcf_projectors_set(rcf_op* op, int natoms, const double* pos, con
       bdf[2 * i + 1] = float(pa.beta[i] - double(h));
     }
     RCF_TRY(upload(ctx, &pa.d_nodemap, nodemap.data(), nodemap.size()));
+    RCF_TRY(upload(ctx, &pa.d_unode, unode.data(), unode.size()));
     RCF_TRY(upload(ctx, &pa.d_uoff, uoff.data(), uoff.size()));
     RCF_TRY(upload(ctx, &pa.d_uent, order.data(), order.size()));
     RCF_TRY(upload(ctx, &pa.d_betadf, bdf.data(), bdf.size()));

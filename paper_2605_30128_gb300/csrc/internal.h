@@ -81,6 +81,7 @@ struct ProjAtoms {
   // union of the supports, for the double-float residual: entries grouped by node
   int nunion = 0;
   int* d_nodemap = nullptr;      // [nnodes] union index or -1
+  int* d_unode = nullptr;        // [nunion] node of each union index
   int* d_uoff = nullptr;         // [nunion + 1]
   int* d_uent = nullptr;         // [nent] entry ids, grouped by node
   float* d_betadf = nullptr;     // [nent][6][2] beta (hi, lo)

@@ -2,8 +2,10 @@
 //   H_nloc = sum_a P_a Delta_a P_a^H,  P_a column (j, i, sigma) = M_I beta_{j,i}(x_I) in row 2I+sigma.
 // Applied in three launches: projection C = P^H (.) (a block reduction per
 // atom and vector: register accumulators, warp shuffles, shared memory),
-// the 12x12 coupling C' = A Delta C, and the add-back (atomics, since the
-// supports of neighbouring atoms may overlap).
+// the 12x12 coupling C' = A Delta C, and the add-back, gathered per node of
+// the union of the supports (each node sums the terms of every atom whose
+// support holds it, then updates its output once: no atomics where the
+// supports of neighbouring atoms overlap).
 #include "internal.h"
 
 namespace rcf {
@@ -91,31 +93,37 @@ __global__ void nl_delta_kernel(const Real* __restrict__ delta, const Real* __re
   }
 }
 
-// grid (ceil(nent/128), nvec); thread per support entry
+// grid (ceil(nunion/128), nvec); thread per node of the support union: the node's
+// output gains w sum_e beta_e C2[atom_e] over its entries e, in one read-modify-write
 template <typename Real>
-__global__ void nl_addback_kernel(const int* __restrict__ node, const int* __restrict__ atom,
+__global__ void nl_addback_kernel(const int* __restrict__ unode, const int* __restrict__ uoff,
+                                  const int* __restrict__ uent, const int* __restrict__ atom,
                                   const Real* __restrict__ beta, const double* __restrict__ mass,
-                                  int64_t nent, const Real* __restrict__ C2, int nvec, int add_mass,
+                                  int nunion, const Real* __restrict__ C2, int nvec, int add_mass,
                                   Real* out, int64_t ld) {
-  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = blockIdx.y;
-  if (e >= nent) return;
-  const int I = node[e], a = atom[e];
-  const Real w = add_mass ? Real(mass[I]) : Real(1);
+  if (u >= nunion) return;
+  const int I = unode[u];
   Real s[4] = {0, 0, 0, 0};
+  for (int k = uoff[u]; k < uoff[u + 1]; ++k) {
+    const int e = uent[k];
+    const int a = atom[e];
 #pragma unroll
-  for (int f6 = 0; f6 < 6; ++f6) {
-    const Real b = beta[6 * e + f6] * w;
+    for (int f6 = 0; f6 < 6; ++f6) {
+      const Real b = beta[6 * int64_t(e) + f6];
 #pragma unroll
-    for (int sg = 0; sg < 2; ++sg) {
-      const int64_t k = 2 * ((int64_t(a) * 12 + 2 * f6 + sg) * nvec + v);
-      s[2 * sg + 0] += b * C2[k];
-      s[2 * sg + 1] += b * C2[k + 1];
+      for (int sg = 0; sg < 2; ++sg) {
+        const int64_t kk = 2 * ((int64_t(a) * 12 + 2 * f6 + sg) * nvec + v);
+        s[2 * sg + 0] += b * C2[kk];
+        s[2 * sg + 1] += b * C2[kk + 1];
+      }
     }
   }
+  const Real w = add_mass ? Real(mass[I]) : Real(1);
   Real* y = out + 2 * int64_t(v) * ld + 4 * int64_t(I);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) atomicAdd(y + i, s[i]);
+  for (int i = 0; i < 4; ++i) y[i] += w * s[i];
 }
 
 // gh[a][j] += wgt Re sum_v CW[a,(j,.,.)]^H P_j CU[a,(j,.,.)]; thread per (a, v), atomics
@@ -186,11 +194,11 @@ template <typename Real>
 int launch_nl_addback(rcf_ctx* ctx, const rcf_op* op, const Real* C2, int nvec, int add_mass,
                       Real* out, int64_t ld) {
   const ProjAtoms& pa = op->proj;
-  if (pa.natoms == 0 || nvec == 0 || pa.nent == 0) return RCF_OK;
-  dim3 grid(unsigned((pa.nent + 127) / 128), nvec);
-  nl_addback_kernel<Real><<<grid, 128, 0, ctx->stream>>>(pa.d_node, pa.d_atom, beta_of<Real>(op),
-                                                          op->mesh->d_mass, pa.nent, C2, nvec,
-                                                          add_mass, out, ld);
+  if (pa.natoms == 0 || nvec == 0 || pa.nunion == 0) return RCF_OK;
+  dim3 grid(unsigned((pa.nunion + 127) / 128), nvec);
+  nl_addback_kernel<Real><<<grid, 128, 0, ctx->stream>>>(pa.d_unode, pa.d_uoff, pa.d_uent, pa.d_atom,
+                                                          beta_of<Real>(op), op->mesh->d_mass, pa.nunion,
+                                                          C2, nvec, add_mass, out, ld);
   RCF_CHECK_LAUNCH(ctx);
   return RCF_OK;
 }

@@ -32,11 +32,13 @@ namespace {
 
 // shared-memory elements of one ring stage: the plane tile with its one-element x/y halo
 template <int P, int TX, int TY>
-__host__ __device__ constexpr int stage_elems() {
-  return (TX + P + 1) * (TY + P + 1);
+__host__ __device__ constexpr int stage_elems(bool own) {
+  return (TX + P + 1) * (TY + P + 1) + (own ? 2 * TX * TY : 0);
 }
 
-template <typename Real, int P, int TX, int TY, int NST>
+// OWN: the tile's own Z_{k-1} and R planes travel through the cp.async ring with the
+// halo (NST-1 planes ahead) instead of register prefetch one plane ahead.
+template <typename Real, int P, int TX, int TY, int NST, bool OWN>
 __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
     step_kernel(const StepArgs<Real> a, const KTab<Real, P> tab, const int Gx, const int Gy,
                 const int Gz) {
@@ -46,8 +48,8 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
   constexpr int NT = TX * TY;
   constexpr int HALO = H * W;
   constexpr int KMAX = (HALO + NT - 1) / NT;
-  constexpr int STAGE = stage_elems<P, TX, TY>();
-  static_assert(STAGE == HALO, "one stage holds the plane tile with its halo");
+  constexpr int STAGE = stage_elems<P, TX, TY>(OWN);
+  static_assert(STAGE == HALO + (OWN ? 2 * NT : 0), "one stage: the plane tile with its halo (+ own planes)");
   using V4 = R4<Real>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   V4* S = reinterpret_cast<V4*>(smem_raw);                        // [NST][STAGE]
@@ -99,6 +101,11 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
       if (hs[k] >= 0) cp_async_r4(st + hs[k], src + hg[k]);
+    if (OWN && active) {
+      const int64_t I = col + int64_t(z) * plane;
+      if (prev) cp_async_r4(st + HALO + tid, prev + I);
+      if (rv) cp_async_r4(st + HALO + NT + tid, rv + I);
+    }
     cp_async_commit();
   };
   // this thread's potential, previous iterate and residual of one plane, one plane ahead.
@@ -108,8 +115,10 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
     if (!active) return;
     const int64_t I = col + int64_t(z) * plane;
     npot = ldg4(pot + I);
-    if (prev) nprev = ldg4(prev + I);
-    if (rv) nrv = ldg4(rv + I);
+    if (!OWN) {
+      if (prev) nprev = ldg4(prev + I);
+      if (rv) nrv = ldg4(rv + I);
+    }
   };
 
   // element -1 (planes Gz-P .. Gz-1) contributes row P of its 1D matrix to the vertex plane 0
@@ -169,7 +178,9 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
       ++zload;
       const V4* Pl = S + (z % NST) * STAGE;
       const V4 u = Pl[(ly + P) * W + lx + P];
-      const V4 cpot = npot, cprev = nprev, crv = nrv;
+      const V4 cpot = npot;
+      const V4 cprev = OWN ? (prev ? Pl[HALO + tid] : zero4<Real>()) : nprev;
+      const V4 crv = OWN ? (rv ? Pl[HALO + NT + tid] : zero4<Real>()) : nrv;
       if (z + 1 < Gz) fetch_own(z + 1);
       // x and y terms (tables carry the factor A)
       V4 self = zero4<Real>();
@@ -236,16 +247,17 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
 template <typename Real, int P>
 int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a) {
   constexpr int TX = TileOf<Real, P>::TX, TY = TileOf<Real, P>::TY;
-  constexpr int NST = 4;   // three planes in flight per block
+  constexpr int NST = TileOf<Real, P>::NST;
+  constexpr bool OWN = TileOf<Real, P>::OWN;
   // the kernel multiplies the operator by A through its tables
   KTab<Real, P> kt;
   for (int d = 0; d < 3; ++d)
     for (int i = 0; i <= P; ++i)
       for (int j = 0; j <= P; ++j) kt.c[d][i][j] = Real(double(a.A) * t.c[d][i][j]);
   const int ntx = (m->G[0] + TX - 1) / TX, nty = (m->G[1] + TY - 1) / TY;
-  const size_t stage = size_t(stage_elems<P, TX, TY>());
+  const size_t stage = size_t(stage_elems<P, TX, TY>(OWN));
   const size_t smem = size_t(NST) * stage * sizeof(R4<Real>) + 2 * (P + 1) * (P + 1) * sizeof(Real);
-  auto kern = step_kernel<Real, P, TX, TY, NST>;
+  auto kern = step_kernel<Real, P, TX, TY, NST, OWN>;
   if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   dim3 grid(ntx * nty, a.nvec);
   kern<<<grid, TX * TY, smem, ctx->stream>>>(a, kt, m->G[0], m->G[1], m->G[2]);

@@ -96,29 +96,29 @@ __device__ __forceinline__ void add_potential(R4<Real>& acc, const R4<Real>& pot
 // lanes pay for them.
 template <int P, int TX, int TY>
 __device__ __forceinline__ void tile_position(int tid, int& lx, int& ly) {
-  if (P == 1) {
+  if constexpr (P == 1) {   // every node is a vertex
     lx = tid % TX;
     ly = tid / TX;
-    return;
-  }
-  constexpr int nxv = TX / P, nxi = TX - nxv, nyv = TY / P, nyi = TY - nyv;
-  constexpr int n0 = nxi * nyi, n1 = n0 + nxv * nyi, n2 = n1 + nxi * nyv;
-  auto interior = [](int i) { return (i / (P - 1)) * P + 1 + i % (P - 1); };
-  if (tid < n0) {
-    lx = interior(tid % nxi);
-    ly = interior(tid / nxi);
-  } else if (tid < n1) {
-    const int i = tid - n0;
-    lx = (i % nxv) * P;
-    ly = interior(i / nxv);
-  } else if (tid < n2) {
-    const int i = tid - n1;
-    lx = interior(i % nxi);
-    ly = (i / nxi) * P;
   } else {
-    const int i = tid - n2;
-    lx = (i % nxv) * P;
-    ly = (i / nxv) * P;
+    constexpr int nxv = TX / P, nxi = TX - nxv, nyv = TY / P, nyi = TY - nyv;
+    constexpr int n0 = nxi * nyi, n1 = n0 + nxv * nyi, n2 = n1 + nxi * nyv;
+    auto interior = [](int i) { return (i / (P - 1)) * P + 1 + i % (P - 1); };
+    if (tid < n0) {
+      lx = interior(tid % nxi);
+      ly = interior(tid / nxi);
+    } else if (tid < n1) {
+      const int i = tid - n0;
+      lx = (i % nxv) * P;
+      ly = interior(i / nxv);
+    } else if (tid < n2) {
+      const int i = tid - n1;
+      lx = interior(i % nxi);
+      ly = (i / nxi) * P;
+    } else {
+      const int i = tid - n2;
+      lx = (i % nxv) * P;
+      ly = (i / nxv) * P;
+    }
   }
 }
 
@@ -139,6 +139,8 @@ struct TileOf {
   static constexpr int TX = f32 ? P * ((20 + P - 1) / P) : P * ((8 + P - 1) / P);
   static constexpr int TY = f32 ? P * (((small ? 10 : 16) + P - 1) / P) : P * ((8 + P - 1) / P);
   static constexpr int MINB = (f32 && small) ? 2 : 1;
+  static constexpr int NST = 4;       // cp.async ring depth of the step kernel (NST-1 planes in flight)
+  static constexpr bool OWN = false;  // own Z_{k-1}, R planes through the ring (else registers)
 };
 
 }  // namespace
