@@ -105,6 +105,10 @@ __global__ void nl_addback_kernel(const int* __restrict__ unode, const int* __re
   const int v = blockIdx.y;
   if (u >= nunion) return;
   const int I = unode[u];
+  Real* y = out + 2 * int64_t(v) * ld + 4 * int64_t(I);
+  Real y0[4];   // loaded first: the read overlaps the sums below
+#pragma unroll
+  for (int i = 0; i < 4; ++i) y0[i] = y[i];
   Real s[4] = {0, 0, 0, 0};
   for (int k = uoff[u]; k < uoff[u + 1]; ++k) {
     const int e = uent[k];
@@ -121,9 +125,8 @@ __global__ void nl_addback_kernel(const int* __restrict__ unode, const int* __re
     }
   }
   const Real w = add_mass ? Real(mass[I]) : Real(1);
-  Real* y = out + 2 * int64_t(v) * ld + 4 * int64_t(I);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) y[i] += w * s[i];
+  for (int i = 0; i < 4; ++i) y[i] = y0[i] + w * s[i];
 }
 
 // gh[a][j] += wgt Re sum_v CW[a,(j,.,.)]^H P_j CU[a,(j,.,.)]; thread per (a, v), atomics
