@@ -220,6 +220,17 @@ int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int
 int rcf_rayleigh_ritz(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int nvec,
                       double* X_out, int64_t ldx, double* ritz_out);
 
+/* The two halves of rcf_rayleigh_ritz, callable (and timed) separately.
+ * rcf_cholqr2: Y (c128, in/out) <- Y made M-orthonormal by Cholesky-QR applied
+ * twice, with one shifted pass in front if the first Gram factorisation breaks
+ * down (then RCF_ENOTSPD only if the shifted pass fails too); synchronises.
+ * rcf_rayleigh_ritz_orth: for an M-orthonormal Y (not modified), A = Y^H H Y
+ * (FP64), its eigenpairs, X_out = Y Q and ascending ritz_out as in
+ * rcf_rayleigh_ritz; X_out must not overlap Y; synchronises. */
+int rcf_cholqr2(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int nvec);
+int rcf_rayleigh_ritz_orth(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nvec,
+                           double* X_out, int64_t ldx, double* ritz_out);
+
 /* ---- derivatives (no counterpart in the paper) ------------------------- */
 
 /* Accumulate (+=) the derivatives of weight * Re tr(W^H H U) with respect to

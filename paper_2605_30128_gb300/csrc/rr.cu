@@ -114,22 +114,21 @@ int cholqr_pass(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int n, b
 
 using namespace rcf;
 
-extern "C" int rcf_rayleigh_ritz(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int nvec,
-                                 double* X_out, int64_t ldx, double* ritz_out) {
-  if (!ctx || !op) return RCF_EINVAL;
+namespace rcf {
+namespace {
+
+int check_y(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nvec) {
   const int64_t N = 2 * op->mesh->nnodes;
   if (nvec <= 0) return fail(ctx, RCF_EINVAL, "nvec must be >= 1");
-  if (!Y || !X_out || !ritz_out) return fail(ctx, RCF_EINVAL, "NULL argument");
-  if (ldy < N || ldx < N || (ldy & 1) || (ldx & 1)) return fail(ctx, RCF_EINVAL, "bad leading dimension");
-  if (ldy > INT32_MAX || ldx > INT32_MAX || N > INT32_MAX)
+  if (!Y) return fail(ctx, RCF_EINVAL, "NULL argument");
+  if (ldy < N || (ldy & 1)) return fail(ctx, RCF_EINVAL, "bad leading dimension");
+  if (ldy > INT32_MAX || N > INT32_MAX)
     return fail(ctx, RCF_ENOTSUP, "leading dimensions above 2^31 are not supported by the BLAS path");
-  {
-    const char* y0 = reinterpret_cast<const char*>(Y);
-    const char* x0 = reinterpret_cast<const char*>(X_out);
-    if (y0 < x0 + size_t(ldx) * nvec * 16 && x0 < y0 + size_t(ldy) * nvec * 16)
-      return fail(ctx, RCF_EINVAL, "X_out overlaps Y");
-  }
-  // Cholesky-QR2, with one shifted pass in front if the first factorisation breaks down
+  return RCF_OK;
+}
+
+// Cholesky-QR2, with one shifted pass in front if the first factorisation breaks down
+int cholqr2(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int nvec) {
   int s = cholqr_pass(ctx, op, Y, ldy, nvec, false);
   if (s == RCF_ENOTSPD) {
     RCF_TRY(cholqr_pass(ctx, op, Y, ldy, nvec, true));
@@ -137,7 +136,13 @@ extern "C" int rcf_rayleigh_ritz(rcf_ctx* ctx, const rcf_op* op, double* Y, int6
   } else if (s != RCF_OK) {
     return s;
   }
-  RCF_TRY(cholqr_pass(ctx, op, Y, ldy, nvec, false));
+  return cholqr_pass(ctx, op, Y, ldy, nvec, false);
+}
+
+// projection, eigensolve and rotation for an M-orthonormal Y
+int rr_orth(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nvec, double* X_out,
+            int64_t ldx, double* ritz_out) {
+  const int64_t N = 2 * op->mesh->nnodes;
   // A = Y^H H Y, column chunks of H Y
   cuDoubleComplex* A = nullptr;
   RCF_TRY(workspace(ctx, WS_RR_S, sizeof(cuDoubleComplex) * size_t(nvec) * nvec, reinterpret_cast<void**>(&A)));
@@ -173,4 +178,44 @@ extern "C" int rcf_rayleigh_ritz(rcf_ctx* ctx, const rcf_op* op, double* Y, int6
   RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (hinfo != 0) return fail(ctx, RCF_ECUDA, "ZHEEVD did not converge (info %d)", hinfo);
   return RCF_OK;
+}
+
+int check_xy(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nvec, const double* X_out,
+             int64_t ldx, const double* ritz_out) {
+  RCF_TRY(check_y(ctx, op, Y, ldy, nvec));
+  const int64_t N = 2 * op->mesh->nnodes;
+  if (!X_out || !ritz_out) return fail(ctx, RCF_EINVAL, "NULL argument");
+  if (ldx < N || (ldx & 1)) return fail(ctx, RCF_EINVAL, "bad leading dimension");
+  if (ldx > INT32_MAX) return fail(ctx, RCF_ENOTSUP, "leading dimensions above 2^31 are not supported by the BLAS path");
+  const char* y0 = reinterpret_cast<const char*>(Y);
+  const char* x0 = reinterpret_cast<const char*>(X_out);
+  if (y0 < x0 + size_t(ldx) * nvec * 16 && x0 < y0 + size_t(ldy) * nvec * 16)
+    return fail(ctx, RCF_EINVAL, "X_out overlaps Y");
+  return RCF_OK;
+}
+
+}  // namespace
+}  // namespace rcf
+
+extern "C" int rcf_cholqr2(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int nvec) {
+  if (!ctx || !op) return RCF_EINVAL;
+  RCF_TRY(check_y(ctx, op, Y, ldy, nvec));
+  RCF_TRY(cholqr2(ctx, op, Y, ldy, nvec));
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RCF_OK;
+}
+
+extern "C" int rcf_rayleigh_ritz_orth(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nvec,
+                                      double* X_out, int64_t ldx, double* ritz_out) {
+  if (!ctx || !op) return RCF_EINVAL;
+  RCF_TRY(check_xy(ctx, op, Y, ldy, nvec, X_out, ldx, ritz_out));
+  return rr_orth(ctx, op, Y, ldy, nvec, X_out, ldx, ritz_out);
+}
+
+extern "C" int rcf_rayleigh_ritz(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int nvec,
+                                 double* X_out, int64_t ldx, double* ritz_out) {
+  if (!ctx || !op) return RCF_EINVAL;
+  RCF_TRY(check_xy(ctx, op, Y, ldy, nvec, X_out, ldx, ritz_out));
+  RCF_TRY(cholqr2(ctx, op, Y, ldy, nvec));
+  return rr_orth(ctx, op, Y, ldy, nvec, X_out, ldx, ritz_out);
 }

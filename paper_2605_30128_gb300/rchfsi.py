@@ -29,7 +29,8 @@ EXPORTS = [
     "rcf_potential_set", "rcf_projectors_set", "rcf_projectors_couplings", "rcf_projector_support",
     "rcf_apply", "rcf_lanczos_bounds", "rcf_residual", "rcf_filter", "rcf_rayleigh_ritz",
     "rcf_grad_bilinear", "rcf_adjoint_filter", "rcf_cheb_step", "rcf_launch_count",
-    "rcf_apply_noalloc", "rcf_set_step_kernel", "rcf_residual_df",
+    "rcf_apply_noalloc", "rcf_set_step_kernel", "rcf_residual_df", "rcf_cholqr2",
+    "rcf_rayleigh_ritz_orth",
 ]
 
 _lib = None
@@ -81,6 +82,8 @@ def lib() -> ctypes.CDLL:
         "rcf_apply_noalloc": (i32, [vp, vp, i32, vp, i64, i32, vp, i64, i32]),
         "rcf_set_step_kernel": (i32, [vp, i32]),
         "rcf_residual_df": (i32, [vp, vp, vp, i64, i32, vp, vp, vp, i64]),
+        "rcf_cholqr2": (i32, [vp, vp, vp, i64, i32]),
+        "rcf_rayleigh_ritz_orth": (i32, [vp, vp, vp, i64, i32, vp, i64, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -291,6 +294,23 @@ def rcf_rayleigh_ritz(ctx, op, Y, X_out):
     px, ldx = _dev(X_out, torch.complex128, "X_out")
     ritz = np.empty(Y.shape[0], dtype=np.float64)
     _check(ctx, lib().rcf_rayleigh_ritz(ctx, op, py, ldy, Y.shape[0], px, ldx, _np_ptr(ritz)))
+    return ritz
+
+
+def rcf_cholqr2(ctx, op, Y):
+    """Y (complex128, in/out) made M-orthonormal (Cholesky-QR2)."""
+    import torch
+    py, ldy = _dev(Y, torch.complex128, "Y")
+    _check(ctx, lib().rcf_cholqr2(ctx, op, py, ldy, Y.shape[0]))
+
+
+def rcf_rayleigh_ritz_orth(ctx, op, Y, X_out):
+    """Rayleigh-Ritz on an M-orthonormal Y: Ritz vectors into X_out, Ritz values returned."""
+    import torch
+    py, ldy = _dev(Y, torch.complex128, "Y")
+    px, ldx = _dev(X_out, torch.complex128, "X_out")
+    ritz = np.empty(Y.shape[0], dtype=np.float64)
+    _check(ctx, lib().rcf_rayleigh_ritz_orth(ctx, op, py, ldy, Y.shape[0], px, ldx, _np_ptr(ritz)))
     return ritz
 
 

@@ -116,6 +116,30 @@ def test_rayleigh_ritz_matches_oracle(cfg1):
     assert np.max(np.abs(s - 1.0)) < 1e-9
 
 
+def test_cholqr2_and_orthonormal_rr_split(cfg1):
+    """rcf_cholqr2 then rcf_rayleigh_ritz_orth = rcf_rayleigh_ritz: M-orthonormal output, same
+    span as the input, Ritz values of the oracle's Rayleigh-Ritz."""
+    import torch
+    from paper_2605_30128_gb300 import rchfsi as R
+    H = cfg1.H
+    Y = rchfsi_filter(H, cfg1.X, cfg1.lam, *cfg1.bounds, 10)
+    Xo, th = rayleigh_ritz(H, Y)
+    Yd = to_dev(Y)
+    R.rcf_cholqr2(cfg1.g.ctx, cfg1.g.op, Yd)
+    Q = to_host(Yd)
+    G = Q.conj().T @ (H.Mdiag[:, None] * Q)
+    assert np.max(np.abs(G - np.eye(G.shape[0]))) < 1e-11
+    # span preserved: Y = Q (Q^H M Y)
+    C = Q.conj().T @ (H.Mdiag[:, None] * Y)
+    assert rel(Q @ C, Y) < 1e-10
+    Xd = torch.zeros_like(Yd)
+    gth = R.rcf_rayleigh_ritz_orth(cfg1.g.ctx, cfg1.g.op, Yd, Xd)
+    np.testing.assert_allclose(gth, th, rtol=1e-10, atol=1e-11)
+    assert torch.equal(to_dev(Q), Yd)                     # Y not modified by the orthonormal RR
+    with pytest.raises(R.RcfError):
+        R.rcf_rayleigh_ritz_orth(cfg1.g.ctx, cfg1.g.op, Yd, Yd)   # X_out overlaps Y
+
+
 def _gpu_loop(pr, X0, q, lmax, tol, cycles, mode, prec, nwanted):
     import torch
     from paper_2605_30128_gb300 import rchfsi as R
