@@ -86,6 +86,11 @@ def max_over_ranks(ws, x: float) -> float:
     return float(t.item())
 
 
+def workloads_mod():
+    import workloads
+    return workloads
+
+
 def workload_of(args):
     import workloads
     over = {}
@@ -425,6 +430,37 @@ def run_ours(args):
                        "h2d_bytes_per_step": int(Xh.numel() * 16), "d2h_bytes_per_step": int(Yh.numel() * 16),
                        "ms_per_step": e_ms, "sample": sample}
         del Xh, Yh
+
+        # ---- the adjoint filter on the 8^3-cell p = 4 workload (64 vectors, degree 15,
+        #      checkpoints every 5 steps) against its forward filter ----
+        wa = workloads_mod().workload("cfg4")
+        pa_ = GPUProblem(wa, device=local, stream=stream)
+        Xa = torch.randn((wa.nvec, pa_.N), dtype=torch.complex128, device=dev, generator=gen)
+        Xa /= torch.linalg.norm(Xa, dim=1, keepdim=True)
+        va = torch.randn((pa_.N,), dtype=torch.complex128, device=dev, generator=gen)
+        la, ha = R.rcf_lanczos_bounds(pa_.ctx, pa_.op, wa.lanczos, va)
+        ra = np.linspace(la, la + 0.05 * (ha - la), wa.nvec, endpoint=False)
+        ba = (la - 1e-3 * abs(la), la + 0.05 * (ha - la), ha)
+        Ya = torch.empty_like(Xa)
+        Yb = torch.randn_like(Xa)
+        dV = torch.zeros((pa_.ncells, pa_.nloc), dtype=torch.float64, device=dev)
+        dB = torch.zeros((3, pa_.ncells, pa_.nloc), dtype=torch.float64, device=dev)
+        adj = {}
+        for pname, prec in (("fp64", R.RCF_FP64), ("fp32", R.RCF_FP32)):
+            fwd = lambda: R.rcf_filter(pa_.ctx, pa_.op, Xa, ra, wa.degree, ba, R.RCF_RCHFSI, prec, wa.nvec, Ya)
+            bwd = lambda: R.rcf_adjoint_filter(pa_.ctx, pa_.op, Xa, ra, wa.degree, ba, R.RCF_RCHFSI, prec, Yb,
+                                               wa.ckpt, dV, dB, None)
+            fwd(); bwd()
+            torch.cuda.synchronize()
+            ev0.record(stream); fwd(); ev1.record(stream); torch.cuda.synchronize()
+            f_ms = ev0.elapsed_time(ev1)
+            ev0.record(stream); bwd(); ev1.record(stream); torch.cuda.synchronize()
+            b_ms = ev0.elapsed_time(ev1)
+            adj[pname] = {"forward_ms": f_ms, "adjoint_ms": b_ms, "ratio": b_ms / f_ms}
+        line["adjoint"] = dict(adj, workload=describe(wa), note="adjoint w.r.t. V, B at all quadrature "
+                               "points, checkpoints every %d steps" % wa.ckpt)
+        pa_.close()
+        del Xa, Ya, Yb, dV, dB
 
         # ---- CPU oracle on a bounded sample (rank 0, one GPU only) ----
         if ws == 1 and rank == 0:

@@ -38,7 +38,8 @@ __host__ __device__ constexpr int stage_elems(bool own) {
 
 // OWN: the tile's own Z_{k-1} and R planes travel through the cp.async ring with the
 // halo (NST-1 planes ahead) instead of register prefetch one plane ahead.
-template <typename Real, int P, int TX, int TY, int NST, bool OWN>
+// ZB: planes consumed per block barrier (1 or 2); NST - ZB planes are in flight.
+template <typename Real, int P, int TX, int TY, int NST, bool OWN, int ZB>
 __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
     step_kernel(const StepArgs<Real> a, const KTab<Real, P> tab, const int Gx, const int Gy,
                 const int Gz) {
@@ -128,12 +129,14 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
     for (int c = 0; c < P; ++c) fma4(accn, tab.c[2][P][c], ldg4(in + col + int64_t(Gz - P + c) * plane));
   }
 
+  static_assert(ZB == 1 || ZB == 2, "one or two planes per barrier");
+  static_assert(NST >= 2 * ZB + 1, "ring too shallow");
 #pragma unroll
-  for (int s = 0; s < NST - 1; ++s) {
+  for (int s = 0; s < NST - ZB; ++s) {
     if (s < Gz) issue_plane(s, s);
     else cp_async_commit();
   }
-  int zload = NST - 1;
+  int zload = NST - ZB;
   fetch_own(0);
 
   __syncthreads();  // tables visible
@@ -171,11 +174,17 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
 #pragma unroll
     for (int c = 0; c < P; ++c) {
       const int z = ez * P + c;
-      cp_async_wait<NST - 2>();
-      __syncthreads();
-      if (zload < Gz) issue_plane(zload, zload % NST);
-      else cp_async_commit();
-      ++zload;
+      if (ZB == 1 || (z & 1) == 0) {
+        // planes z .. z + ZB - 1 have landed; the stages of the previous ZB planes are free
+        cp_async_wait<NST - 2 * ZB>();
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < ZB; ++j) {
+          if (zload < Gz) issue_plane(zload, zload % NST);
+          else cp_async_commit();
+          ++zload;
+        }
+      }
       const V4* Pl = S + (z % NST) * STAGE;
       const V4 u = Pl[(ly + P) * W + lx + P];
       const V4 cpot = npot;
@@ -249,6 +258,7 @@ int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Re
   constexpr int TX = TileOf<Real, P>::TX, TY = TileOf<Real, P>::TY;
   constexpr int NST = TileOf<Real, P>::NST;
   constexpr bool OWN = TileOf<Real, P>::OWN;
+  constexpr int ZB = TileOf<Real, P>::ZB;
   // the kernel multiplies the operator by A through its tables
   KTab<Real, P> kt;
   for (int d = 0; d < 3; ++d)
@@ -257,7 +267,7 @@ int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Re
   const int ntx = (m->G[0] + TX - 1) / TX, nty = (m->G[1] + TY - 1) / TY;
   const size_t stage = size_t(stage_elems<P, TX, TY>(OWN));
   const size_t smem = size_t(NST) * stage * sizeof(R4<Real>) + 2 * (P + 1) * (P + 1) * sizeof(Real);
-  auto kern = step_kernel<Real, P, TX, TY, NST, OWN>;
+  auto kern = step_kernel<Real, P, TX, TY, NST, OWN, ZB>;
   if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   dim3 grid(ntx * nty, a.nvec);
   kern<<<grid, TX * TY, smem, ctx->stream>>>(a, kt, m->G[0], m->G[1], m->G[2]);

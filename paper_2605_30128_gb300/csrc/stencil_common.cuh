@@ -141,6 +141,7 @@ struct TileOf {
   static constexpr int MINB = (f32 && small) ? 2 : 1;
   static constexpr int NST = 4;       // cp.async ring depth of the step kernel (NST-1 planes in flight)
   static constexpr bool OWN = false;  // own Z_{k-1}, R planes through the ring (else registers)
+  static constexpr int ZB = 1;        // planes per block barrier
 };
 
 }  // namespace

@@ -167,3 +167,39 @@ def test_filter_mixed_df_full_block_columns(full):
     dz = ref - Xc * Lq[None, :]
     err = Y[COLS].cpu().numpy().T - ref
     assert np.linalg.norm(err) < 1e-5 * np.linalg.norm(dz)
+
+
+def test_fp64_chfsi_16cubed_p6_full_block_columns():
+    """The FP64 ChFSI configuration at full size: 16^3 cells, p = 6 (1,769,472 DoF), 16 atoms,
+    512 vectors in one block, degree 30, bounds from 10 Lanczos steps; three columns (first,
+    middle, last) recomputed by the oracle, relative Frobenius error <= 1e-10."""
+    import torch
+    from oracle import Hamiltonian, Mesh, chfsi_filter
+    from paper_2605_30128_gb300 import rchfsi as R
+    from paper_2605_30128_gb300.problem import GPUProblem
+    w = workloads.workload("cfg2")
+    prm = workloads.draw_parameters(w)
+    mesh = Mesh(w.ncell, w.side, w.p)
+    q = mesh.quad_coords().reshape(-1, 3)
+    V = workloads.gaussian_sum_potential(q, prm["centres"], prm["depths"], prm["widths"], prm["L"])
+    B = workloads.smooth_periodic_field(q, prm["kvec"], prm["amps"], prm["phases"], prm["L"], prm["bmax"])
+    V = V.reshape(mesh.ncells, mesh.nloc)
+    B = B.reshape(3, mesh.ncells, mesh.nloc)
+    H = Hamiltonian(mesh, V, B, prm["atoms"], prm["proj_width"], prm["proj_h"])
+    g = GPUProblem(w, params=prm)
+    try:
+        g.set_potential(V, B)
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(7)
+        X = torch.randn((w.nvec, H.N), dtype=torch.complex128, device="cuda", generator=gen)
+        X /= torch.linalg.norm(X, dim=1, keepdim=True)
+        v0 = torch.randn((H.N,), dtype=torch.complex128, device="cuda", generator=gen)
+        lo, hi = R.rcf_lanczos_bounds(g.ctx, g.op, w.lanczos, v0)
+        bounds = (lo - 1e-3 * abs(lo), lo + 0.05 * (hi - lo), hi)
+        Y = torch.empty_like(X)
+        R.rcf_filter(g.ctx, g.op, X, None, w.degree, bounds, R.RCF_CHFSI, R.RCF_FP64, w.block, Y)
+        cols = [0, w.nvec // 2, w.nvec - 1]
+        ref = chfsi_filter(H, X[cols].cpu().numpy().T, *bounds, w.degree)
+        assert rel(Y[cols].cpu().numpy().T, ref) < 1e-10
+    finally:
+        g.close()
