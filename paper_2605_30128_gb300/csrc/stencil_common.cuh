@@ -127,21 +127,28 @@ struct KTab {
   Real c[3][P + 1][P + 1];
 };
 
-// Tile shapes (multiples of P so that tiles start on element vertices) and blocks
-// per SM.  FP32: about 20 x 10 columns, two blocks per SM without spilling (the
-// best of the shapes timed on a GB300 for p = 5: 20x20/1, 20x10/2, 15x15/2,
-// 10x10/4), about 20 x 16 and one block for p >= 6; FP64 (ALU bound): about
-// 8 x 8, one block per SM.
+// Tile shapes (multiples of P so that tiles start on element vertices), blocks per SM
+// and ring depth of the step kernel.
+// FP32 (HBM bound): a tile one element high (TY = P, at least about 5 rows) and about
+// 24 nodes wide, with as many blocks per SM as 128 registers allow.  Timed on a GB300
+// (256-vector step, 2M DoF at p = 5): 20x10 two blocks per SM 4.05 ms, 50x5/2 3.67,
+// 25x10/2 3.71, 50x10/1 3.85, 25x5/4 3.60, 25x5/4 with a 6-deep ring and two planes per
+// barrier 3.57 (kept); with no arithmetic at all the 20x10 form still took 3.65 ms, so
+// the tile shape, through the DRAM access pattern and the number of independent blocks,
+// is what sets the time.  p = 6 (3.46M DoF): 24x18/1 7.28 ms, 24x12/1 8.85, 30x6/2 7.31,
+// 24x6/3 6.62 (kept).
+// FP64 (ALU bound): about 8 x 8, one block per SM.
 template <typename Real, int P>
 struct TileOf {
   static constexpr bool f32 = sizeof(Real) == 4;
-  static constexpr bool small = P <= 5;   // two FP32 blocks per SM fit without spilling
-  static constexpr int TX = f32 ? P * ((20 + P - 1) / P) : P * ((8 + P - 1) / P);
-  static constexpr int TY = f32 ? P * (((small ? 10 : 16) + P - 1) / P) : P * ((8 + P - 1) / P);
-  static constexpr int MINB = (f32 && small) ? 2 : 1;
-  static constexpr int NST = 4;       // cp.async ring depth of the step kernel (NST-1 planes in flight)
-  static constexpr bool OWN = false;  // own Z_{k-1}, R planes through the ring (else registers)
-  static constexpr int ZB = 1;        // planes per block barrier
+  static constexpr int TX = f32 ? P * ((24 + P - 1) / P) : P * ((8 + P - 1) / P);
+  static constexpr int TY_MIN = (120 + TX - 1) / TX;   // FP32: at least ~120 threads per block
+  static constexpr int TY = f32 ? P * ((TY_MIN + P - 1) / P) : P * ((8 + P - 1) / P);
+  static constexpr int WARPS = (TX * TY + 31) / 32;
+  static constexpr int MINB = f32 ? (65536 / (WARPS * 32 * 128) < 1 ? 1 : 65536 / (WARPS * 32 * 128)) : 1;
+  static constexpr int NST = f32 ? 6 : 4;   // cp.async ring depth (NST - ZB planes in flight)
+  static constexpr bool OWN = false;        // own Z_{k-1}, R planes through the ring (else registers)
+  static constexpr int ZB = f32 ? 2 : 1;    // planes per block barrier
 };
 
 }  // namespace

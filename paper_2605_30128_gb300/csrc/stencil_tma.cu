@@ -79,8 +79,14 @@ struct Stage {
   static constexpr uint32_t TX_BYTES = 16u * (TX * TY + P * TY + TY + TX * P + TX);
 };
 
+// blocks per SM for a block of consumer warps plus one producer warp at 128 registers
+template <int TX, int TY>
+constexpr int tma_minb() {
+  return 65536 / (((TX * TY + 31) / 32 + 1) * 32 * 128) < 1 ? 1 : 65536 / (((TX * TY + 31) / 32 + 1) * 32 * 128);
+}
+
 template <int P, int TX, int TY, int NST>
-__global__ void __launch_bounds__((((TX * TY) + 31) / 32 + 1) * 32, TileOf<float, P>::MINB)
+__global__ void __launch_bounds__((((TX * TY) + 31) / 32 + 1) * 32, tma_minb<TX, TY>())
     step_kernel_tma(const StepArgs<float> a, const KTab<float, P> tab, const __grid_constant__ Maps maps,
                     const int Gx, const int Gy, const int Gz, int* err) {
   using V4 = R4<float>;

@@ -1,8 +1,8 @@
 """GPU path (librchfsi through the C ABI) against the FP64 CPU oracle, element by element.
 
 Meshes span several stencil tiles with a ragged tail in x and y (FP32 tiles
-are about 16 nodes, FP64 tiles about 8), single-cell directions, and degrees
-p = 1 .. 6.  Tolerances: FP64 products 1e-12 relative (rounding of ~30-term
+are 24-25 nodes wide and one element high, FP64 tiles about 8 x 8), single-cell
+directions, and degrees p = 1 .. 6.  Tolerances: FP64 products 1e-12 relative (rounding of ~30-term
 sums); FP64 filters 1e-10 relative Frobenius (the target for filtered
 blocks); FP32 products 2e-6 relative (float rounding of the same sums,
 about 30 eps_32 in the worst row).
@@ -16,18 +16,23 @@ from gpu_cases import Pair, rel, to_dev, to_host
 pytestmark = pytest.mark.gpu
 
 MESHES = [
-    ((7, 3, 2), (7.0, 4.5, 3.0), 3),    # Gx = 21: two FP32 tiles, three FP64 tiles, ragged
+    # FP32 tiles are 24-25 nodes wide and one element (at least ~5 rows) high; FP64 tiles ~8x8
+    ((7, 3, 2), (7.0, 4.5, 3.0), 3),    # Gx = 21 < 24: one ragged FP32 tile, three FP64 tiles
+    ((11, 3, 2), (11.0, 4.5, 3.0), 3),  # Gx = 33, Gy = 9: ragged in x and y
     ((4, 4, 4), 8.0, 4),                 # the 4^3 p=4 workload mesh
-    ((5, 3, 2), (10.0, 6.0, 4.0), 5),    # p = 5, Gx = 25 > 20
-    ((4, 3, 2), (8.0, 6.0, 4.0), 6),     # p = 6, Gx = 24 > 18
+    ((5, 3, 2), (10.0, 6.0, 4.0), 5),    # p = 5, Gx = 25: one full tile in x, three in y
+    ((7, 3, 2), (14.0, 6.0, 4.0), 5),    # p = 5, Gx = 35: a full and a ragged tile
+    ((4, 3, 2), (8.0, 6.0, 4.0), 6),     # p = 6, Gx = 24, Gy = 18: 1 x 3 tiles
+    ((5, 3, 2), (10.0, 6.0, 4.0), 6),    # p = 6, Gx = 30: ragged
     ((1, 2, 3), (2.0, 4.0, 6.0), 2),     # one cell along x: a node is its own periodic image
     ((9, 2, 1), (9.0, 2.0, 1.0), 1),     # p = 1
     # meshes that the FP32 tiles divide, run with the TMA step kernel selected: one tile
-    # per plane (its strips wrap onto itself) and several tiles; p = 5 (20 x 10 tiles)
-    # and p = 4 (20 x 12)
-    ((4, 2, 2), (8.0, 4.0, 4.0), 5, "tma"),
-    ((8, 4, 2), (16.0, 8.0, 4.0), 5, "tma"),
-    ((5, 3, 2), (10.0, 6.0, 4.0), 4, "tma"),
+    # per plane (its strips wrap onto itself) and several tiles; p = 5 (25 x 5 tiles),
+    # p = 4 (24 x 8) and p = 6 (24 x 6)
+    ((5, 1, 2), (10.0, 2.0, 4.0), 5, "tma"),
+    ((10, 2, 2), (20.0, 4.0, 4.0), 5, "tma"),
+    ((6, 2, 2), (12.0, 4.0, 4.0), 4, "tma"),
+    ((4, 2, 2), (8.0, 4.0, 4.0), 6, "tma"),
 ]
 
 
