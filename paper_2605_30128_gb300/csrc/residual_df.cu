@@ -186,15 +186,6 @@ struct ResidualDFArgs {
   int nvec;
 };
 
-template <int P>
-struct DFTile {
-  static constexpr bool small = P <= 5;
-  static constexpr int TX = small ? P * ((20 + P - 1) / P) : P * ((12 + P - 1) / P);
-  static constexpr int TY = small ? P * ((10 + P - 1) / P) : P * ((12 + P - 1) / P);
-  static constexpr int MINB = small ? 2 : 1;
-  static constexpr int NST = 3;   // two planes in flight
-};
-
 template <int P, int TX, int TY, int NST>
 constexpr size_t df_smem_bytes() {
   constexpr int W = TX + P + 1, H = TY + P + 1, HALO = W * H, NT = TX * TY;
@@ -203,6 +194,23 @@ constexpr size_t df_smem_bytes() {
          + size_t(2) * 2 * HALO * sizeof(float4)    // converted planes (hi, lo), double buffered
          + size_t(3) * (P + 1) * (P + 1) * sizeof(Coef);
 }
+
+// Tiles as the FP32 step kernel's (one element high, about 24 nodes wide), a 2-deep ring
+// (one plane in flight: the kernel is ALU bound), and as many blocks per SM (at most
+// three) as 227 KB of shared memory and the registers hold.  Timed on a GB300 at p = 5 (256 vectors, 2M
+// DoF, kernel alone): 20x10/2 blocks with a 3-deep ring 18.2 ms, 20x10/2 ring 2 18.1,
+// 25x5/2 ring 3 19.1, 25x10/2 ring 2 16.0, 25x5/3 ring 2 15.9 (kept).
+template <int P>
+struct DFTile {
+  static constexpr int TX = TileOf<float, P>::TX;
+  static constexpr int TY = TileOf<float, P>::TY;
+  static constexpr int NST = 2;
+  static constexpr int FIT_SMEM = int((227u * 1024u) / df_smem_bytes<P, TX, TY, NST>());
+  // registers a thread needs without spilling grow with the P z-accumulators (~96 + 12 P)
+  static constexpr int FIT_REGS = 65536 / (((TX * TY + 31) / 32) * 32 * (96 + 12 * P));
+  static constexpr int FIT = FIT_SMEM < FIT_REGS ? FIT_SMEM : FIT_REGS;
+  static constexpr int MINB = FIT < 1 ? 1 : (FIT > 3 ? 3 : FIT);
+};
 
 template <int P, int TX, int TY, int NST>
 __global__ void __launch_bounds__(TX* TY, DFTile<P>::MINB)
