@@ -93,23 +93,28 @@ __global__ void nl_delta_kernel(const Real* __restrict__ delta, const Real* __re
   }
 }
 
-// grid (ceil(nunion/128), nvec); thread per node of the support union: the node's
-// output gains w sum_e beta_e C2[atom_e] over its entries e, in one read-modify-write
+// grid (ceil(nunion/128), ceil(nvec/NV)); thread per node of the support union and NV
+// consecutive vectors: the node's outputs gain w sum_e beta_e C2[atom_e][.][v] over its
+// support entries e, in one read-modify-write per vector.  The entry lists and beta are
+// read once for the NV vectors; C2[a][f][v..v+NV) is contiguous.
+constexpr int kAddbackNV = 8;
 template <typename Real>
 __global__ void nl_addback_kernel(const int* __restrict__ unode, const int* __restrict__ uoff,
                                   const int* __restrict__ uent, const int* __restrict__ atom,
                                   const Real* __restrict__ beta, const double* __restrict__ mass,
                                   int nunion, const Real* __restrict__ C2, int nvec, int add_mass,
                                   Real* out, int64_t ld) {
+  constexpr int NV = kAddbackNV;
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y;
+  const int v0 = blockIdx.y * NV;
   if (u >= nunion) return;
   const int I = unode[u];
-  Real* y = out + 2 * int64_t(v) * ld + 4 * int64_t(I);
-  Real y0[4];   // loaded first: the read overlaps the sums below
+  const int nv = min(NV, nvec - v0);
+  Real s[NV][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) y0[i] = y[i];
-  Real s[4] = {0, 0, 0, 0};
+  for (int j = 0; j < NV; ++j)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) s[j][i] = Real(0);
   for (int k = uoff[u]; k < uoff[u + 1]; ++k) {
     const int e = uent[k];
     const int a = atom[e];
@@ -118,15 +123,24 @@ __global__ void nl_addback_kernel(const int* __restrict__ unode, const int* __re
       const Real b = beta[6 * int64_t(e) + f6];
 #pragma unroll
       for (int sg = 0; sg < 2; ++sg) {
-        const int64_t kk = 2 * ((int64_t(a) * 12 + 2 * f6 + sg) * nvec + v);
-        s[2 * sg + 0] += b * C2[kk];
-        s[2 * sg + 1] += b * C2[kk + 1];
+        const Real* c = C2 + 2 * ((int64_t(a) * 12 + 2 * f6 + sg) * nvec + v0);
+#pragma unroll
+        for (int j = 0; j < NV; ++j)
+          if (j < nv) {
+            s[j][2 * sg + 0] += b * c[2 * j];
+            s[j][2 * sg + 1] += b * c[2 * j + 1];
+          }
       }
     }
   }
   const Real w = add_mass ? Real(mass[I]) : Real(1);
 #pragma unroll
-  for (int i = 0; i < 4; ++i) y[i] = y0[i] + w * s[i];
+  for (int j = 0; j < NV; ++j)
+    if (j < nv) {
+      Real* y = out + 2 * int64_t(v0 + j) * ld + 4 * int64_t(I);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) y[i] += w * s[j][i];
+    }
 }
 
 // gh[a][j] += wgt Re sum_v CW[a,(j,.,.)]^H P_j CU[a,(j,.,.)]; thread per (a, v), atomics
@@ -198,7 +212,7 @@ int launch_nl_addback(rcf_ctx* ctx, const rcf_op* op, const Real* C2, int nvec, 
                       Real* out, int64_t ld) {
   const ProjAtoms& pa = op->proj;
   if (pa.natoms == 0 || nvec == 0 || pa.nunion == 0) return RCF_OK;
-  dim3 grid(unsigned((pa.nunion + 127) / 128), nvec);
+  dim3 grid(unsigned((pa.nunion + 127) / 128), unsigned((nvec + kAddbackNV - 1) / kAddbackNV));
   nl_addback_kernel<Real><<<grid, 128, 0, ctx->stream>>>(pa.d_unode, pa.d_uoff, pa.d_uent, pa.d_atom,
                                                           beta_of<Real>(op), op->mesh->d_mass, pa.nunion,
                                                           C2, nvec, add_mass, out, ld);
