@@ -416,19 +416,20 @@ def run_ours(args):
             Xh.copy_(X[:blk])
             sample = f"first block of {blk} vectors (pinned host memory for the full block set unavailable)"
         ne = Xh.shape[0]
+        # the C ABI's host-buffer filter: band blocks stream through device slots, copies in
+        # and out overlapping the filtering of the neighbouring blocks
+        R.rcf_filter_host(ctx, op, Xh, ritz[:ne], q, bounds, R.RCF_RCHFSI, R.RCF_FP32_DF, w.block, Yh)
         torch.cuda.synchronize()
-        ev0.record(stream)
+        t0 = time.perf_counter()
         for _ in range(max(1, args.steps)):
-            X[:ne].copy_(Xh, non_blocking=True)
-            R.rcf_filter(ctx, op, X[:ne], ritz[:ne], q, bounds, R.RCF_RCHFSI, R.RCF_FP32_DF, w.block, Y[:ne])
-            Yh.copy_(Y[:ne], non_blocking=True)
-        ev1.record(stream)
+            R.rcf_filter_host(ctx, op, Xh, ritz[:ne], q, bounds, R.RCF_RCHFSI, R.RCF_FP32_DF, w.block, Yh)
         torch.cuda.synchronize()
-        e_ms = ev0.elapsed_time(ev1) / max(1, args.steps)
+        e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
         e_ms = max_over_ranks(ws, e_ms)
         line["e2e"] = {"value": float(N) * ne * q * ws / (e_ms * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": int(Xh.numel() * 16), "d2h_bytes_per_step": int(Yh.numel() * 16),
-                       "ms_per_step": e_ms, "sample": sample}
+                       "ms_per_step": e_ms, "sample": sample,
+                       "call": "rcf_filter_host (pinned host X and Y; wall clock around the synchronising call)"}
         del Xh, Yh
 
         # ---- the adjoint filter on the 8^3-cell p = 4 workload (64 vectors, degree 15,

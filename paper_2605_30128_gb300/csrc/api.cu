@@ -231,6 +231,8 @@ extern "C" int rcf_destroy(rcf_ctx* ctx) {
   if (ctx->solver) cusolverDnDestroy(ctx->solver);
   if (ctx->d_pj) cudaFree(ctx->d_pj);
   if (ctx->d_err) cudaFree(ctx->d_err);
+  if (ctx->copy_in) cudaStreamDestroy(ctx->copy_in);
+  if (ctx->copy_out) cudaStreamDestroy(ctx->copy_out);
   delete ctx;
   return RCF_OK;
 }

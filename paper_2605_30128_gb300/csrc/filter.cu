@@ -30,6 +30,11 @@ int check_block(rcf_ctx* ctx, const rcf_op* op, const void* p, int64_t ld, int n
   return RCF_OK;
 }
 
+// status of a CUDA call, recorded in the context (for use where RCF_CUDA cannot return)
+int cuda_check(rcf_ctx* ctx, cudaError_t e) {
+  return e == cudaSuccess ? RCF_OK : cuda_fail(ctx, e, "CUDA call", __FILE__, __LINE__);
+}
+
 // do two multivectors (nvec columns of ld complex elements of size_a / size_b bytes) overlap
 bool overlaps(const void* a, int64_t lda, size_t size_a, const void* b, int64_t ldb, size_t size_b, int nvec) {
   if (!a || !b || nvec == 0) return false;
@@ -486,6 +491,97 @@ extern "C" int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64
     // the per-block coefficient table is a host vector copied asynchronously
     RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   }
+  return check_device_error(ctx);
+}
+
+extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
+                               const double* ritz, int degree, const double bounds[3], int mode, int prec,
+                               int block, double* Y, int64_t ldy) {
+  if (!ctx || !op) return RCF_EINVAL;
+  const int64_t rows = 2 * op->mesh->nnodes;
+  if (nvec < 0) return fail(ctx, RCF_EINVAL, "nvec < 0");
+  if (nvec > 0 && (!X || !Y)) return fail(ctx, RCF_EINVAL, "NULL X or Y");
+  if (ldx < rows || ldy < rows) return fail(ctx, RCF_EINVAL, "leading dimension below 2M");
+  if (overlaps(X, ldx, Y, ldy, nvec, 16)) return fail(ctx, RCF_EINVAL, "Y overlaps X");
+  if (mode != RCF_CHFSI && mode != RCF_RCHFSI) return fail(ctx, RCF_EINVAL, "unknown mode %d", mode);
+  if (prec != RCF_FP64 && prec != RCF_FP32 && prec != RCF_FP32_DF)
+    return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  if (prec == RCF_FP32_DF && mode != RCF_RCHFSI) return fail(ctx, RCF_EINVAL, "RCF_FP32_DF applies to R-ChFSI only");
+  if (mode == RCF_RCHFSI && !ritz && nvec > 0) return fail(ctx, RCF_EINVAL, "ritz is NULL");
+  Cheb ch;
+  RCF_TRY(cheb_scalars(ctx, bounds, degree, &ch));
+  if (nvec == 0) return RCF_OK;
+  for (cudaStream_t* st : {&ctx->copy_in, &ctx->copy_out})
+    if (!*st) RCF_CUDA(ctx, cudaStreamCreateWithFlags(st, cudaStreamNonBlocking));
+  const int nb = (block <= 0 || block > nvec) ? nvec : block;
+  const int nblk = (nvec + nb - 1) / nb;
+  // two device slots for X blocks and two for Y blocks, ld = 2M
+  double* dx[2] = {nullptr, nullptr};
+  double* dy[2] = {nullptr, nullptr};
+  const size_t bytes = sizeof(double) * 2 * size_t(rows) * nb;
+  RCF_TRY(workspace(ctx, WS_HX0, bytes, reinterpret_cast<void**>(&dx[0])));
+  RCF_TRY(workspace(ctx, WS_HY0, bytes, reinterpret_cast<void**>(&dy[0])));
+  if (nblk > 1) {
+    RCF_TRY(workspace(ctx, WS_HX1, bytes, reinterpret_cast<void**>(&dx[1])));
+    RCF_TRY(workspace(ctx, WS_HY1, bytes, reinterpret_cast<void**>(&dy[1])));
+  }
+  // events: X block landed, block filtered (its X slot free, Y ready), Y slot copied out
+  std::vector<cudaEvent_t> ev_in(nblk), ev_done(nblk), ev_out(nblk);
+  auto make = [&](std::vector<cudaEvent_t>& v) -> int {
+    for (auto& e : v) RCF_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return RCF_OK;
+  };
+  int st = make(ev_in);
+  if (st == RCF_OK) st = make(ev_done);
+  if (st == RCF_OK) st = make(ev_out);
+  auto copy_rows = [&](double* dst, int64_t ldd, const double* src, int64_t lds, int n, cudaMemcpyKind kind,
+                       cudaStream_t s) -> int {
+    RCF_CUDA(ctx, cudaMemcpy2DAsync(dst, sizeof(double) * 2 * ldd, src, sizeof(double) * 2 * lds,
+                                    sizeof(double) * 2 * rows, n, kind, s));
+    return RCF_OK;
+  };
+  auto count = [&](int b) { return std::min(nb, nvec - b * nb); };
+  if (st == RCF_OK) st = copy_rows(dx[0], rows, X, ldx, count(0), cudaMemcpyHostToDevice, ctx->copy_in);
+  if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_in[0], ctx->copy_in));
+  for (int b = 0; b < nblk && st == RCF_OK; ++b) {
+    const int n = count(b);
+    // prefetch the next block into the other X slot once the block that used it is done
+    if (b + 1 < nblk) {
+      if (b >= 1) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->copy_in, ev_done[b - 1], 0));
+      if (st == RCF_OK)
+        st = copy_rows(dx[(b + 1) % 2], rows, X + 2 * int64_t(b + 1) * nb * ldx, ldx, count(b + 1),
+                       cudaMemcpyHostToDevice, ctx->copy_in);
+      if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_in[b + 1], ctx->copy_in));
+    }
+    if (st == RCF_OK) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ev_in[b], 0));
+    if (st == RCF_OK && b >= 2) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ev_out[b - 2], 0));
+    if (st == RCF_OK) {
+      double* xs = dx[b % 2];
+      double* ys = dy[b % 2];
+      if (mode == RCF_RCHFSI) {
+        if (prec == RCF_FP64) st = rchfsi_block<double>(ctx, op, ch, degree, xs, rows, n, ritz + int64_t(b) * nb, ys, rows);
+        else st = rchfsi_block<float>(ctx, op, ch, degree, xs, rows, n, ritz + int64_t(b) * nb, ys, rows, prec == RCF_FP32_DF);
+      } else {
+        if (prec == RCF_FP64) st = chfsi_block64(ctx, op, ch, degree, xs, rows, n, ys, rows);
+        else st = chfsi_block32(ctx, op, ch, degree, xs, rows, n, ys, rows);
+      }
+    }
+    if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_done[b], ctx->stream));
+    // copy the filtered block out while the next one is filtered
+    if (st == RCF_OK) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->copy_out, ev_done[b], 0));
+    if (st == RCF_OK)
+      st = copy_rows(Y + 2 * int64_t(b) * nb * ldy, ldy, dy[b % 2], rows, n, cudaMemcpyDeviceToHost, ctx->copy_out);
+    if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_out[b], ctx->copy_out));
+    // the per-block coefficient table is a host vector copied asynchronously
+    if (st == RCF_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream));
+  }
+  // drain both copy streams (also on failure, before the events go away)
+  cudaStreamSynchronize(ctx->copy_in);
+  cudaStreamSynchronize(ctx->copy_out);
+  for (auto* v : {&ev_in, &ev_done, &ev_out})
+    for (auto e : *v)
+      if (e) cudaEventDestroy(e);
+  if (st != RCF_OK) return st;
   return check_device_error(ctx);
 }
 

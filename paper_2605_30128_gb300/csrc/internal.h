@@ -37,6 +37,8 @@ struct rcf_ctx {
   int64_t launches = 0;     // kernels launched by this library on this context
   int* d_err = nullptr;     // device error word: set by a kernel whose bounded wait timed out
   int step_kernel = RCF_STEP_CPASYNC;   // FP32 step kernel (rcf_set_step_kernel)
+  cudaStream_t copy_in = nullptr;       // host-to-device and device-to-host streams of
+  cudaStream_t copy_out = nullptr;      // rcf_filter_host (created on first use)
   // grow-only scratch buffers, one per slot
   std::vector<void*> ws_ptr;
   std::vector<size_t> ws_size;
@@ -127,7 +129,7 @@ int workspace(rcf_ctx* ctx, int slot, size_t bytes, void** out);
 enum WsSlot {
   WS_R64 = 0, WS_R32, WS_ZA, WS_ZB, WS_COEF, WS_NLC, WS_NLC2, WS_LANCZOS, WS_RR_W, WS_RR_S,
   WS_RR_T, WS_RR_INFO, WS_RR_WORK, WS_GRAD, WS_CKPT, WS_ADJ_A, WS_ADJ_B, WS_ADJ_C, WS_ADJ_U,
-  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_COUNT
+  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HX1, WS_HY0, WS_HY1, WS_COUNT
 };
 
 // ---------------------------------------------------------------------------

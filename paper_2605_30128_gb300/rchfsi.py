@@ -30,7 +30,7 @@ EXPORTS = [
     "rcf_apply", "rcf_lanczos_bounds", "rcf_residual", "rcf_filter", "rcf_rayleigh_ritz",
     "rcf_grad_bilinear", "rcf_adjoint_filter", "rcf_cheb_step", "rcf_launch_count",
     "rcf_apply_noalloc", "rcf_set_step_kernel", "rcf_residual_df", "rcf_cholqr2",
-    "rcf_rayleigh_ritz_orth",
+    "rcf_rayleigh_ritz_orth", "rcf_filter_host",
 ]
 
 _lib = None
@@ -83,6 +83,7 @@ def lib() -> ctypes.CDLL:
         "rcf_set_step_kernel": (i32, [vp, i32]),
         "rcf_residual_df": (i32, [vp, vp, vp, i64, i32, vp, vp, vp, i64]),
         "rcf_cholqr2": (i32, [vp, vp, vp, i64, i32]),
+        "rcf_filter_host": (i32, [vp, vp, vp, i64, i32, vp, i32, vp, i32, i32, i32, vp, i64]),
         "rcf_rayleigh_ritz_orth": (i32, [vp, vp, vp, i64, i32, vp, i64, vp]),
     }
     for name, (res, args) in sig.items():
@@ -286,6 +287,28 @@ def rcf_filter(ctx, op, X, ritz, degree: int, bounds, mode: int, prec: int, bloc
     b = np.ascontiguousarray(bounds, dtype=np.float64)
     _check(ctx, lib().rcf_filter(ctx, op, px, ldx, X.shape[0], _np_ptr(rz) if rz is not None else None,
                                  int(degree), _np_ptr(b), int(mode), int(prec), int(block), py, ldy))
+
+
+def _host(t, name):
+    """(pointer, ld) of a host multivector tensor of shape (nvec, rows), complex128."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a host tensor")
+    if t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be complex128, got {t.dtype}")
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError(f"{name} must be (nvec, rows) with unit row stride")
+    return ctypes.c_void_p(t.data_ptr()), int(t.stride(0))
+
+
+def rcf_filter_host(ctx, op, X, ritz, degree: int, bounds, mode: int, prec: int, block: int, Y):
+    """rcf_filter with X and Y in host memory (pin them for copy/compute overlap)."""
+    px, ldx = _host(X, "X")
+    py, ldy = _host(Y, "Y")
+    rz = None if ritz is None else np.ascontiguousarray(ritz, dtype=np.float64)
+    b = np.ascontiguousarray(bounds, dtype=np.float64)
+    _check(ctx, lib().rcf_filter_host(ctx, op, px, ldx, X.shape[0], _np_ptr(rz) if rz is not None else None,
+                                      int(degree), _np_ptr(b), int(mode), int(prec), int(block), py, ldy))
 
 
 def rcf_rayleigh_ritz(ctx, op, Y, X_out):
