@@ -30,6 +30,8 @@ int check_block(rcf_ctx* ctx, const rcf_op* op, const void* p, int64_t ld, int n
   return RCF_OK;
 }
 
+constexpr int kHostSlots = 4;   // device slots per direction of rcf_filter_host
+
 // status of a CUDA call, recorded in the context (for use where RCF_CUDA cannot return)
 int cuda_check(rcf_ctx* ctx, cudaError_t e) {
   return e == cudaSuccess ? RCF_OK : cuda_fail(ctx, e, "CUDA call", __FILE__, __LINE__);
@@ -515,16 +517,16 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
     if (!*st) RCF_CUDA(ctx, cudaStreamCreateWithFlags(st, cudaStreamNonBlocking));
   const int nb = (block <= 0 || block > nvec) ? nvec : block;
   const int nblk = (nvec + nb - 1) / nb;
-  // two device slots for X blocks and two for Y blocks, ld = 2M
-  double* dx[2] = {nullptr, nullptr};
-  double* dy[2] = {nullptr, nullptr};
+  // S device slots for X blocks and S for Y blocks (ld = 2M): the copies of up to S
+  // blocks ahead (in) and behind (out) proceed while a block is filtered
+  const int S = std::min(nblk, kHostSlots);
   const size_t bytes = sizeof(double) * 2 * size_t(rows) * nb;
-  RCF_TRY(workspace(ctx, WS_HX0, bytes, reinterpret_cast<void**>(&dx[0])));
-  RCF_TRY(workspace(ctx, WS_HY0, bytes, reinterpret_cast<void**>(&dy[0])));
-  if (nblk > 1) {
-    RCF_TRY(workspace(ctx, WS_HX1, bytes, reinterpret_cast<void**>(&dx[1])));
-    RCF_TRY(workspace(ctx, WS_HY1, bytes, reinterpret_cast<void**>(&dy[1])));
-  }
+  double* dxs = nullptr;
+  double* dys = nullptr;
+  RCF_TRY(workspace(ctx, WS_HX0, bytes * S, reinterpret_cast<void**>(&dxs)));
+  RCF_TRY(workspace(ctx, WS_HY0, bytes * S, reinterpret_cast<void**>(&dys)));
+  auto dx = [&](int b) { return dxs + 2 * size_t(rows) * nb * (b % S); };
+  auto dy = [&](int b) { return dys + 2 * size_t(rows) * nb * (b % S); };
   // events: X block landed, block filtered (its X slot free, Y ready), Y slot copied out
   std::vector<cudaEvent_t> ev_in(nblk), ev_done(nblk), ev_out(nblk);
   auto make = [&](std::vector<cudaEvent_t>& v) -> int {
@@ -541,23 +543,21 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
     return RCF_OK;
   };
   auto count = [&](int b) { return std::min(nb, nvec - b * nb); };
-  if (st == RCF_OK) st = copy_rows(dx[0], rows, X, ldx, count(0), cudaMemcpyHostToDevice, ctx->copy_in);
-  if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_in[0], ctx->copy_in));
+  // block b into its X slot once the block that used the slot before (b - S) is filtered
+  auto copy_in = [&](int b) -> int {
+    if (b >= S) RCF_TRY(cuda_check(ctx, cudaStreamWaitEvent(ctx->copy_in, ev_done[b - S], 0)));
+    RCF_TRY(copy_rows(dx(b), rows, X + 2 * int64_t(b) * nb * ldx, ldx, count(b), cudaMemcpyHostToDevice,
+                      ctx->copy_in));
+    return cuda_check(ctx, cudaEventRecord(ev_in[b], ctx->copy_in));
+  };
+  for (int b = 0; b < S && st == RCF_OK; ++b) st = copy_in(b);
   for (int b = 0; b < nblk && st == RCF_OK; ++b) {
     const int n = count(b);
-    // prefetch the next block into the other X slot once the block that used it is done
-    if (b + 1 < nblk) {
-      if (b >= 1) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->copy_in, ev_done[b - 1], 0));
-      if (st == RCF_OK)
-        st = copy_rows(dx[(b + 1) % 2], rows, X + 2 * int64_t(b + 1) * nb * ldx, ldx, count(b + 1),
-                       cudaMemcpyHostToDevice, ctx->copy_in);
-      if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_in[b + 1], ctx->copy_in));
-    }
-    if (st == RCF_OK) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ev_in[b], 0));
-    if (st == RCF_OK && b >= 2) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ev_out[b - 2], 0));
+    st = cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ev_in[b], 0));
+    if (st == RCF_OK && b >= S) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ev_out[b - S], 0));
     if (st == RCF_OK) {
-      double* xs = dx[b % 2];
-      double* ys = dy[b % 2];
+      double* xs = dx(b);
+      double* ys = dy(b);
       if (mode == RCF_RCHFSI) {
         if (prec == RCF_FP64) st = rchfsi_block<double>(ctx, op, ch, degree, xs, rows, n, ritz + int64_t(b) * nb, ys, rows);
         else st = rchfsi_block<float>(ctx, op, ch, degree, xs, rows, n, ritz + int64_t(b) * nb, ys, rows, prec == RCF_FP32_DF);
@@ -567,11 +567,12 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
       }
     }
     if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_done[b], ctx->stream));
-    // copy the filtered block out while the next one is filtered
+    // copy the filtered block out while the next ones are filtered
     if (st == RCF_OK) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->copy_out, ev_done[b], 0));
     if (st == RCF_OK)
-      st = copy_rows(Y + 2 * int64_t(b) * nb * ldy, ldy, dy[b % 2], rows, n, cudaMemcpyDeviceToHost, ctx->copy_out);
+      st = copy_rows(Y + 2 * int64_t(b) * nb * ldy, ldy, dy(b), rows, n, cudaMemcpyDeviceToHost, ctx->copy_out);
     if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_out[b], ctx->copy_out));
+    if (st == RCF_OK && b + S < nblk) st = copy_in(b + S);
     // the per-block coefficient table is a host vector copied asynchronously
     if (st == RCF_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream));
   }
