@@ -297,16 +297,21 @@ def run_ours(args):
     units = float(N) * nvec * q
     value = units * ws / (ms * 1e-3)
 
-    # the same filter with the residual in native FP64
-    step(R.RCF_FP32)
-    torch.cuda.synchronize()
-    barrier(ws)
-    ev0.record(stream)
-    for _ in range(max(1, args.steps - 1)):
-        step(R.RCF_FP32)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms64 = max_over_ranks(ws, ev0.elapsed_time(ev1) / max(1, args.steps - 1))
+    # the same filter with the residual in native FP64, and with the recurrence stored in 16 bits
+    def time_variant(prec):
+        step(prec)
+        torch.cuda.synchronize()
+        barrier(ws)
+        ev0.record(stream)
+        for _ in range(max(1, args.steps - 1)):
+            step(prec)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(ws, ev0.elapsed_time(ev1) / max(1, args.steps - 1))
+
+    ms64 = time_variant(R.RCF_FP32)
+    ms16 = time_variant(R.RCF_FP16)
+    msb16 = time_variant(R.RCF_BF16)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -321,7 +326,12 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "variants": {"fp64_residual": {"value": units * ws / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
-                                       "precision": "as above with the residual in native FP64 (RCF_FP32)"}},
+                                       "precision": "as above with the residual in native FP64 (RCF_FP32)"},
+                     "fp16_storage": {"value": units * ws / (ms16 * 1e-3), "unit": UNIT, "ms_per_step": ms16,
+                                      "precision": "Z_k, Z_{k-1}, R stored as binary16 pairs (R scaled per column), "
+                                                   "products in FP32, double-float residual (RCF_FP16)"},
+                     "bf16_storage": {"value": units * ws / (msb16 * 1e-3), "unit": UNIT, "ms_per_step": msb16,
+                                      "precision": "as fp16_storage with bfloat16 (RCF_BF16)"}},
     }
 
     # ---- dominant kernel: one FP32 recurrence step on a block, timed alone ----
@@ -349,6 +359,20 @@ def run_ours(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     step_ms = ev0.elapsed_time(ev1) / nrep
+    # the same step with the vectors stored as binary16 (16 B per unit)
+    zk16 = torch.view_as_real(Zk).reshape(blk, -1).to(torch.float16)
+    zm16 = torch.view_as_real(Zm).reshape(blk, -1).to(torch.float16)
+    rr16 = torch.view_as_real(Rr).reshape(blk, -1).to(torch.float16)
+    for _ in range(3):
+        R.rcf_cheb_step(ctx, op1, R.RCF_FORM_H_DINV, R.RCF_FP16, zk16, zm16, rr16, 0.1, -0.5, -1.0, g, zm16)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(nrep):
+        R.rcf_cheb_step(ctx, op1, R.RCF_FORM_H_DINV, R.RCF_FP16, zk16, zm16, rr16, 0.1, -0.5, -1.0, g, zm16)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    k16_ms = ev0.elapsed_time(ev1) / nrep
+    del zk16, zm16, rr16
     R.rcf_op_destroy(op1)
     del Zk, Zm, Rr
     # the residual of one block: double-float (the headline path) and native FP64
@@ -379,6 +403,10 @@ def run_ours(args):
                         "kernel_ms": k_ms, "algorithmic_bytes": BYTES_PER_UNIT * N * blk,
                         "peak_source": "measured" if peaks else "fallback",
                         "step_with_projectors_ms": step_ms}
+    line["roofline_fp16_step"] = {"bound": "hbm", "achieved": 16.0 * N * blk / (k16_ms * 1e-3) / 1e9, "peak": peak,
+                                  "unit": "GB/s", "frac": 16.0 * N * blk / (k16_ms * 1e-3) / 1e9 / peak,
+                                  "kernel_ms": k16_ms, "algorithmic_bytes": 16.0 * N * blk,
+                                  "kernel": "step_kernel<float,__half,5> (recurrence step, vectors stored as binary16)"}
     line["residual"] = {"double_float_ms": res_df_ms, "fp64_ms": res64_ms, "vectors": blk,
                         "note": "R = H X - M X Lambda of one block, spin-orbit terms included"}
 

@@ -57,7 +57,18 @@ typedef enum {
  * sums: about 2^-46 relative accuracy, against 2^-52 for FP64) instead of FP64,
  * because this GPU runs FP64 at a small fraction of its FP32 rate.  The paper
  * keeps R in FP64 (Section III-C); this variant is the library's. */
-typedef enum { RCF_FP64 = 0, RCF_FP32 = 1, RCF_FP32_DF = 2 } rcf_precision;
+typedef enum { RCF_FP64 = 0, RCF_FP32 = 1, RCF_FP32_DF = 2, RCF_FP16 = 3, RCF_BF16 = 4 } rcf_precision;
+/* RCF_FP16 / RCF_BF16 (R-ChFSI only; in rcf_apply and rcf_cheb_step the
+ * multivectors are 16-bit complex pairs): the recurrence vectors Z_k, Z_{k-1}
+ * and R are STORED as IEEE binary16 / bfloat16 pairs and the products are
+ * computed in FP32 from them; R is the double-float residual, each column
+ * scaled to unit norm before rounding (the recurrence is linear in (Z, R), so
+ * the scale returns exactly in the recovery).  This halves the bytes per step
+ * of the bandwidth-bound recurrence; the residual-proportional error bound
+ * that lets the paper run the products in FP32/TF32 (Section III-C) covers the
+ * 16-bit rounding of the stored vectors as well, since that error too scales
+ * with ||R||.  The paper applies 16-bit and block-floating-point formats to
+ * communicated data (Section III-C-3); this variant is the library's. */
 
 /* Filter form: plain ChFSI (Eq. ChFSIrecurrence) or R-ChFSI (Eq. rChFSIrecurrence). */
 typedef enum { RCF_CHFSI = 0, RCF_RCHFSI = 1 } rcf_mode;

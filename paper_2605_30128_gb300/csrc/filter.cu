@@ -5,6 +5,8 @@
 #include <cmath>
 #include <vector>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace rcf {
@@ -164,9 +166,9 @@ double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, i
 //   form H_DINV: out = A (H D^{-1}) in + ...       (R-ChFSI, Eq. rChFSIrecurrence)
 //   form DINV_H: out = A (D^{-1} H) in + ...       (ChFSI, Eq. ChFSIrecurrence)
 //   form H:      out = M (A (D^{-1} H_loc) in + B in + C prev + g rv) + A H_nloc in
-template <typename Real>
-int apply_full(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real>& a0) {
-  StepArgs<Real> a = a0;
+template <typename Real, typename St>
+int apply_full(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real, St>& a0) {
+  StepArgs<Real, St> a = a0;
   a.pot = pot_of<Real>(op);
   a.mass = op->mesh->d_mass;
   Tables t;
@@ -181,22 +183,24 @@ int apply_full(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real>& a
     const size_t bytes = sizeof(Real) * 24 * size_t(op->proj.natoms) * a.nvec;
     RCF_TRY(workspace(ctx, WS_NLC, bytes, reinterpret_cast<void**>(&C)));
     RCF_TRY(workspace(ctx, WS_NLC2, bytes, reinterpret_cast<void**>(&C2)));
-    RCF_TRY(launch_nl_project<Real>(ctx, op, a.in, a.ld_in, a.nvec, proj_mass, C));
+    RCF_TRY((launch_nl_project<Real, St>(ctx, op, a.in, a.ld_in, a.nvec, proj_mass, C)));
     RCF_TRY(launch_nl_delta<Real>(ctx, op, C, a.nvec, a.A, C2));
   }
-  RCF_TRY(launch_step<Real>(ctx, op->mesh, t, a));
-  if (nl) RCF_TRY(launch_nl_addback<Real>(ctx, op, C2, a.nvec, add_mass, a.out, a.ld_out));
+  RCF_TRY((launch_step<Real, St>(ctx, op->mesh, t, a)));
+  if (nl) RCF_TRY((launch_nl_addback<Real, St>(ctx, op, C2, a.nvec, add_mass, a.out, a.ld_out)));
   return RCF_OK;
 }
-template int apply_full<float>(rcf_ctx*, const rcf_op*, int, const StepArgs<float>&);
-template int apply_full<double>(rcf_ctx*, const rcf_op*, int, const StepArgs<double>&);
+template int apply_full<float, float>(rcf_ctx*, const rcf_op*, int, const StepArgs<float, float>&);
+template int apply_full<double, double>(rcf_ctx*, const rcf_op*, int, const StepArgs<double, double>&);
+template int apply_full<float, __half>(rcf_ctx*, const rcf_op*, int, const StepArgs<float, __half>&);
+template int apply_full<float, __nv_bfloat16>(rcf_ctx*, const rcf_op*, int, const StepArgs<float, __nv_bfloat16>&);
 
 namespace {
 
-template <typename Real>
-StepArgs<Real> step_args(const Real* in, int64_t ldin, Real* out, int64_t ldout, int nvec, Real A,
-                         Real B) {
-  StepArgs<Real> a{};
+template <typename Real, typename St = Real>
+StepArgs<Real, St> step_args(const St* in, int64_t ldin, St* out, int64_t ldout, int nvec, Real A,
+                             Real B) {
+  StepArgs<Real, St> a{};
   a.in = in; a.ld_in = ldin;
   a.out = out; a.ld_out = ldout;
   a.A = A; a.B = B; a.C = Real(0);
@@ -214,15 +218,15 @@ int residual_impl(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, 
 
 // One R-ChFSI step (Eq. rChFSIrecurrence) for k >= 1:
 //   out = a_k H D^{-1} (zs Zk) - a_k c (zs Zk) + cp * Zkm1 + g[v] R
-template <typename Real>
-int rchfsi_step(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int k, const Real* Zk, double zs,
-                const Real* Zkm1, double cp, const Real* R, const double* g, Real* out, int64_t ld,
+template <typename Real, typename St = Real>
+int rchfsi_step(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int k, const St* Zk, double zs,
+                const St* Zkm1, double cp, const St* R, const double* g, St* out, int64_t ld,
                 int nvec) {
   const double ak = 2.0 * ch.sigma[k + 1] / ch.e;
-  StepArgs<Real> a = step_args<Real>(Zk, ld, out, ld, nvec, Real(ak * zs), Real(-ak * ch.c * zs));
+  StepArgs<Real, St> a = step_args<Real, St>(Zk, ld, out, ld, nvec, Real(ak * zs), Real(-ak * ch.c * zs));
   if (Zkm1) { a.prev = Zkm1; a.ld_prev = ld; a.C = Real(cp); }
   a.rv = R; a.ld_rv = ld; a.g = g;
-  return apply_full<Real>(ctx, op, RCF_FORM_H_DINV, a);
+  return apply_full<Real, St>(ctx, op, RCF_FORM_H_DINV, a);
 }
 
 // df: the residual in double-float arithmetic, written straight to its FP32 rounding
@@ -272,7 +276,7 @@ int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const do
     RCF_TRY(workspace(ctx, WS_ZA, sizeof(Real) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&ZA)));
     RCF_TRY(workspace(ctx, WS_ZB, sizeof(Real) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&ZB)));
     // k = 1: Z_2 = a_1 H D^-1 (s R) - a_1 c s R + a_1 Lambda_1 R   (Z_0 = 0)
-    RCF_TRY(rchfsi_step<Real>(ctx, op, ch, 1, R, s, nullptr, 0.0, R, tab_d + nvec, ZA, ld, nvec));
+    RCF_TRY((rchfsi_step<Real, Real>(ctx, op, ch, 1, R, s, nullptr, 0.0, R, tab_d + nvec, ZA, ld, nvec)));
     // Z_1 = s R is never materialised: it is R with the scale folded into the coefficients.
     const Real* Zkm1 = R;
     double zps = s;
@@ -280,8 +284,8 @@ int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const do
     for (int k = 2; k < q; ++k) {
       const double bk = ch.sigma[k] * ch.sigma[k + 1];
       Real* out = (Zkm1 == R) ? ZB : const_cast<Real*>(Zkm1);   // in place over Z_{k-1}
-      RCF_TRY(rchfsi_step<Real>(ctx, op, ch, k, Zk, 1.0, Zkm1, -bk * zps, R,
-                                tab_d + size_t(k) * nvec, out, ld, nvec));
+      RCF_TRY((rchfsi_step<Real, Real>(ctx, op, ch, k, Zk, 1.0, Zkm1, -bk * zps, R,
+                                       tab_d + size_t(k) * nvec, out, ld, nvec)));
       Zkm1 = Zk;
       zps = 1.0;
       Zk = out;
@@ -290,6 +294,65 @@ int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const do
   }
   return RCF_OK;
 }
+
+// R-ChFSI with the recurrence vectors Z_k, Z_{k-1} and R stored in a 16-bit float type
+// (FP32 arithmetic): the residual in double-float arithmetic, each column of R scaled to
+// unit norm before rounding (the recurrence is linear in (Z, R), so the scale returns in
+// the recovery), q >= 2.
+template <typename St>
+int rchfsi_block16(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
+                   int nvec, const double* lam_h, double* Y, int64_t ldy) {
+  if (q < 2) return rchfsi_block<float>(ctx, op, ch, q, X, ldx, nvec, lam_h, Y, ldy, true);
+  const rcf_mesh* m = op->mesh;
+  const int64_t rows = 2 * m->nnodes;
+  const int64_t ld = rows;
+  std::vector<double> L;
+  ritz_filter_values(ch, lam_h, nvec, q, &L);
+  std::vector<double> tab(size_t(q + 1) * nvec);
+  for (int v = 0; v < nvec; ++v) tab[v] = -lam_h[v];
+  for (int k = 1; k < q; ++k) {
+    const double ak = 2.0 * ch.sigma[k + 1] / ch.e;
+    for (int v = 0; v < nvec; ++v) tab[size_t(k) * nvec + v] = ak * L[size_t(k) * nvec + v];
+  }
+  for (int v = 0; v < nvec; ++v) tab[size_t(q) * nvec + v] = L[size_t(q) * nvec + v];
+  double* tab_d = nullptr;
+  RCF_TRY(workspace(ctx, WS_COEF, sizeof(double) * tab.size(), reinterpret_cast<void**>(&tab_d)));
+  RCF_CUDA(ctx, cudaMemcpyAsync(tab_d, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
+  // R (double-float) -> FP32 rounding -> column scale -> 16-bit copy
+  float* R32 = nullptr;
+  RCF_TRY(workspace(ctx, WS_R32, sizeof(float) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R32)));
+  RCF_TRY(launch_residual_df(ctx, op, X, ldx, nvec, tab_d, R32, nullptr, ld));
+  double* sc = nullptr;   // [nrm2 | scale] doubles, then [inv] floats
+  RCF_TRY(workspace(ctx, WS_SCALE, (2 * sizeof(double) + sizeof(float)) * size_t(nvec), reinterpret_cast<void**>(&sc)));
+  double* nrm2 = sc;
+  double* scale = sc + nvec;
+  float* inv = reinterpret_cast<float*>(sc + 2 * nvec);
+  RCF_CUDA(ctx, cudaMemsetAsync(nrm2, 0, sizeof(double) * nvec, ctx->stream));
+  RCF_TRY(launch_colnorm2_f32(ctx, rows, R32, ld, nvec, nrm2));
+  RCF_TRY(launch_norm_scale(ctx, nrm2, nvec, scale, inv));
+  St* R = nullptr;
+  RCF_TRY(workspace(ctx, WS_R16, sizeof(St) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R)));
+  RCF_TRY(launch_to_storage<St>(ctx, rows, R32, ld, nvec, inv, R, ld));
+  St *ZA = nullptr, *ZB = nullptr;
+  RCF_TRY(workspace(ctx, WS_ZA, sizeof(St) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&ZA)));
+  RCF_TRY(workspace(ctx, WS_ZB, sizeof(St) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&ZB)));
+  const double s = ch.sigma[1] / ch.e;
+  RCF_TRY((rchfsi_step<float, St>(ctx, op, ch, 1, R, s, nullptr, 0.0, R, tab_d + nvec, ZA, ld, nvec)));
+  const St* Zkm1 = R;
+  double zps = s;
+  St* Zk = ZA;
+  for (int k = 2; k < q; ++k) {
+    const double bk = ch.sigma[k] * ch.sigma[k + 1];
+    St* out = (Zkm1 == R) ? ZB : const_cast<St*>(Zkm1);
+    RCF_TRY((rchfsi_step<float, St>(ctx, op, ch, k, Zk, 1.0, Zkm1, -bk * zps, R, tab_d + size_t(k) * nvec, out,
+                                    ld, nvec)));
+    Zkm1 = Zk;
+    zps = 1.0;
+    Zk = out;
+  }
+  return launch_recover_scaled<St>(ctx, m, Zk, ld, scale, X, ldx, tab_d + size_t(q) * nvec, nvec, Y, ldy);
+}
+
 
 // ChFSI (Eq. ChFSIrecurrence) in FP64 on c128 blocks
 int chfsi_block64(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
@@ -359,22 +422,71 @@ int chfsi_block32(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const d
 
 using namespace rcf;
 
+namespace rcf {
+namespace {
+
+// one band block of the filter in the requested mode and precision
+int filter_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, int mode, int prec, const double* X,
+                 int64_t ldx, int n, const double* lam, double* Y, int64_t ldy) {
+  if (mode == RCF_RCHFSI) {
+    switch (prec) {
+      case RCF_FP64: return rchfsi_block<double>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy);
+      case RCF_FP32: return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, false);
+      case RCF_FP32_DF: return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, true);
+      case RCF_FP16: return rchfsi_block16<__half>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy);
+      case RCF_BF16: return rchfsi_block16<__nv_bfloat16>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy);
+      default: return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+    }
+  }
+  if (prec == RCF_FP64) return chfsi_block64(ctx, op, ch, q, X, ldx, n, Y, ldy);
+  return chfsi_block32(ctx, op, ch, q, X, ldx, n, Y, ldy);
+}
+
+// precision and mode of rcf_filter / rcf_filter_host
+int check_filter_mode(rcf_ctx* ctx, int mode, int prec) {
+  if (mode != RCF_CHFSI && mode != RCF_RCHFSI) return fail(ctx, RCF_EINVAL, "unknown mode %d", mode);
+  if (prec < RCF_FP64 || prec > RCF_BF16) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  if (prec >= RCF_FP32_DF && mode != RCF_RCHFSI)
+    return fail(ctx, RCF_EINVAL, "precision %d applies to R-ChFSI only (it reshapes the residual)", prec);
+  return RCF_OK;
+}
+
+// bytes of one real of a multivector in precision prec (rcf_apply, rcf_cheb_step)
+size_t real_bytes(int prec) {
+  switch (prec) {
+    case RCF_FP64: return 8;
+    case RCF_FP32: return 4;
+    case RCF_FP16: case RCF_BF16: return 2;
+    default: return 0;
+  }
+}
+
+}  // namespace
+}  // namespace rcf
+
 extern "C" int rcf_apply(rcf_ctx* ctx, const rcf_op* op, int form, const void* X, int64_t ldx,
                          int nvec, void* Y, int64_t ldy, int prec) {
   if (!ctx || !op) return RCF_EINVAL;
   if (form < 0 || form > 2) return fail(ctx, RCF_EINVAL, "unknown form %d", form);
-  const size_t real = prec == RCF_FP64 ? 8 : 4;
-  if (prec != RCF_FP64 && prec != RCF_FP32) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  const size_t real = real_bytes(prec);
+  if (real == 0) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
   RCF_TRY(check_block(ctx, op, X, ldx, nvec, real, "X"));
   RCF_TRY(check_block(ctx, op, Y, ldy, nvec, real, "Y"));
   if (overlaps(X, ldx, Y, ldy, nvec, 2 * real)) return fail(ctx, RCF_EINVAL, "Y overlaps X");
   if (nvec == 0) return RCF_OK;
-  if (prec == RCF_FP64) {
-    StepArgs<double> a = step_args<double>(static_cast<const double*>(X), ldx, static_cast<double*>(Y), ldy, nvec, 1.0, 0.0);
-    return apply_full<double>(ctx, op, form, a);
+  auto run = [&](auto tag) {
+    using St = decltype(tag);
+    using Real = std::conditional_t<std::is_same_v<St, double>, double, float>;
+    StepArgs<Real, St> a = step_args<Real, St>(static_cast<const St*>(X), ldx, static_cast<St*>(Y), ldy, nvec,
+                                               Real(1), Real(0));
+    return apply_full<Real, St>(ctx, op, form, a);
+  };
+  switch (prec) {
+    case RCF_FP64: return run(double{});
+    case RCF_FP32: return run(float{});
+    case RCF_FP16: return run(__half{});
+    default: return run(__nv_bfloat16{});
   }
-  StepArgs<float> a = step_args<float>(static_cast<const float*>(X), ldx, static_cast<float*>(Y), ldy, nvec, 1.0f, 0.0f);
-  return apply_full<float>(ctx, op, form, a);
 }
 
 extern "C" int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec, const void* Zk,
@@ -382,8 +494,8 @@ extern "C" int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec,
                              double beta, double gamma, const double* g, void* out) {
   if (!ctx || !op) return RCF_EINVAL;
   if (form < 0 || form > 2) return fail(ctx, RCF_EINVAL, "unknown form %d", form);
-  if (prec != RCF_FP64 && prec != RCF_FP32) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
-  const size_t real = prec == RCF_FP64 ? 8 : 4;
+  const size_t real = real_bytes(prec);
+  if (real == 0) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
   RCF_TRY(check_block(ctx, op, Zk, ld, nvec, real, "Zk"));
   RCF_TRY(check_block(ctx, op, out, ld, nvec, real, "out"));
   if (Zkm1) RCF_TRY(check_block(ctx, op, Zkm1, ld, nvec, real, "Zkm1"));
@@ -394,16 +506,21 @@ extern "C" int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec,
     return fail(ctx, RCF_EINVAL, "out partly overlaps Zkm1");
   if (R && !g) return fail(ctx, RCF_EINVAL, "R given without g");
   if (nvec == 0) return RCF_OK;
-  if (prec == RCF_FP64) {
-    StepArgs<double> a = step_args<double>(static_cast<const double*>(Zk), ld, static_cast<double*>(out), ld, nvec, alpha, beta);
-    if (Zkm1) { a.prev = static_cast<const double*>(Zkm1); a.ld_prev = ld; a.C = gamma; }
-    if (R) { a.rv = static_cast<const double*>(R); a.ld_rv = ld; a.g = g; }
-    return apply_full<double>(ctx, op, form, a);
+  auto run = [&](auto tag) {
+    using St = decltype(tag);
+    using Real = std::conditional_t<std::is_same_v<St, double>, double, float>;
+    StepArgs<Real, St> a = step_args<Real, St>(static_cast<const St*>(Zk), ld, static_cast<St*>(out), ld, nvec,
+                                               Real(alpha), Real(beta));
+    if (Zkm1) { a.prev = static_cast<const St*>(Zkm1); a.ld_prev = ld; a.C = Real(gamma); }
+    if (R) { a.rv = static_cast<const St*>(R); a.ld_rv = ld; a.g = g; }
+    return apply_full<Real, St>(ctx, op, form, a);
+  };
+  switch (prec) {
+    case RCF_FP64: return run(double{});
+    case RCF_FP32: return run(float{});
+    case RCF_FP16: return run(__half{});
+    default: return run(__nv_bfloat16{});
   }
-  StepArgs<float> a = step_args<float>(static_cast<const float*>(Zk), ld, static_cast<float*>(out), ld, nvec, float(alpha), float(beta));
-  if (Zkm1) { a.prev = static_cast<const float*>(Zkm1); a.ld_prev = ld; a.C = float(gamma); }
-  if (R) { a.rv = static_cast<const float*>(R); a.ld_rv = ld; a.g = g; }
-  return apply_full<float>(ctx, op, form, a);
 }
 
 extern "C" int64_t rcf_launch_count(const rcf_ctx* ctx) { return ctx ? ctx->launches : -1; }
@@ -469,11 +586,7 @@ extern "C" int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64
   RCF_TRY(check_block(ctx, op, X, ldx, nvec, 8, "X"));
   RCF_TRY(check_block(ctx, op, Y, ldy, nvec, 8, "Y"));
   if (overlaps(X, ldx, Y, ldy, nvec, 16)) return fail(ctx, RCF_EINVAL, "Y overlaps X");
-  if (mode != RCF_CHFSI && mode != RCF_RCHFSI) return fail(ctx, RCF_EINVAL, "unknown mode %d", mode);
-  if (prec != RCF_FP64 && prec != RCF_FP32 && prec != RCF_FP32_DF)
-    return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
-  if (prec == RCF_FP32_DF && mode != RCF_RCHFSI)
-    return fail(ctx, RCF_EINVAL, "RCF_FP32_DF applies to R-ChFSI only");
+  RCF_TRY(check_filter_mode(ctx, mode, prec));
   if (mode == RCF_RCHFSI && !ritz && nvec > 0) return fail(ctx, RCF_EINVAL, "ritz is NULL");
   Cheb ch;
   RCF_TRY(cheb_scalars(ctx, bounds, degree, &ch));
@@ -483,13 +596,7 @@ extern "C" int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64
     const int n = std::min(nb, nvec - b0);
     const double* Xb = X + 2 * int64_t(b0) * ldx;
     double* Yb = Y + 2 * int64_t(b0) * ldy;
-    if (mode == RCF_RCHFSI) {
-      if (prec == RCF_FP64) RCF_TRY((rchfsi_block<double>(ctx, op, ch, degree, Xb, ldx, n, ritz + b0, Yb, ldy)));
-      else RCF_TRY((rchfsi_block<float>(ctx, op, ch, degree, Xb, ldx, n, ritz + b0, Yb, ldy, prec == RCF_FP32_DF)));
-    } else {
-      if (prec == RCF_FP64) RCF_TRY(chfsi_block64(ctx, op, ch, degree, Xb, ldx, n, Yb, ldy));
-      else RCF_TRY(chfsi_block32(ctx, op, ch, degree, Xb, ldx, n, Yb, ldy));
-    }
+    RCF_TRY(filter_block(ctx, op, ch, degree, mode, prec, Xb, ldx, n, ritz ? ritz + b0 : nullptr, Yb, ldy));
     // the per-block coefficient table is a host vector copied asynchronously
     RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   }
@@ -505,10 +612,7 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
   if (nvec > 0 && (!X || !Y)) return fail(ctx, RCF_EINVAL, "NULL X or Y");
   if (ldx < rows || ldy < rows) return fail(ctx, RCF_EINVAL, "leading dimension below 2M");
   if (overlaps(X, ldx, Y, ldy, nvec, 16)) return fail(ctx, RCF_EINVAL, "Y overlaps X");
-  if (mode != RCF_CHFSI && mode != RCF_RCHFSI) return fail(ctx, RCF_EINVAL, "unknown mode %d", mode);
-  if (prec != RCF_FP64 && prec != RCF_FP32 && prec != RCF_FP32_DF)
-    return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
-  if (prec == RCF_FP32_DF && mode != RCF_RCHFSI) return fail(ctx, RCF_EINVAL, "RCF_FP32_DF applies to R-ChFSI only");
+  RCF_TRY(check_filter_mode(ctx, mode, prec));
   if (mode == RCF_RCHFSI && !ritz && nvec > 0) return fail(ctx, RCF_EINVAL, "ritz is NULL");
   Cheb ch;
   RCF_TRY(cheb_scalars(ctx, bounds, degree, &ch));
@@ -558,13 +662,8 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
     if (st == RCF_OK) {
       double* xs = dx(b);
       double* ys = dy(b);
-      if (mode == RCF_RCHFSI) {
-        if (prec == RCF_FP64) st = rchfsi_block<double>(ctx, op, ch, degree, xs, rows, n, ritz + int64_t(b) * nb, ys, rows);
-        else st = rchfsi_block<float>(ctx, op, ch, degree, xs, rows, n, ritz + int64_t(b) * nb, ys, rows, prec == RCF_FP32_DF);
-      } else {
-        if (prec == RCF_FP64) st = chfsi_block64(ctx, op, ch, degree, xs, rows, n, ys, rows);
-        else st = chfsi_block32(ctx, op, ch, degree, xs, rows, n, ys, rows);
-      }
+      st = filter_block(ctx, op, ch, degree, mode, prec, xs, rows, n, ritz ? ritz + int64_t(b) * nb : nullptr,
+                        ys, rows);
     }
     if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_done[b], ctx->stream));
     // copy the filtered block out while the next ones are filtered

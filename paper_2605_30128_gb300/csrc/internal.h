@@ -1,6 +1,8 @@
 // Internal types of librchfsi: context, mesh, operator, kernel launchers.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cublas_v2.h>
 #include <cusolverDn.h>
@@ -129,7 +131,7 @@ int workspace(rcf_ctx* ctx, int slot, size_t bytes, void** out);
 enum WsSlot {
   WS_R64 = 0, WS_R32, WS_ZA, WS_ZB, WS_COEF, WS_NLC, WS_NLC2, WS_LANCZOS, WS_RR_W, WS_RR_S,
   WS_RR_T, WS_RR_INFO, WS_RR_WORK, WS_GRAD, WS_CKPT, WS_ADJ_A, WS_ADJ_B, WS_ADJ_C, WS_ADJ_U,
-  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HY0, WS_COUNT
+  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HY0, WS_R16, WS_SCALE, WS_COUNT
 };
 
 // ---------------------------------------------------------------------------
@@ -139,13 +141,15 @@ enum WsSlot {
 //   then optionally out *= M_I
 // where H_loc = kinetic + spinor potential (Eq. hloc, Eq. cellHam).
 // ---------------------------------------------------------------------------
-template <typename Real>
+// Real: arithmetic type; St: storage type of the multivectors (Real, or a 16-bit float
+// type with FP32 arithmetic)
+template <typename Real, typename St = Real>
 struct StepArgs {
-  const Real* in;    int64_t ld_in;     // complex elements per vector (even)
-  const Real* prev;  int64_t ld_prev;   // may be null
-  const Real* rv;    int64_t ld_rv;     // may be null
+  const St* in;      int64_t ld_in;     // complex elements per vector (even)
+  const St* prev;    int64_t ld_prev;   // may be null
+  const St* rv;      int64_t ld_rv;     // may be null
   const double* g;                      // [nvec] coefficients of rv (device), may be null
-  Real* out;         int64_t ld_out;
+  St* out;           int64_t ld_out;
   Real A, B, C;
   const Real* pot;                      // [nnodes][4]
   const double* mass;                   // used if scale_out
@@ -160,8 +164,8 @@ struct Tables {
 enum TableKind { TAB_ROW_SCALED = 0 /* D^{-1} H */, TAB_COL_SCALED = 1 /* H D^{-1} */ };
 void build_tables(const rcf_mesh* m, int kind, Tables* t);
 
-template <typename Real>
-int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a);
+template <typename Real, typename St = Real>
+int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real, St>& a);
 // FP32 step with TMA plane loads (stencil_tma.cu); *used = false when it does not apply
 // (degree, tile divisibility, alignment, tensor-map encoding) and the caller falls back.
 int launch_step_tma(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<float>& a, bool* used);
@@ -184,16 +188,16 @@ int launch_split_f64(rcf_ctx* ctx, int64_t n, const double* x, float* hi, float*
 // ---------------------------------------------------------------------------
 // C[a][f][v] = sum_e w_e beta_e[j,i] in[v][node_e][sigma],  f = 6 j + 2 i + sigma,
 // w_e = M_node if proj_mass else 1.   C is complex (Real2) [natoms][12][nvec].
-template <typename Real>
-int launch_nl_project(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ld, int nvec,
+template <typename Real, typename St = Real>
+int launch_nl_project(rcf_ctx* ctx, const rcf_op* op, const St* in, int64_t ld, int nvec,
                       int proj_mass, Real* C);
 // C2 = A * Delta_a C
 template <typename Real>
 int launch_nl_delta(rcf_ctx* ctx, const rcf_op* op, const Real* C, int nvec, Real A, Real* C2);
 // out[v][node_e][sigma] += w_e sum_{j,i} beta_e[j,i] C2[a][6j+2i+sigma][v], w_e = M if add_mass
-template <typename Real>
+template <typename Real, typename St = Real>
 int launch_nl_addback(rcf_ctx* ctx, const rcf_op* op, const Real* C2, int nvec, int add_mass,
-                      Real* out, int64_t ld);
+                      St* out, int64_t ld);
 
 // ---------------------------------------------------------------------------
 // vector kernels (vectors.cu)
@@ -211,6 +215,17 @@ int launch_to_c64(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, int 
                   int64_t ldy);
 int launch_colnorm2(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, int nvec,
                     double* nrm2);
+// 16-bit storage of the recurrence: column norms^2 of a complex64 block (nrm2 pre-zeroed),
+// per-column scale = norm (1 for zero columns) and its reciprocal, the scaled copy in the
+// storage type, and the recovery Y = D^{-1} Z zscale[v] + X lam[v]
+int launch_colnorm2_f32(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec, double* nrm2);
+int launch_norm_scale(rcf_ctx* ctx, const double* nrm2, int n, double* scale, float* inv);
+template <typename St>
+int launch_to_storage(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec, const float* inv,
+                      St* y, int64_t ldy);
+template <typename St>
+int launch_recover_scaled(rcf_ctx* ctx, const rcf_mesh* m, const St* Z, int64_t ldz, const double* zscale,
+                          const double* X, int64_t ldx, const double* lam, int nvec, double* Y, int64_t ldy);
 int launch_sqrt_inplace(rcf_ctx* ctx, double* v, int n);
 int launch_copy_c128(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, int nvec,
                      double* y, int64_t ldy);
@@ -240,7 +255,7 @@ int launch_grad_to_quadrature(rcf_ctx* ctx, const rcf_mesh* m, const double* gno
                               double* dB);
 
 // the Hamiltonian-multivector product with the nonlocal part (filter.cu)
-template <typename Real>
-int apply_full(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real>& a);
+template <typename Real, typename St = Real>
+int apply_full(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real, St>& a);
 
 }  // namespace rcf

@@ -6,10 +6,26 @@
 // the union of the supports (each node sums the terms of every atom whose
 // support holds it, then updates its output once: no atomics where the
 // supports of neighbouring atoms overlap).
+#include <type_traits>
+
 #include "internal.h"
 
 namespace rcf {
 namespace {
+
+// a stored value as arithmetic type and back (round to nearest even)
+template <typename Real, typename St>
+__device__ __forceinline__ Real to_real(St x) {
+  if constexpr (std::is_same_v<St, __half>) return Real(__half2float(x));
+  else if constexpr (std::is_same_v<St, __nv_bfloat16>) return Real(__bfloat162float(x));
+  else return Real(x);
+}
+template <typename St, typename Real>
+__device__ __forceinline__ St from_real(Real x) {
+  if constexpr (std::is_same_v<St, __half>) return __float2half_rn(float(x));
+  else if constexpr (std::is_same_v<St, __nv_bfloat16>) return __float2bfloat16_rn(float(x));
+  else return St(x);
+}
 
 template <typename Real>
 __device__ __forceinline__ Real warp_sum(Real x) {
@@ -21,23 +37,23 @@ __device__ __forceinline__ Real warp_sum(Real x) {
 constexpr int kProjThreads = 128;
 
 // grid (natoms, nvec); C[(a*12 + f)*nvec + v] complex
-template <typename Real>
+template <typename Real, typename St>
 __global__ void __launch_bounds__(kProjThreads)
     nl_project_kernel(const int* __restrict__ off, const int* __restrict__ node,
                       const Real* __restrict__ beta, const double* __restrict__ mass,
-                      const Real* __restrict__ in, int64_t ld, int nvec, int proj_mass,
+                      const St* __restrict__ in, int64_t ld, int nvec, int proj_mass,
                       Real* __restrict__ C) {
   const int a = blockIdx.x, v = blockIdx.y;
   const int e0 = off[a], e1 = off[a + 1];
-  const Real* x = in + 2 * int64_t(v) * ld;
+  const St* x = in + 2 * int64_t(v) * ld;
   Real acc[24];
 #pragma unroll
   for (int i = 0; i < 24; ++i) acc[i] = Real(0);
   for (int e = e0 + threadIdx.x; e < e1; e += kProjThreads) {
     const int I = node[e];
     const Real w = proj_mass ? Real(mass[I]) : Real(1);
-    const Real ur = x[4 * int64_t(I) + 0], ui = x[4 * int64_t(I) + 1];
-    const Real dr = x[4 * int64_t(I) + 2], di = x[4 * int64_t(I) + 3];
+    const Real ur = to_real<Real>(x[4 * int64_t(I) + 0]), ui = to_real<Real>(x[4 * int64_t(I) + 1]);
+    const Real dr = to_real<Real>(x[4 * int64_t(I) + 2]), di = to_real<Real>(x[4 * int64_t(I) + 3]);
 #pragma unroll
     for (int f6 = 0; f6 < 6; ++f6) {          // f6 = 3 j + i
       const Real b = w * beta[6 * int64_t(e) + f6];
@@ -98,12 +114,12 @@ __global__ void nl_delta_kernel(const Real* __restrict__ delta, const Real* __re
 // support entries e, in one read-modify-write per vector.  The entry lists and beta are
 // read once for the NV vectors; C2[a][f][v..v+NV) is contiguous.
 constexpr int kAddbackNV = 8;
-template <typename Real>
+template <typename Real, typename St>
 __global__ void nl_addback_kernel(const int* __restrict__ unode, const int* __restrict__ uoff,
                                   const int* __restrict__ uent, const int* __restrict__ atom,
                                   const Real* __restrict__ beta, const double* __restrict__ mass,
                                   int nunion, const Real* __restrict__ C2, int nvec, int add_mass,
-                                  Real* out, int64_t ld) {
+                                  St* out, int64_t ld) {
   constexpr int NV = kAddbackNV;
   const int u = blockIdx.x * blockDim.x + threadIdx.x;
   const int v0 = blockIdx.y * NV;
@@ -137,9 +153,9 @@ __global__ void nl_addback_kernel(const int* __restrict__ unode, const int* __re
 #pragma unroll
   for (int j = 0; j < NV; ++j)
     if (j < nv) {
-      Real* y = out + 2 * int64_t(v0 + j) * ld + 4 * int64_t(I);
+      St* y = out + 2 * int64_t(v0 + j) * ld + 4 * int64_t(I);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) y[i] += w * s[j][i];
+      for (int i = 0; i < 4; ++i) y[i] = from_real<St>(to_real<Real>(y[i]) + w * s[j][i]);
     }
 }
 
@@ -184,13 +200,13 @@ const double* delta_of<double>(const rcf_op* op) { return op->proj.d_delta64; }
 template <>
 const float* delta_of<float>(const rcf_op* op) { return op->proj.d_delta32; }
 
-template <typename Real>
-int launch_nl_project(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ld, int nvec,
+template <typename Real, typename St>
+int launch_nl_project(rcf_ctx* ctx, const rcf_op* op, const St* in, int64_t ld, int nvec,
                       int proj_mass, Real* C) {
   const ProjAtoms& pa = op->proj;
   if (pa.natoms == 0 || nvec == 0) return RCF_OK;
   dim3 grid(pa.natoms, nvec);
-  nl_project_kernel<Real><<<grid, kProjThreads, 0, ctx->stream>>>(
+  nl_project_kernel<Real, St><<<grid, kProjThreads, 0, ctx->stream>>>(
       pa.d_offsets, pa.d_node, beta_of<Real>(op), op->mesh->d_mass, in, ld, nvec, proj_mass, C);
   RCF_CHECK_LAUNCH(ctx);
   return RCF_OK;
@@ -207,13 +223,13 @@ int launch_nl_delta(rcf_ctx* ctx, const rcf_op* op, const Real* C, int nvec, Rea
   return RCF_OK;
 }
 
-template <typename Real>
+template <typename Real, typename St>
 int launch_nl_addback(rcf_ctx* ctx, const rcf_op* op, const Real* C2, int nvec, int add_mass,
-                      Real* out, int64_t ld) {
+                      St* out, int64_t ld) {
   const ProjAtoms& pa = op->proj;
   if (pa.natoms == 0 || nvec == 0 || pa.nunion == 0) return RCF_OK;
   dim3 grid(unsigned((pa.nunion + 127) / 128), unsigned((nvec + kAddbackNV - 1) / kAddbackNV));
-  nl_addback_kernel<Real><<<grid, 128, 0, ctx->stream>>>(pa.d_unode, pa.d_uoff, pa.d_uent, pa.d_atom,
+  nl_addback_kernel<Real, St><<<grid, 128, 0, ctx->stream>>>(pa.d_unode, pa.d_uoff, pa.d_uent, pa.d_atom,
                                                           beta_of<Real>(op), op->mesh->d_mass, pa.nunion,
                                                           C2, nvec, add_mass, out, ld);
   RCF_CHECK_LAUNCH(ctx);
@@ -262,12 +278,18 @@ int launch_grad_h(rcf_ctx* ctx, const rcf_op* op, const Real* CW, const Real* CU
 }
 
 #define INST(R)                                                                                  \
-  template int launch_nl_project<R>(rcf_ctx*, const rcf_op*, const R*, int64_t, int, int, R*); \
+  template int launch_nl_project<R, R>(rcf_ctx*, const rcf_op*, const R*, int64_t, int, int, R*); \
   template int launch_nl_delta<R>(rcf_ctx*, const rcf_op*, const R*, int, R, R*);              \
-  template int launch_nl_addback<R>(rcf_ctx*, const rcf_op*, const R*, int, int, R*, int64_t); \
+  template int launch_nl_addback<R, R>(rcf_ctx*, const rcf_op*, const R*, int, int, R*, int64_t); \
   template int launch_grad_h<R>(rcf_ctx*, const rcf_op*, const R*, const R*, int, double, double*);
 INST(float)
 INST(double)
 #undef INST
+#define INST16(S)                                                                                 \
+  template int launch_nl_project<float, S>(rcf_ctx*, const rcf_op*, const S*, int64_t, int, int, float*); \
+  template int launch_nl_addback<float, S>(rcf_ctx*, const rcf_op*, const float*, int, int, S*, int64_t);
+INST16(__half)
+INST16(__nv_bfloat16)
+#undef INST16
 
 }  // namespace rcf

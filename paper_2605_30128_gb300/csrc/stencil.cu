@@ -39,9 +39,10 @@ __host__ __device__ constexpr int stage_elems(bool own) {
 // OWN: the tile's own Z_{k-1} and R planes travel through the cp.async ring with the
 // halo (NST-1 planes ahead) instead of register prefetch one plane ahead.
 // ZB: planes consumed per block barrier (1 or 2); NST - ZB planes are in flight.
-template <typename Real, int P, int TX, int TY, int NST, bool OWN, int ZB>
+// St: storage type of the multivectors (arithmetic in Real; a 16-bit St halves the traffic)
+template <typename Real, typename St, int P, int TX, int TY, int NST, bool OWN, int ZB>
 __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
-    step_kernel(const StepArgs<Real> a, const KTab<Real, P> tab, const int Gx, const int Gy,
+    step_kernel(const StepArgs<Real, St> a, const KTab<Real, P> tab, const int Gx, const int Gy,
                 const int Gz) {
   // tab holds A * (x, y, z 1D operators); see launch_p.
   constexpr int W = TX + P + 1;        // staged columns: x0 - P .. x0 + TX
@@ -52,8 +53,10 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
   constexpr int STAGE = stage_elems<P, TX, TY>(OWN);
   static_assert(STAGE == HALO + (OWN ? 2 * NT : 0), "one stage: the plane tile with its halo (+ own planes)");
   using V4 = R4<Real>;
+  using S4 = R4<St>;
+  using CV = Cvt<Real, St>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  V4* S = reinterpret_cast<V4*>(smem_raw);                        // [NST][STAGE]
+  S4* S = reinterpret_cast<S4*>(smem_raw);                        // [NST][STAGE]
   Real* ST = reinterpret_cast<Real*>(S + NST * STAGE);           // [2][P+1][P+1] x and y tables
 
   const int tid = threadIdx.x;
@@ -70,10 +73,10 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
   const int64_t plane = int64_t(Gx) * Gy;
   const int64_t col = active ? int64_t(gx) + int64_t(Gx) * gy : 0;
 
-  const V4* in = reinterpret_cast<const V4*>(a.in + 2 * int64_t(v) * a.ld_in);
-  const V4* prev = a.prev ? reinterpret_cast<const V4*>(a.prev + 2 * int64_t(v) * a.ld_prev) : nullptr;
-  const V4* rv = a.rv ? reinterpret_cast<const V4*>(a.rv + 2 * int64_t(v) * a.ld_rv) : nullptr;
-  V4* out = reinterpret_cast<V4*>(a.out + 2 * int64_t(v) * a.ld_out);
+  const S4* in = reinterpret_cast<const S4*>(a.in + 2 * int64_t(v) * a.ld_in);
+  const S4* prev = a.prev ? reinterpret_cast<const S4*>(a.prev + 2 * int64_t(v) * a.ld_prev) : nullptr;
+  const S4* rv = a.rv ? reinterpret_cast<const S4*>(a.rv + 2 * int64_t(v) * a.ld_rv) : nullptr;
+  S4* out = reinterpret_cast<S4*>(a.out + 2 * int64_t(v) * a.ld_out);
   const V4* pot = reinterpret_cast<const V4*>(a.pot);
 
   // this thread's share of the halo plane: shared-memory slot and in-plane offset (periodic wrap)
@@ -97,15 +100,15 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
   }
 
   auto issue_plane = [&](int z, int s) {
-    V4* st = S + s * STAGE;
-    const V4* src = in + int64_t(z) * plane;
+    S4* st = S + s * STAGE;
+    const S4* src = in + int64_t(z) * plane;
 #pragma unroll
     for (int k = 0; k < KMAX; ++k)
-      if (hs[k] >= 0) cp_async_r4(st + hs[k], src + hg[k]);
+      if (hs[k] >= 0) cp_async_s4(st + hs[k], src + hg[k]);
     if (OWN && active) {
       const int64_t I = col + int64_t(z) * plane;
-      if (prev) cp_async_r4(st + HALO + tid, prev + I);
-      if (rv) cp_async_r4(st + HALO + NT + tid, rv + I);
+      if (prev) cp_async_s4(st + HALO + tid, prev + I);
+      if (rv) cp_async_s4(st + HALO + NT + tid, rv + I);
     }
     cp_async_commit();
   };
@@ -117,8 +120,8 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
     const int64_t I = col + int64_t(z) * plane;
     npot = ldg4(pot + I);
     if (!OWN) {
-      if (prev) nprev = ldg4(prev + I);
-      if (rv) nrv = ldg4(rv + I);
+      if (prev) nprev = CV::in(ldgs(prev + I));
+      if (rv) nrv = CV::in(ldgs(rv + I));
     }
   };
 
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
   V4 accn = zero4<Real>();
   if (active) {
 #pragma unroll
-    for (int c = 0; c < P; ++c) fma4(accn, tab.c[2][P][c], ldg4(in + col + int64_t(Gz - P + c) * plane));
+    for (int c = 0; c < P; ++c) fma4(accn, tab.c[2][P][c], CV::in(ldgs(in + col + int64_t(Gz - P + c) * plane)));
   }
 
   static_assert(ZB == 1 || ZB == 2, "one or two planes per barrier");
@@ -166,7 +169,7 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
 #pragma unroll
         for (int i = 0; i < 4; ++i) r.v[i] *= mI;
       }
-      st4(out + I, r);
+      st4(out + I, CV::out(r));
     }
   };
 
@@ -185,29 +188,29 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
           ++zload;
         }
       }
-      const V4* Pl = S + (z % NST) * STAGE;
-      const V4 u = Pl[(ly + P) * W + lx + P];
+      const S4* Pl = S + (z % NST) * STAGE;
+      const V4 u = CV::in(Pl[(ly + P) * W + lx + P]);
       const V4 cpot = npot;
-      const V4 cprev = OWN ? (prev ? Pl[HALO + tid] : zero4<Real>()) : nprev;
-      const V4 crv = OWN ? (rv ? Pl[HALO + NT + tid] : zero4<Real>()) : nrv;
+      const V4 cprev = OWN ? (prev ? CV::in(Pl[HALO + tid]) : zero4<Real>()) : nprev;
+      const V4 crv = OWN ? (rv ? CV::in(Pl[HALO + NT + tid]) : zero4<Real>()) : nrv;
       if (z + 1 < Gz) fetch_own(z + 1);
       // x and y terms (tables carry the factor A)
       V4 self = zero4<Real>();
       {
-        const V4* row = Pl + (ly + P) * W;
+        const S4* row = Pl + (ly + P) * W;
         const int cb = lx - ax + P;
 #pragma unroll
-        for (int q = 0; q <= P; ++q) fma4(self, cx[q], row[cb + q]);
+        for (int q = 0; q <= P; ++q) fma4(self, cx[q], CV::in(row[cb + q]));
         if (ax == 0) {
 #pragma unroll
-          for (int q = 0; q <= P; ++q) fma4(self, cxv[q], row[cb - P + q]);
+          for (int q = 0; q <= P; ++q) fma4(self, cxv[q], CV::in(row[cb - P + q]));
         }
         const int rb = ly - by + P;
 #pragma unroll
-        for (int q = 0; q <= P; ++q) fma4(self, cy[q], Pl[(rb + q) * W + lx + P]);
+        for (int q = 0; q <= P; ++q) fma4(self, cy[q], CV::in(Pl[(rb + q) * W + lx + P]));
         if (by == 0) {
 #pragma unroll
-          for (int q = 0; q <= P; ++q) fma4(self, cyv[q], Pl[(rb - P + q) * W + lx + P]);
+          for (int q = 0; q <= P; ++q) fma4(self, cyv[q], CV::in(Pl[(rb - P + q) * W + lx + P]));
         }
       }
       // A (potential) u + B u + C prev + g rv
@@ -253,8 +256,8 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
   cp_async_wait<0>();
 }
 
-template <typename Real, int P>
-int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a) {
+template <typename Real, typename St, int P>
+int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real, St>& a) {
   constexpr int TX = TileOf<Real, P>::TX, TY = TileOf<Real, P>::TY;
   constexpr int NST = TileOf<Real, P>::NST;
   constexpr bool OWN = TileOf<Real, P>::OWN;
@@ -266,8 +269,8 @@ int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Re
       for (int j = 0; j <= P; ++j) kt.c[d][i][j] = Real(double(a.A) * t.c[d][i][j]);
   const int ntx = (m->G[0] + TX - 1) / TX, nty = (m->G[1] + TY - 1) / TY;
   const size_t stage = size_t(stage_elems<P, TX, TY>(OWN));
-  const size_t smem = size_t(NST) * stage * sizeof(R4<Real>) + 2 * (P + 1) * (P + 1) * sizeof(Real);
-  auto kern = step_kernel<Real, P, TX, TY, NST, OWN, ZB>;
+  const size_t smem = size_t(NST) * stage * sizeof(R4<St>) + 2 * (P + 1) * (P + 1) * sizeof(Real);
+  auto kern = step_kernel<Real, St, P, TX, TY, NST, OWN, ZB>;
   if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   dim3 grid(ntx * nty, a.nvec);
   kern<<<grid, TX * TY, smem, ctx->stream>>>(a, kt, m->G[0], m->G[1], m->G[2]);
@@ -295,10 +298,10 @@ void build_tables(const rcf_mesh* m, int kind, Tables* t) {
   }
 }
 
-template <typename Real>
-int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real>& a) {
+template <typename Real, typename St>
+int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real, St>& a) {
   if (a.nvec <= 0) return RCF_OK;
-  if constexpr (sizeof(Real) == 4) {
+  if constexpr (sizeof(Real) == 4 && sizeof(St) == 4) {
     if (ctx->step_kernel == RCF_STEP_TMA) {
       bool used = false;
       RCF_TRY(launch_step_tma(ctx, m, t, a, &used));
@@ -306,19 +309,22 @@ int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs
     }
   }
   switch (m->p) {
-    case 1: return launch_p<Real, 1>(ctx, m, t, a);
-    case 2: return launch_p<Real, 2>(ctx, m, t, a);
-    case 3: return launch_p<Real, 3>(ctx, m, t, a);
-    case 4: return launch_p<Real, 4>(ctx, m, t, a);
-    case 5: return launch_p<Real, 5>(ctx, m, t, a);
-    case 6: return launch_p<Real, 6>(ctx, m, t, a);
-    case 7: return launch_p<Real, 7>(ctx, m, t, a);
-    case 8: return launch_p<Real, 8>(ctx, m, t, a);
+    case 1: return launch_p<Real, St, 1>(ctx, m, t, a);
+    case 2: return launch_p<Real, St, 2>(ctx, m, t, a);
+    case 3: return launch_p<Real, St, 3>(ctx, m, t, a);
+    case 4: return launch_p<Real, St, 4>(ctx, m, t, a);
+    case 5: return launch_p<Real, St, 5>(ctx, m, t, a);
+    case 6: return launch_p<Real, St, 6>(ctx, m, t, a);
+    case 7: return launch_p<Real, St, 7>(ctx, m, t, a);
+    case 8: return launch_p<Real, St, 8>(ctx, m, t, a);
     default: return fail(ctx, RCF_ENOTSUP, "degree p=%d not built (1..8)", m->p);
   }
 }
 
-template int launch_step<float>(rcf_ctx*, const rcf_mesh*, const Tables&, const StepArgs<float>&);
-template int launch_step<double>(rcf_ctx*, const rcf_mesh*, const Tables&, const StepArgs<double>&);
+template int launch_step<float, float>(rcf_ctx*, const rcf_mesh*, const Tables&, const StepArgs<float, float>&);
+template int launch_step<double, double>(rcf_ctx*, const rcf_mesh*, const Tables&, const StepArgs<double, double>&);
+template int launch_step<float, __half>(rcf_ctx*, const rcf_mesh*, const Tables&, const StepArgs<float, __half>&);
+template int launch_step<float, __nv_bfloat16>(rcf_ctx*, const rcf_mesh*, const Tables&,
+                                               const StepArgs<float, __nv_bfloat16>&);
 
 }  // namespace rcf

@@ -75,6 +75,71 @@ __device__ __forceinline__ void cp_async_r4(R4<Real>* dst, const R4<Real>* src) 
     cp_async16(reinterpret_cast<char*>(dst) + 16 * i, reinterpret_cast<const char*>(src) + 16 * i);
 }
 
+// ---- storage types: multivectors kept in St, arithmetic in Real ----
+// Conversion of a node's 4-tuple between storage and arithmetic (round to nearest even).
+template <typename Real, typename St>
+struct Cvt;
+template <typename R>
+struct Cvt<R, R> {
+  static __device__ __forceinline__ R4<R> in(const R4<R>& x) { return x; }
+  static __device__ __forceinline__ R4<R> out(const R4<R>& x) { return x; }
+};
+template <>
+struct Cvt<float, __half> {
+  static __device__ __forceinline__ R4<float> in(const R4<__half>& x) {
+    const float2 a = __half22float2(__halves2half2(x.v[0], x.v[1]));
+    const float2 b = __half22float2(__halves2half2(x.v[2], x.v[3]));
+    R4<float> r;
+    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = b.x; r.v[3] = b.y;
+    return r;
+  }
+  static __device__ __forceinline__ R4<__half> out(const R4<float>& x) {
+    const __half2 a = __floats2half2_rn(x.v[0], x.v[1]), b = __floats2half2_rn(x.v[2], x.v[3]);
+    R4<__half> r;
+    r.v[0] = __low2half(a); r.v[1] = __high2half(a); r.v[2] = __low2half(b); r.v[3] = __high2half(b);
+    return r;
+  }
+};
+template <>
+struct Cvt<float, __nv_bfloat16> {
+  static __device__ __forceinline__ R4<float> in(const R4<__nv_bfloat16>& x) {
+    R4<float> r;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r.v[i] = __bfloat162float(x.v[i]);
+    return r;
+  }
+  static __device__ __forceinline__ R4<__nv_bfloat16> out(const R4<float>& x) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(x.v[0], x.v[1]), b = __floats2bfloat162_rn(x.v[2], x.v[3]);
+    R4<__nv_bfloat16> r;
+    r.v[0] = __low2bfloat16(a); r.v[1] = __high2bfloat16(a); r.v[2] = __low2bfloat16(b); r.v[3] = __high2bfloat16(b);
+    return r;
+  }
+};
+
+// read-only load of a stored 4-tuple
+template <typename St>
+__device__ __forceinline__ R4<St> ldgs(const R4<St>* p) {
+  if constexpr (sizeof(R4<St>) == 8) {
+    const uint2 t = __ldg(reinterpret_cast<const uint2*>(p));
+    R4<St> r;
+    static_assert(sizeof(r) == sizeof(t), "8-byte tuple");
+    __builtin_memcpy(&r, &t, sizeof(t));
+    return r;
+  } else {
+    return ldg4(p);
+  }
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// asynchronous copy of one stored 4-tuple (8, 16 or 32 bytes)
+template <typename St>
+__device__ __forceinline__ void cp_async_s4(R4<St>* dst, const R4<St>* src) {
+  if constexpr (sizeof(R4<St>) == 8) cp_async8(dst, src);
+  else cp_async_r4(dst, src);
+}
+
 // 2x2 spinor potential (Eq. hloc): [[pv + bz, bx - i by], [bx + i by, pv - bz]] u
 template <typename Real>
 __device__ __forceinline__ void add_potential(R4<Real>& acc, const R4<Real>& pot, const R4<Real>& u) {

@@ -2,6 +2,8 @@
 // mass scalings, the R-ChFSI recovery Y = D^{-1} Z_q + X Lambda_q (Algorithm
 // 1), FP64 -> FP32 shadows, column norms, Lanczos vector updates, and the
 // node-level bilinear derivative reductions of the adjoint.
+#include <type_traits>
+
 #include "internal.h"
 
 namespace rcf {
@@ -114,6 +116,66 @@ __global__ void colnorm2_kernel(int64_t rows, const double* __restrict__ x, int6
     s += a.x * a.x + a.y * a.y;
   }
   block_atomic_add(s, nrm2 + v);
+}
+
+// column norms^2 of a complex64 block (accumulated in FP64)
+__global__ void colnorm2_f32_kernel(int64_t rows, const float* __restrict__ x, int64_t ldx, double* nrm2) {
+  const int v = blockIdx.y;
+  const float2* xv = reinterpret_cast<const float2*>(x + 2 * int64_t(v) * ldx);
+  double s = 0.0;
+  for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    const float2 a = xv[r];
+    s += double(a.x) * a.x + double(a.y) * a.y;
+  }
+  block_atomic_add(s, nrm2 + v);
+}
+
+// scale[v] = ||x_v|| (1 for a zero column), inv[v] = 1 / scale[v]
+__global__ void norm_scale_kernel(const double* __restrict__ nrm2, int n, double* __restrict__ scale,
+                                  float* __restrict__ inv) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  const double s = nrm2[v] > 0.0 ? sqrt(nrm2[v]) : 1.0;
+  scale[v] = s;
+  inv[v] = float(1.0 / s);
+}
+
+// y = x * inv[v], rounded to the storage type
+template <typename St>
+__global__ void to_storage_kernel(int64_t rows, const float* __restrict__ x, int64_t ldx,
+                                  const float* __restrict__ inv, St* __restrict__ y, int64_t ldy) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (r >= rows) return;
+  const float2 a = reinterpret_cast<const float2*>(x + 2 * int64_t(v) * ldx)[r];
+  const float s = inv[v];
+  St* o = y + 2 * int64_t(v) * ldy + 2 * r;
+  if constexpr (std::is_same_v<St, __half>) {
+    *reinterpret_cast<__half2*>(o) = __floats2half2_rn(a.x * s, a.y * s);
+  } else {
+    *reinterpret_cast<__nv_bfloat162*>(o) = __floats2bfloat162_rn(a.x * s, a.y * s);
+  }
+}
+
+// Y = D^{-1} Z zscale[v] + X lam[v] with Z stored in a 16-bit type
+template <typename St>
+__global__ void recover_scaled_kernel(const float* __restrict__ invm, int64_t rows, const St* __restrict__ Z,
+                                      int64_t ldz, const double* __restrict__ zscale,
+                                      const double* __restrict__ X, int64_t ldx,
+                                      const double* __restrict__ lam, double* __restrict__ Y, int64_t ldy) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (r >= rows) return;
+  const St* zp = Z + 2 * int64_t(v) * ldz + 2 * r;
+  float2 z;
+  if constexpr (std::is_same_v<St, __half>) z = __half22float2(*reinterpret_cast<const __half2*>(zp));
+  else z = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(zp));
+  const double d = double(invm[r >> 1]) * zscale[v];
+  const double2 xv = reinterpret_cast<const double2*>(X + 2 * int64_t(v) * ldx)[r];
+  const double l = lam[v];
+  reinterpret_cast<double2*>(Y + 2 * int64_t(v) * ldy)[r] =
+      make_double2(fma(l, xv.x, d * z.x), fma(l, xv.y, d * z.y));
 }
 
 __global__ void sqrt_kernel(double* v, int n) {
@@ -263,6 +325,49 @@ int launch_copy_c128(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, i
   RCF_CHECK_LAUNCH(ctx);
   return RCF_OK;
 }
+
+int launch_colnorm2_f32(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec, double* nrm2) {
+  if (nvec <= 0) return RCF_OK;
+  const unsigned nb = unsigned(std::min<int64_t>(blocks_for(rows), 152));
+  colnorm2_f32_kernel<<<dim3(nb, nvec), kThreads, 0, ctx->stream>>>(rows, x, ldx, nrm2);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+
+int launch_norm_scale(rcf_ctx* ctx, const double* nrm2, int n, double* scale, float* inv) {
+  if (n <= 0) return RCF_OK;
+  norm_scale_kernel<<<unsigned((n + 127) / 128), 128, 0, ctx->stream>>>(nrm2, n, scale, inv);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+
+template <typename St>
+int launch_to_storage(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec, const float* inv,
+                      St* y, int64_t ldy) {
+  if (nvec <= 0) return RCF_OK;
+  to_storage_kernel<St><<<dim3(blocks_for(rows), nvec), kThreads, 0, ctx->stream>>>(rows, x, ldx, inv, y, ldy);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+template int launch_to_storage<__half>(rcf_ctx*, int64_t, const float*, int64_t, int, const float*, __half*, int64_t);
+template int launch_to_storage<__nv_bfloat16>(rcf_ctx*, int64_t, const float*, int64_t, int, const float*,
+                                              __nv_bfloat16*, int64_t);
+
+template <typename St>
+int launch_recover_scaled(rcf_ctx* ctx, const rcf_mesh* m, const St* Z, int64_t ldz, const double* zscale,
+                          const double* X, int64_t ldx, const double* lam, int nvec, double* Y, int64_t ldy) {
+  if (nvec <= 0) return RCF_OK;
+  const int64_t rows = 2 * m->nnodes;
+  recover_scaled_kernel<St><<<dim3(blocks_for(rows), nvec), kThreads, 0, ctx->stream>>>(
+      m->d_inv_mass32, rows, Z, ldz, zscale, X, ldx, lam, Y, ldy);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+template int launch_recover_scaled<__half>(rcf_ctx*, const rcf_mesh*, const __half*, int64_t, const double*,
+                                           const double*, int64_t, const double*, int, double*, int64_t);
+template int launch_recover_scaled<__nv_bfloat16>(rcf_ctx*, const rcf_mesh*, const __nv_bfloat16*, int64_t,
+                                                  const double*, const double*, int64_t, const double*, int,
+                                                  double*, int64_t);
 
 int launch_colnorm2(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, int nvec,
                     double* nrm2) {

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librchfsi.so")
 
 RCF_OK, RCF_EINVAL, RCF_ENOMEM, RCF_ECUDA, RCF_ENOTSPD, RCF_ETIMEOUT, RCF_ENOTSUP = range(7)
-RCF_FP64, RCF_FP32, RCF_FP32_DF = 0, 1, 2
+RCF_FP64, RCF_FP32, RCF_FP32_DF, RCF_FP16, RCF_BF16 = 0, 1, 2, 3, 4
 RCF_CHFSI, RCF_RCHFSI = 0, 1
 RCF_FORM_H, RCF_FORM_DINV_H, RCF_FORM_H_DINV = 0, 1, 2
 RCF_STEP_CPASYNC, RCF_STEP_TMA = 0, 1
@@ -238,11 +238,27 @@ def rcf_projector_support(op, atom: int) -> np.ndarray:
 
 # ---- compute -----------------------------------------------------------------------
 
-def rcf_apply(ctx, op, form: int, X, Y, prec: int = RCF_FP64):
+def _dev_mv(t, prec: int, name: str):
+    """(pointer, ld in complex elements) of a device multivector of precision prec: complex128
+    (FP64), complex64 (FP32), complex32 or float16 with interleaved (re, im) (FP16), bfloat16
+    with interleaved (re, im) (BF16); shape (nvec, rows) for complex, (nvec, 2 rows) for real."""
     import torch
-    dt = torch.complex128 if prec == RCF_FP64 else torch.complex64
-    px, ldx = _dev(X, dt, "X")
-    py, ldy = _dev(Y, dt, "Y")
+    if prec == RCF_FP64:
+        return _dev(t, torch.complex128, name)
+    if prec == RCF_FP32:
+        return _dev(t, torch.complex64, name)
+    if prec == RCF_FP16 and t.dtype == torch.complex32:
+        return _dev(t, torch.complex32, name)
+    dt = torch.float16 if prec == RCF_FP16 else torch.bfloat16
+    p, ld = _dev(t, dt, name)
+    if t.dim() == 2 and ld % 2:
+        raise ValueError(f"{name}: interleaved (re, im) rows need an even row stride")
+    return p, ld // 2 if t.dim() == 2 else ld // 2
+
+
+def rcf_apply(ctx, op, form: int, X, Y, prec: int = RCF_FP64):
+    px, ldx = _dev_mv(X, prec, "X")
+    py, ldy = _dev_mv(Y, prec, "Y")
     nvec = X.shape[0] if X.dim() == 2 else 1
     _check(ctx, lib().rcf_apply(ctx, op, form, px, ldx, nvec, py, ldy, prec))
 
@@ -362,14 +378,12 @@ def rcf_adjoint_filter(ctx, op, X, ritz, degree: int, bounds, mode: int, prec: i
 def rcf_cheb_step(ctx, op, form: int, prec: int, Zk, Zkm1, R, alpha: float, beta: float, gamma: float,
                   g, out):
     """out = alpha op(Zk) + beta Zk + gamma Zkm1 + g[v] R (tensors of shape (nvec, rows))."""
-    import torch
-    dt = torch.complex128 if prec == RCF_FP64 else torch.complex64
-    pz, ld = _dev(Zk, dt, "Zk")
-    po, ldo = _dev(out, dt, "out")
+    pz, ld = _dev_mv(Zk, prec, "Zk")
+    po, ldo = _dev_mv(out, prec, "out")
     if ldo != ld:
         raise ValueError("Zk and out must share the leading dimension")
-    pm = None if Zkm1 is None else _dev(Zkm1, dt, "Zkm1")[0]
-    pr = None if R is None else _dev(R, dt, "R")[0]
+    pm = None if Zkm1 is None else _dev_mv(Zkm1, prec, "Zkm1")[0]
+    pr = None if R is None else _dev_mv(R, prec, "R")[0]
     pg = None if g is None else ctypes.c_void_p(g.data_ptr())
     _check(ctx, lib().rcf_cheb_step(ctx, op, int(form), int(prec), pz, pm, pr, ld, Zk.shape[0],
                                     float(alpha), float(beta), float(gamma), pg, po))

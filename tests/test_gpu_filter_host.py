@@ -23,7 +23,8 @@ def pr():
     p.close()
 
 
-@pytest.mark.parametrize("mode,prec", [(1, 2), (1, 1), (0, 0)], ids=["rchfsi-fp32df", "rchfsi-fp32", "chfsi-fp64"])
+@pytest.mark.parametrize("mode,prec", [(1, 2), (1, 1), (0, 0), (1, 3), (1, 4)],
+                         ids=["rchfsi-fp32df", "rchfsi-fp32", "chfsi-fp64", "rchfsi-fp16", "rchfsi-bf16"])
 @pytest.mark.parametrize("block", [0, 12, 32])
 @pytest.mark.parametrize("pinned", [True, False], ids=["pinned", "pageable"])
 def test_host_filter_equals_device_filter(pr, mode, prec, block, pinned):
