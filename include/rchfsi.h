@@ -62,8 +62,9 @@ typedef enum { RCF_FP64 = 0, RCF_FP32 = 1, RCF_FP32_DF = 2, RCF_FP16 = 3, RCF_BF
  * multivectors are 16-bit complex pairs): the recurrence vectors Z_k, Z_{k-1}
  * and R are STORED as IEEE binary16 / bfloat16 pairs and the products are
  * computed in FP32 from them; R is the double-float residual, each column
- * scaled to unit norm before rounding (the recurrence is linear in (Z, R), so
- * the scale returns exactly in the recovery).  This halves the bytes per step
+ * scaled by the power of two that puts its largest entry in [1/2, 1) before
+ * rounding (the recurrence is linear in (Z, R), so the scale returns exactly
+ * in the recovery; results are reproducible bit for bit).  This halves the bytes per step
  * of the bandwidth-bound recurrence; the residual-proportional error bound
  * that lets the paper run the products in FP32/TF32 (Section III-C) covers the
  * 16-bit rounding of the stored vectors as well, since that error too scales

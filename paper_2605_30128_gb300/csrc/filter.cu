@@ -296,9 +296,10 @@ int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const do
 }
 
 // R-ChFSI with the recurrence vectors Z_k, Z_{k-1} and R stored in a 16-bit float type
-// (FP32 arithmetic): the residual in double-float arithmetic, each column of R scaled to
-// unit norm before rounding (the recurrence is linear in (Z, R), so the scale returns in
-// the recovery), q >= 2.
+// (FP32 arithmetic): the residual in double-float arithmetic, each column of R scaled by
+// the power of two that puts its largest entry in [1/2, 1) before rounding (exact, and
+// independent of summation order; the recurrence is linear in (Z, R), so the scale
+// returns exactly in the recovery), q >= 2.
 template <typename St>
 int rchfsi_block16(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
                    int nvec, const double* lam_h, double* Y, int64_t ldy) {
@@ -322,14 +323,15 @@ int rchfsi_block16(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const 
   float* R32 = nullptr;
   RCF_TRY(workspace(ctx, WS_R32, sizeof(float) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R32)));
   RCF_TRY(launch_residual_df(ctx, op, X, ldx, nvec, tab_d, R32, nullptr, ld));
-  double* sc = nullptr;   // [nrm2 | scale] doubles, then [inv] floats
-  RCF_TRY(workspace(ctx, WS_SCALE, (2 * sizeof(double) + sizeof(float)) * size_t(nvec), reinterpret_cast<void**>(&sc)));
-  double* nrm2 = sc;
-  double* scale = sc + nvec;
-  float* inv = reinterpret_cast<float*>(sc + 2 * nvec);
-  RCF_CUDA(ctx, cudaMemsetAsync(nrm2, 0, sizeof(double) * nvec, ctx->stream));
-  RCF_TRY(launch_colnorm2_f32(ctx, rows, R32, ld, nvec, nrm2));
-  RCF_TRY(launch_norm_scale(ctx, nrm2, nvec, scale, inv));
+  double* sc = nullptr;   // [scale] doubles, then [inv] floats, then [column max] bits
+  RCF_TRY(workspace(ctx, WS_SCALE, (sizeof(double) + sizeof(float) + sizeof(unsigned)) * size_t(nvec),
+                    reinterpret_cast<void**>(&sc)));
+  double* scale = sc;
+  float* inv = reinterpret_cast<float*>(sc + nvec);
+  unsigned* cmax = reinterpret_cast<unsigned*>(inv + nvec);
+  RCF_CUDA(ctx, cudaMemsetAsync(cmax, 0, sizeof(unsigned) * nvec, ctx->stream));
+  RCF_TRY(launch_colmax_f32(ctx, rows, R32, ld, nvec, cmax));
+  RCF_TRY(launch_pow2_scale(ctx, cmax, nvec, scale, inv));
   St* R = nullptr;
   RCF_TRY(workspace(ctx, WS_R16, sizeof(St) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R)));
   RCF_TRY(launch_to_storage<St>(ctx, rows, R32, ld, nvec, inv, R, ld));

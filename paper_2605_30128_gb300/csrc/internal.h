@@ -215,11 +215,11 @@ int launch_to_c64(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, int 
                   int64_t ldy);
 int launch_colnorm2(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, int nvec,
                     double* nrm2);
-// 16-bit storage of the recurrence: column norms^2 of a complex64 block (nrm2 pre-zeroed),
-// per-column scale = norm (1 for zero columns) and its reciprocal, the scaled copy in the
-// storage type, and the recovery Y = D^{-1} Z zscale[v] + X lam[v]
-int launch_colnorm2_f32(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec, double* nrm2);
-int launch_norm_scale(rcf_ctx* ctx, const double* nrm2, int n, double* scale, float* inv);
+// 16-bit storage of the recurrence: per-column largest modulus of a complex64 block (as
+// float bits; cmax pre-zeroed), the power-of-two scale above it and its reciprocal, the
+// scaled copy in the storage type, and the recovery Y = D^{-1} Z zscale[v] + X lam[v]
+int launch_colmax_f32(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec, unsigned* cmax);
+int launch_pow2_scale(rcf_ctx* ctx, const unsigned* cmax, int n, double* scale, float* inv);
 template <typename St>
 int launch_to_storage(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec, const float* inv,
                       St* y, int64_t ldy);

@@ -118,27 +118,38 @@ __global__ void colnorm2_kernel(int64_t rows, const double* __restrict__ x, int6
   block_atomic_add(s, nrm2 + v);
 }
 
-// column norms^2 of a complex64 block (accumulated in FP64)
-__global__ void colnorm2_f32_kernel(int64_t rows, const float* __restrict__ x, int64_t ldx, double* nrm2) {
+// per column the largest modulus of any real or imaginary part of a complex64 block, as float
+// bits (non-negative floats order like their bit patterns, so atomicMax is exact and the
+// result does not depend on the order of the updates); cmax pre-zeroed
+__global__ void colmax_f32_kernel(int64_t rows, const float* __restrict__ x, int64_t ldx,
+                                  unsigned* __restrict__ cmax) {
   const int v = blockIdx.y;
   const float2* xv = reinterpret_cast<const float2*>(x + 2 * int64_t(v) * ldx);
-  double s = 0.0;
+  float m = 0.f;
   for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < rows;
        r += int64_t(gridDim.x) * blockDim.x) {
     const float2 a = xv[r];
-    s += double(a.x) * a.x + double(a.y) * a.y;
+    m = fmaxf(m, fmaxf(fabsf(a.x), fabsf(a.y)));
   }
-  block_atomic_add(s, nrm2 + v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(cmax + v, __float_as_uint(m));
 }
 
-// scale[v] = ||x_v|| (1 for a zero column), inv[v] = 1 / scale[v]
-__global__ void norm_scale_kernel(const double* __restrict__ nrm2, int n, double* __restrict__ scale,
+// scale[v] = 2^e with the column maximum in [2^(e-1), 2^e) (1 for a zero or non-finite
+// column), inv[v] = 2^-e: exact scalings, so the scaled values lie in (-1, 1)
+__global__ void pow2_scale_kernel(const unsigned* __restrict__ cmax, int n, double* __restrict__ scale,
                                   float* __restrict__ inv) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n) return;
-  const double s = nrm2[v] > 0.0 ? sqrt(nrm2[v]) : 1.0;
-  scale[v] = s;
-  inv[v] = float(1.0 / s);
+  const float m = __uint_as_float(cmax[v]);
+  int e = 0;
+  if (m > 0.f && m <= 3.4e38f) {
+    frexpf(m, &e);   // m = f 2^e, f in [1/2, 1)
+    e = e < -120 ? -120 : (e > 120 ? 120 : e);
+  }
+  scale[v] = ldexp(1.0, e);
+  inv[v] = ldexpf(1.0f, -e);
 }
 
 // y = x * inv[v], rounded to the storage type
@@ -326,17 +337,17 @@ int launch_copy_c128(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, i
   return RCF_OK;
 }
 
-int launch_colnorm2_f32(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec, double* nrm2) {
+int launch_colmax_f32(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec, unsigned* cmax) {
   if (nvec <= 0) return RCF_OK;
   const unsigned nb = unsigned(std::min<int64_t>(blocks_for(rows), 152));
-  colnorm2_f32_kernel<<<dim3(nb, nvec), kThreads, 0, ctx->stream>>>(rows, x, ldx, nrm2);
+  colmax_f32_kernel<<<dim3(nb, nvec), kThreads, 0, ctx->stream>>>(rows, x, ldx, cmax);
   RCF_CHECK_LAUNCH(ctx);
   return RCF_OK;
 }
 
-int launch_norm_scale(rcf_ctx* ctx, const double* nrm2, int n, double* scale, float* inv) {
+int launch_pow2_scale(rcf_ctx* ctx, const unsigned* cmax, int n, double* scale, float* inv) {
   if (n <= 0) return RCF_OK;
-  norm_scale_kernel<<<unsigned((n + 127) / 128), 128, 0, ctx->stream>>>(nrm2, n, scale, inv);
+  pow2_scale_kernel<<<unsigned((n + 127) / 128), 128, 0, ctx->stream>>>(cmax, n, scale, inv);
   RCF_CHECK_LAUNCH(ctx);
   return RCF_OK;
 }
