@@ -87,31 +87,36 @@ struct Cvt<R, R> {
 template <>
 struct Cvt<float, __half> {
   static __device__ __forceinline__ R4<float> in(const R4<__half>& x) {
-    const float2 a = __half22float2(__halves2half2(x.v[0], x.v[1]));
-    const float2 b = __half22float2(__halves2half2(x.v[2], x.v[3]));
+    const __half2* h = reinterpret_cast<const __half2*>(&x);   // the tuple is two half2 words
+    const float2 a = __half22float2(h[0]);
+    const float2 b = __half22float2(h[1]);
     R4<float> r;
     r.v[0] = a.x; r.v[1] = a.y; r.v[2] = b.x; r.v[3] = b.y;
     return r;
   }
   static __device__ __forceinline__ R4<__half> out(const R4<float>& x) {
-    const __half2 a = __floats2half2_rn(x.v[0], x.v[1]), b = __floats2half2_rn(x.v[2], x.v[3]);
     R4<__half> r;
-    r.v[0] = __low2half(a); r.v[1] = __high2half(a); r.v[2] = __low2half(b); r.v[3] = __high2half(b);
+    __half2* h = reinterpret_cast<__half2*>(&r);
+    h[0] = __floats2half2_rn(x.v[0], x.v[1]);
+    h[1] = __floats2half2_rn(x.v[2], x.v[3]);
     return r;
   }
 };
 template <>
 struct Cvt<float, __nv_bfloat16> {
   static __device__ __forceinline__ R4<float> in(const R4<__nv_bfloat16>& x) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&x);
+    const float2 a = __bfloat1622float2(h[0]);
+    const float2 b = __bfloat1622float2(h[1]);
     R4<float> r;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) r.v[i] = __bfloat162float(x.v[i]);
+    r.v[0] = a.x; r.v[1] = a.y; r.v[2] = b.x; r.v[3] = b.y;
     return r;
   }
   static __device__ __forceinline__ R4<__nv_bfloat16> out(const R4<float>& x) {
-    const __nv_bfloat162 a = __floats2bfloat162_rn(x.v[0], x.v[1]), b = __floats2bfloat162_rn(x.v[2], x.v[3]);
     R4<__nv_bfloat16> r;
-    r.v[0] = __low2bfloat16(a); r.v[1] = __high2bfloat16(a); r.v[2] = __low2bfloat16(b); r.v[3] = __high2bfloat16(b);
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&r);
+    h[0] = __floats2bfloat162_rn(x.v[0], x.v[1]);
+    h[1] = __floats2bfloat162_rn(x.v[2], x.v[3]);
     return r;
   }
 };
