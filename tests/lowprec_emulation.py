@@ -1,0 +1,40 @@
+"""CPU emulation of the R-ChFSI filter with its recurrence vectors stored in 16 bits (test helper).
+
+Z_k, Z_{k-1} and R are rounded to binary16 / bfloat16 (round to nearest even) each time they are
+stored, R scaled per column by the power of two that puts its largest entry in [1/2, 1); the
+arithmetic is FP64, so the difference from the oracle's filter is the storage rounding alone.
+It mirrors the recurrence of the library's RCF_FP16 / RCF_BF16 filters and is the source of the
+error scales their GPU tests allow (it uses the oracle's building blocks, not the GPU code).
+"""
+import numpy as np
+
+from oracle.chebyshev import filter_scalars, ritz_filter_values
+
+
+def round16(x: np.ndarray, fmt: str) -> np.ndarray:
+    """Real and imaginary parts rounded to binary16 ('fp16') or bfloat16 ('bf16')."""
+    def one(a):
+        if fmt == "fp16":
+            return a.astype(np.float16).astype(np.float64)
+        f = a.astype(np.float32)
+        b = f.view(np.uint32).astype(np.uint64)
+        b = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)   # RNE to the top 16 bits
+        return b.view(np.float32).astype(np.float64)
+    return one(np.real(x)) + 1j * one(np.imag(x))
+
+
+def rchfsi_filter_16(Hop, X, lam, lmin, lT, lmax, q, fmt):
+    c, e, sigma = filter_scalars(lmin, lT, lmax, q)
+    lam = np.asarray(lam, dtype=np.float64)
+    Dinv = 1.0 / Hop.Mdiag[:, None]
+    R = Hop.apply(X) - Hop.Mdiag[:, None] * X * lam[None, :]
+    m = np.max(np.maximum(np.abs(R.real), np.abs(R.imag)), axis=0)
+    s = np.where(m > 0, 2.0 ** (np.floor(np.log2(np.where(m > 0, m, 1.0))) + 1), 1.0)
+    Rs = round16(R / s[None, :], fmt)
+    Lk = ritz_filter_values(lam, lmin, lT, lmax, q)
+    Zprev, Z = np.zeros_like(X), round16((sigma[1] / e) * Rs, fmt)
+    for k in range(1, q):
+        a = 2.0 * sigma[k + 1] / e
+        Zn = a * Hop.apply(Dinv * Z) - a * c * Z - sigma[k] * sigma[k + 1] * Zprev + a * Rs * Lk[k][None, :]
+        Zprev, Z = Z, round16(Zn, fmt)
+    return Dinv * Z * s[None, :] + X * Lk[q][None, :]

@@ -7,9 +7,10 @@ binary16 / bfloat16 pairs, products in FP32, against the FP64 oracle.
   that distance of a rounding boundary match exactly; >= 99 % here) without projectors, and within
   one 16-bit ulp of the magnitude scale with them (the spin-orbit add-back rounds a second time).
 - The filter: its error against the oracle's FP64 filter falls with ||R|| (residual-proportional,
-  the property R-ChFSI rests on).  Expected scale from a CPU emulation of 16-bit storage with exact
-  arithmetic on this workload: 9.8e-7 / 9.8e-10 (FP16) and 7.0e-6 / 7.0e-9 (BF16) at perturbations
-  1e-3 / 1e-6 of an eigenvector block; the bounds below allow 5x.
+  the property R-ChFSI rests on).  Expected scale from the CPU emulation of 16-bit storage with exact
+  arithmetic on this workload (tests/lowprec_emulation.py, pinned in tests/test_oracle_lowprec.py):
+  9.8e-7 / 9.8e-10 (FP16) and 7.0e-6 / 7.0e-9 (BF16) at perturbations 1e-3 / 1e-6 of an
+  eigenvector block; the bounds below allow 5x.
 - The eigensolver loop reaches the oracle's eigenvalues within 1e-7 Ha (in
   test_gpu_filters.py and here for both 16-bit formats).
 """

@@ -1,0 +1,70 @@
+"""The R-ChFSI property behind the 16-bit storage variants, on the CPU: with Z_k, Z_{k-1} and R
+rounded to 16 bits whenever stored (exact FP64 arithmetic otherwise, tests/lowprec_emulation.py),
+the filter's error against the oracle's FP64 filter falls in proportion to the residual.  On the
+4^3-cell workload near an eigenvector block (perturbations 1e-3 and 1e-6) the errors are about
+9.8e-7 / 9.8e-10 (binary16) and 7.0e-6 / 7.0e-9 (bfloat16): the scales the GPU tests of RCF_FP16 /
+RCF_BF16 allow with a factor 5.  A 16-bit rounding of the stored vectors alone, without the
+residual form (plain ChFSI with 16-bit storage of Y_k), keeps an error near the 16-bit epsilon."""
+import numpy as np
+import pytest
+
+import workloads
+from lowprec_emulation import rchfsi_filter_16, round16
+from oracle import chfsi_filter, lanczos_bounds, rayleigh_ritz, rchfsi_eigensolver, rchfsi_filter
+from oracle.chebyshev import filter_scalars
+from oracle_cases import build_oracle
+
+
+def test_round16_is_round_to_nearest_even():
+    x = np.array([1.0, 1.0 + 2 ** -11, 1.0 + 3 * 2 ** -11, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -1.5e-3])
+    f16 = round16(x, "fp16").real
+    assert f16[1] == 1.0 and f16[2] == 1.0 + 2 ** -9       # ties to even at half a binary16 ulp
+    b16 = round16(x, "bf16").real
+    assert b16[3] == 1.0 and b16[4] == 1.0 + 2 ** -6       # ties to even at half a bfloat16 ulp
+    assert abs(b16[5] + 1.5e-3) <= 2 ** -8 * 1.5e-3         # half an ulp: at most 2^-8 relative
+    assert np.all(round16(f16, "fp16").real == f16)         # idempotent
+
+
+@pytest.fixture(scope="module")
+def near_converged():
+    w = workloads.workload("cfg1")
+    H, *_ = build_oracle(w)
+    X, _ = rayleigh_ritz(H, workloads.complex_normal(w.seed + 100, (H.N, w.nvec)))
+    v0 = workloads.complex_normal(w.seed + 200, H.N)
+    lo, hi, *_ = lanczos_bounds(H, v0, w.lanczos)
+    Xc, lam_c, _ = rchfsi_eigensolver(H, X, q=10, lmax=hi, tol=1e-11, max_cycles=80, nwanted=28)
+    b = (float(lam_c.min()), float(lam_c.max()), hi)
+    return H, Xc, lam_c, b, workloads.complex_normal(77, Xc.shape)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("fmt,lo,hi", [("fp16", 4e-7, 2e-6), ("bf16", 3e-6, 1.5e-5)])
+def test_16bit_storage_error_is_residual_proportional(near_converged, fmt, lo, hi):
+    H, Xc, lam, b, noise = near_converged
+    errs = []
+    for delta in (1e-3, 1e-6):
+        X = Xc + delta * noise / np.linalg.norm(noise) * np.linalg.norm(Xc)
+        ref = rchfsi_filter(H, X, lam, *b, 10)
+        errs.append(_rel(rchfsi_filter_16(H, X, lam, *b, 10, fmt)[:, :28], ref[:, :28]))
+    assert lo < errs[0] < hi
+    assert 0.5e-3 < errs[1] / errs[0] < 2e-3                  # scales with the perturbation
+
+
+def test_16bit_storage_without_residual_form_keeps_its_floor(near_converged):
+    """ChFSI with Y_k stored in binary16: the error does not fall with the perturbation."""
+    H, Xc, lam, b, noise = near_converged
+    c, e, sigma = filter_scalars(*b, 10)
+    Minv = 1.0 / H.Mdiag[:, None]
+    errs = []
+    for delta in (1e-3, 1e-6):
+        X = Xc + delta * noise / np.linalg.norm(noise) * np.linalg.norm(Xc)
+        ref = chfsi_filter(H, X, *b, 10)
+        Yp, Y = round16(X, "fp16"), round16((sigma[1] / e) * (Minv * H.apply(X) - c * X), "fp16")
+        for k in range(1, 10):
+            a = 2.0 * sigma[k + 1] / e
+            Yp, Y = Y, round16(a * (Minv * H.apply(Y) - c * Y) - sigma[k] * sigma[k + 1] * Yp, "fp16")
+        errs.append(_rel(Y[:, :28], ref[:, :28]))
+    assert errs[1] > 0.3 * errs[0] > 1e-5
