@@ -182,6 +182,16 @@ int64_t rcf_launch_count(const rcf_ctx* ctx);
  * RCF_EINVAL for an unknown kind.  Takes effect at the next launch. */
 int rcf_set_step_kernel(rcf_ctx* ctx, int kind);
 
+/* Arithmetic of the Gram matrix of Cholesky-QR and of the projected matrix
+ * Y^H H Y of Rayleigh-Ritz (library-specific; the paper has no counterpart).
+ * RCF_RR_FP64 (default): cuBLAS ZHERK / ZGEMM in FP64.  RCF_RR_DF: this
+ * library's split-K GEMM in double-float arithmetic on the FP32 pipes (about
+ * 2^-46 relative to the magnitudes of the terms), for GPUs whose FP64 rate is a
+ * small fraction of their FP32 rate.  The triangular solves, the eigensolve
+ * and the rotation stay FP64. */
+typedef enum { RCF_RR_FP64 = 0, RCF_RR_DF = 1 } rcf_rr_arith;
+int rcf_set_rr_arith(rcf_ctx* ctx, int kind);
+
 /* ---- filter bounds (Section III-B-2; Lanczos as in Section III-C-1) --- */
 
 /* nsteps of Lanczos on D^{-1/2} H D^{-1/2} from the device c128 vector v0

@@ -223,6 +223,13 @@ extern "C" int rcf_set_step_kernel(rcf_ctx* ctx, int kind) {
   return RCF_OK;
 }
 
+extern "C" int rcf_set_rr_arith(rcf_ctx* ctx, int kind) {
+  if (!ctx) return RCF_EINVAL;
+  if (kind != RCF_RR_FP64 && kind != RCF_RR_DF) return fail(ctx, RCF_EINVAL, "unknown Rayleigh-Ritz arithmetic %d", kind);
+  ctx->rr_arith = kind;
+  return RCF_OK;
+}
+
 extern "C" int rcf_destroy(rcf_ctx* ctx) {
   if (!ctx) return RCF_OK;
   cudaStreamSynchronize(ctx->stream);

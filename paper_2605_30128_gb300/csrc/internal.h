@@ -39,6 +39,7 @@ struct rcf_ctx {
   int64_t launches = 0;     // kernels launched by this library on this context
   int* d_err = nullptr;     // device error word: set by a kernel whose bounded wait timed out
   int step_kernel = RCF_STEP_CPASYNC;   // FP32 step kernel (rcf_set_step_kernel)
+  int rr_arith = RCF_RR_FP64;           // Gram / projection GEMMs (rcf_set_rr_arith)
   cudaStream_t copy_in = nullptr;       // host-to-device and device-to-host streams of
   cudaStream_t copy_out = nullptr;      // rcf_filter_host (created on first use)
   // grow-only scratch buffers, one per slot
@@ -131,7 +132,7 @@ int workspace(rcf_ctx* ctx, int slot, size_t bytes, void** out);
 enum WsSlot {
   WS_R64 = 0, WS_R32, WS_ZA, WS_ZB, WS_COEF, WS_NLC, WS_NLC2, WS_LANCZOS, WS_RR_W, WS_RR_S,
   WS_RR_T, WS_RR_INFO, WS_RR_WORK, WS_GRAD, WS_CKPT, WS_ADJ_A, WS_ADJ_B, WS_ADJ_C, WS_ADJ_U,
-  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HY0, WS_R16, WS_SCALE, WS_COUNT
+  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HY0, WS_R16, WS_SCALE, WS_GEMM_PART, WS_COUNT
 };
 
 // ---------------------------------------------------------------------------
@@ -180,6 +181,11 @@ int check_device_error(rcf_ctx* ctx);
 // -lambda (device, FP64).  X c128 [nvec][ldx], Rh/Rl c64 [nvec][ldr].
 int launch_residual_df(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
                        const double* neglam_d, float* Rh, float* Rl, int64_t ldr);
+// C (m x n, column-major, ldc) = A^H diag(w) B for complex FP64 A (K x m), B (K x n), w the
+// weight of complex row k = w[k >> 1] (null: 1), in double-float arithmetic; lower: only
+// the tiles on or below the diagonal of a square C (Hermitian A^H A)  (gemm_df.cu)
+int launch_gemm_tn_df(rcf_ctx* ctx, const double* A, int64_t lda, const double* B, int64_t ldb,
+                      const double* w, int64_t K, int m, int n, int lower, double* C, int64_t ldc);
 // hi[i], lo[i] = double-float split of x[i] (integer operations only)
 int launch_split_f64(rcf_ctx* ctx, int64_t n, const double* x, float* hi, float* lo);
 

@@ -55,6 +55,9 @@ const char* cublas_name(cublasStatus_t s) {
 // S = Y^H M Y  (lower triangle), S: n x n
 int gram(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int n, cuDoubleComplex* S) {
   const int64_t N = 2 * op->mesh->nnodes;
+  if (ctx->rr_arith == RCF_RR_DF)   // lower triangle of Y^H M Y in double-float arithmetic
+    return launch_gemm_tn_df(ctx, Y, ldy, Y, ldy, op->mesh->d_mass, N, n, n, 1,
+                             reinterpret_cast<double*>(S), n);
   int64_t cr = std::max<int64_t>(1024, (int64_t(1) << 26) / std::max(n, 1));   // ~1 GiB chunks
   cr = std::min<int64_t>(cr, N);
   double* W = nullptr;
@@ -153,10 +156,15 @@ int rr_orth(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nv
   for (int c0 = 0; c0 < nvec; c0 += cb) {
     const int nc = std::min(cb, nvec - c0);
     RCF_TRY(rcf_apply(ctx, op, RCF_FORM_H, Y + 2 * int64_t(c0) * ldy, ldy, nc, T, N, RCF_FP64));
-    RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_C, CUBLAS_OP_N, nvec, nc, int(N), &onec,
-                              reinterpret_cast<const cuDoubleComplex*>(Y), int(ldy),
-                              reinterpret_cast<const cuDoubleComplex*>(T), int(N), &zeroc,
-                              A + size_t(c0) * nvec, nvec));
+    if (ctx->rr_arith == RCF_RR_DF) {
+      RCF_TRY(launch_gemm_tn_df(ctx, Y, ldy, T, N, nullptr, N, nvec, nc, 0,
+                                reinterpret_cast<double*>(A + size_t(c0) * nvec), nvec));
+    } else {
+      RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_C, CUBLAS_OP_N, nvec, nc, int(N), &onec,
+                                reinterpret_cast<const cuDoubleComplex*>(Y), int(ldy),
+                                reinterpret_cast<const cuDoubleComplex*>(T), int(N), &zeroc,
+                                A + size_t(c0) * nvec, nvec));
+    }
   }
   double* w = nullptr;
   int* info = nullptr;

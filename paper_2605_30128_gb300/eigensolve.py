@@ -50,7 +50,7 @@ class Timer:
         return out, self.e0.elapsed_time(self.e1)
 
 
-def run(w, runs, cycles, tol, nwanted, seed=0, device=0):
+def run(w, runs, cycles, tol, nwanted, seed=0, device=0, rr_arith=None):
     import torch
     dev = torch.device("cuda", device)
     torch.cuda.set_device(dev)
@@ -58,6 +58,8 @@ def run(w, runs, cycles, tol, nwanted, seed=0, device=0):
     tm = Timer(torch, stream)
     prob = GPUProblem(w, device=device, stream=stream)
     ctx, op = prob.ctx, prob.op
+    if rr_arith is not None:
+        R.rcf_set_rr_arith(ctx, rr_arith)
     N, nvec = prob.N, w.nvec
     gen = torch.Generator(device=dev)
     gen.manual_seed(w.seed + 100 + seed)
@@ -139,6 +141,8 @@ def main(argv=None):
     ap.add_argument("--nwanted", type=int, default=None,
                     help="wanted vectors (default: all but a buffer of max(4, nvec/10))")
     ap.add_argument("--runs", default="rchfsi_fp32_df,rchfsi_fp32,chfsi_fp64")
+    ap.add_argument("--rr", default="fp64", choices=["fp64", "df"],
+                    help="Gram / projection GEMMs: cuBLAS FP64 or double-float")
     a = ap.parse_args(argv)
     over = {k: v for k, v in (("nvec", a.nvec), ("block", a.block), ("degree", a.degree)) if v}
     w = workloads.workload(a.workload, **over)
@@ -150,7 +154,8 @@ def main(argv=None):
     # FP64 runs first so the others can be compared as they finish
     runs.sort(key=lambda r: RUNS[r][1] != R.RCF_FP64)
     t0 = time.time()
-    out = run(w, runs, a.cycles, a.tol, nw)
+    out = run(w, runs, a.cycles, a.tol, nw, rr_arith=R.RCF_RR_DF if a.rr == "df" else R.RCF_RR_FP64)
+    out["rr_arith"] = a.rr
     out["wall_s"] = time.time() - t0
     print(json.dumps(out), flush=True)
     return 0

@@ -21,6 +21,7 @@ RCF_FP64, RCF_FP32, RCF_FP32_DF, RCF_FP16, RCF_BF16 = 0, 1, 2, 3, 4
 RCF_CHFSI, RCF_RCHFSI = 0, 1
 RCF_FORM_H, RCF_FORM_DINV_H, RCF_FORM_H_DINV = 0, 1, 2
 RCF_STEP_CPASYNC, RCF_STEP_TMA = 0, 1
+RCF_RR_FP64, RCF_RR_DF = 0, 1
 
 EXPORTS = [
     "rcf_create", "rcf_destroy", "rcf_status_string", "rcf_last_error", "rcf_sync",
@@ -30,7 +31,7 @@ EXPORTS = [
     "rcf_apply", "rcf_lanczos_bounds", "rcf_residual", "rcf_filter", "rcf_rayleigh_ritz",
     "rcf_grad_bilinear", "rcf_adjoint_filter", "rcf_cheb_step", "rcf_launch_count",
     "rcf_apply_noalloc", "rcf_set_step_kernel", "rcf_residual_df", "rcf_cholqr2",
-    "rcf_rayleigh_ritz_orth", "rcf_filter_host",
+    "rcf_rayleigh_ritz_orth", "rcf_filter_host", "rcf_set_rr_arith",
 ]
 
 _lib = None
@@ -81,6 +82,7 @@ def lib() -> ctypes.CDLL:
         "rcf_launch_count": (i64, [vp]),
         "rcf_apply_noalloc": (i32, [vp, vp, i32, vp, i64, i32, vp, i64, i32]),
         "rcf_set_step_kernel": (i32, [vp, i32]),
+        "rcf_set_rr_arith": (i32, [vp, i32]),
         "rcf_residual_df": (i32, [vp, vp, vp, i64, i32, vp, vp, vp, i64]),
         "rcf_cholqr2": (i32, [vp, vp, vp, i64, i32]),
         "rcf_filter_host": (i32, [vp, vp, vp, i64, i32, vp, i32, vp, i32, i32, i32, vp, i64]),
@@ -391,6 +393,11 @@ def rcf_cheb_step(ctx, op, form: int, prec: int, Zk, Zkm1, R, alpha: float, beta
 
 def rcf_launch_count(ctx) -> int:
     return int(lib().rcf_launch_count(ctx))
+
+
+def rcf_set_rr_arith(ctx, kind: int) -> None:
+    """Gram / projection GEMMs of this context: RCF_RR_FP64 (cuBLAS, default) or RCF_RR_DF."""
+    _check(ctx, lib().rcf_set_rr_arith(ctx, int(kind)))
 
 
 def rcf_set_step_kernel(ctx, kind: int) -> None:

@@ -98,7 +98,16 @@ def test_rchfsi_fp32_error_scales_with_residual(cfg1):
     assert errs_ch[1] > 1e2 * errs32[1]          # plain FP32 ChFSI keeps its eps_32 floor
 
 
-def test_rayleigh_ritz_matches_oracle(cfg1):
+@pytest.fixture(params=[0, 1], ids=["rr-fp64", "rr-df"])
+def rr_arith(request, cfg1):
+    """Run with the cuBLAS FP64 and the double-float Gram / projection GEMMs."""
+    from paper_2605_30128_gb300 import rchfsi as R
+    R.rcf_set_rr_arith(cfg1.g.ctx, request.param)
+    yield request.param
+    R.rcf_set_rr_arith(cfg1.g.ctx, R.RCF_RR_FP64)
+
+
+def test_rayleigh_ritz_matches_oracle(cfg1, rr_arith):
     import torch
     from paper_2605_30128_gb300 import rchfsi as R
     H = cfg1.H
@@ -116,7 +125,7 @@ def test_rayleigh_ritz_matches_oracle(cfg1):
     assert np.max(np.abs(s - 1.0)) < 1e-9
 
 
-def test_cholqr2_and_orthonormal_rr_split(cfg1):
+def test_cholqr2_and_orthonormal_rr_split(cfg1, rr_arith):
     """rcf_cholqr2 then rcf_rayleigh_ritz_orth = rcf_rayleigh_ritz: M-orthonormal output, same
     span as the input, Ritz values of the oracle's Rayleigh-Ritz."""
     import torch
@@ -175,6 +184,14 @@ def test_eigensolver_loop_reaches_oracle_eigenvalues(cfg1):
         assert np.max(np.abs(lam[:nw] - ref[:nw])) < 1e-7, (mode, prec)
     lam, hist = _gpu_loop(cfg1, X0, 10, cfg1.hi, 1e-9, 60, R.RCF_CHFSI, R.RCF_FP32, nw)
     assert min(hist) > 1e-8
+    # the double-float Gram / projection GEMMs in the loop
+    R.rcf_set_rr_arith(cfg1.g.ctx, R.RCF_RR_DF)
+    try:
+        lam, hist = _gpu_loop(cfg1, X0, 10, cfg1.hi, 1e-9, 150, R.RCF_RCHFSI, R.RCF_FP32_DF, nw)
+    finally:
+        R.rcf_set_rr_arith(cfg1.g.ctx, R.RCF_RR_FP64)
+    assert hist[-1] < 1e-9
+    assert np.max(np.abs(lam[:nw] - ref[:nw])) < 1e-7
 
 
 def test_three_cycles_match_oracle_per_cycle(cfg1):
@@ -207,6 +224,9 @@ def test_invalid_arguments_are_rejected(cfg1):
     with pytest.raises(R.RcfError) as e:
         R.rcf_filter(cfg1.g.ctx, cfg1.g.op, Xd, cfg1.lam, 5, cfg1.bounds, R.RCF_CHFSI, R.RCF_FP32_DF, 0, Yd)
     assert e.value.status == R.RCF_EINVAL                                               # no residual in ChFSI
+    with pytest.raises(R.RcfError) as e:
+        R.rcf_set_rr_arith(cfg1.g.ctx, 5)                                                # unknown RR arithmetic
+    assert e.value.status == R.RCF_EINVAL
     with pytest.raises(R.RcfError) as e:
         R.rcf_set_step_kernel(cfg1.g.ctx, 7)                                             # unknown kernel
     assert e.value.status == R.RCF_EINVAL
