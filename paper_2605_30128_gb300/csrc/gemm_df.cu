@@ -9,6 +9,12 @@
 // compensated dot product of Ogita, Rump and Oishi), giving about 2^-46 relative to the sum
 // of the magnitudes of the terms.
 //
+// Summation is blocked: each stage of 16 rows accumulates into a fresh pair, which is then
+// added to the running pair by a normalised double-float addition.  (Accumulating a long
+// sum in one pair would let the low word collect ~n TwoSum errors of the size eps |sum|
+// and lose accuracy once n eps is no longer small; blocked, the error grows with the
+// number of stages and stays near eps^2 |sum| per stage.)
+//
 // Tiling: a block computes a 64 x 64 tile of C over one chunk of the K rows (split-K);
 // 256 threads, each 4 x 4 outputs strided by 16 (conflict-free shared-memory reads); the
 // K rows stream through shared memory 16 at a time as (hi, lo) pairs.  The partial tiles
@@ -39,6 +45,16 @@ __device__ __forceinline__ void tap(float2& Sh, float2& Sl, float ch, float cl, 
   const float2 db = add2(np, bp);
   Sh = s;
   Sl = add2(Sl, add2(t, sub2(da, db)));
+}
+
+// (Sh, Sl) += (bh, bl), both unevaluated pairs; the result normalised (|Sl| <= ulp(Sh) / 2)
+__device__ __forceinline__ void dfacc(float2& Sh, float2& Sl, float2 bh, float2 bl) {
+  const float2 s = add2(Sh, bh);
+  const float2 bp = sub2(s, Sh);
+  const float2 err = add2(sub2(Sh, sub2(s, bp)), sub2(bh, bp));
+  const float2 l = add2(add2(Sl, bl), err);
+  Sh = add2(s, l);
+  Sl = sub2(l, sub2(Sh, s));
 }
 
 // FP64 -> (hi, lo) with integer operations (as in the double-float residual): hi the top
@@ -95,7 +111,7 @@ __device__ __forceinline__ void tile_of(int t, int tiles_n, int lower, int& ti, 
 }
 
 // grid (ntiles, nchunks), NTHR threads
-__global__ void __launch_bounds__(NTHR, 2) gemm_tn_df_kernel(const TNArgs a) {
+__global__ void __launch_bounds__(NTHR, 1) gemm_tn_df_kernel(const TNArgs a) {
   __shared__ float2 Ah[KT][TM], Al[KT][TM], Bh[KT][TN], Bl[KT][TN];   // (re, im) pairs: 32 KB
   int ti, tj;
   tile_of(blockIdx.x, a.tiles_n, a.lower, ti, tj);
@@ -140,6 +156,11 @@ __global__ void __launch_bounds__(NTHR, 2) gemm_tn_df_kernel(const TNArgs a) {
       Bl[kk][c] = make_float2(br.y, bi.y);
     }
     __syncthreads();
+    float2 Bh_[4][4], Bl_[4][4];   // this stage's sums
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Bh_[u][v] = Bl_[u][v] = make_float2(0.f, 0.f);
 #pragma unroll 4
     for (int kk = 0; kk < KT; ++kk) {
       float2 ah[4], al[4], bh[4], bl[4];
@@ -152,11 +173,15 @@ __global__ void __launch_bounds__(NTHR, 2) gemm_tn_df_kernel(const TNArgs a) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           // conj(a) b = a_r (b_r, b_i) + a_i (b_i, -b_r)
-          tap(Sh[u][v], Sl[u][v], ah[u].x, al[u].x, bh[v], bl[v]);
-          tap(Sh[u][v], Sl[u][v], ah[u].y, al[u].y, make_float2(bh[v].y, -bh[v].x),
+          tap(Bh_[u][v], Bl_[u][v], ah[u].x, al[u].x, bh[v], bl[v]);
+          tap(Bh_[u][v], Bl_[u][v], ah[u].y, al[u].y, make_float2(bh[v].y, -bh[v].x),
               make_float2(bl[v].y, -bl[v].x));
         }
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dfacc(Sh[u][v], Sl[u][v], Bh_[u][v], Bl_[u][v]);
   }
   // partial tile
   float4* out = reinterpret_cast<float4*>(a.part) +
@@ -182,12 +207,7 @@ __global__ void gemm_tn_reduce_kernel(const float* __restrict__ part, int nchunk
     for (int c = 0; c < nchunks; ++c) {
       const float4 p = reinterpret_cast<const float4*>(part)[(int64_t(c) * ntiles + t) * (TM * TN) + e];
       // (sh, sl) += (p.xy, p.zw): TwoSum of the hi parts, lo parts added
-      const float2 ph = make_float2(p.x, p.y), pl = make_float2(p.z, p.w);
-      const float2 s = add2(sh, ph);
-      const float2 bp = sub2(s, sh);
-      const float2 err = add2(sub2(sh, sub2(s, bp)), sub2(ph, bp));
-      sh = s;
-      sl = add2(sl, add2(pl, err));
+      dfacc(sh, sl, make_float2(p.x, p.y), make_float2(p.z, p.w));
     }
     reinterpret_cast<double2*>(C)[int64_t(j) * ldc + i] =
         make_double2(double(sh.x) + double(sl.x), double(sh.y) + double(sl.y));
@@ -206,8 +226,8 @@ int launch_gemm_tn_df(rcf_ctx* ctx, const double* A, int64_t lda, const double* 
   a.tiles_n = (n + TN - 1) / TN;
   if (lower && a.tiles_m != a.tiles_n) return fail(ctx, RCF_EINVAL, "lower needs a square C");
   const int ntiles = lower ? a.tiles_m * (a.tiles_m + 1) / 2 : a.tiles_m * a.tiles_n;
-  // enough chunks for about four blocks per SM on 152 SMs, each at least 1024 rows
-  int64_t nchunks = std::max<int64_t>(1, (4 * 152 + ntiles - 1) / ntiles);
+  // enough chunks for about eight blocks per SM-slot on 152 SMs, each at least 1024 rows
+  int64_t nchunks = std::max<int64_t>(1, (8 * 152 + ntiles - 1) / ntiles);
   nchunks = std::min<int64_t>(nchunks, std::max<int64_t>(1, K / 1024));
   int64_t kchunk = (K + nchunks - 1) / nchunks;
   kchunk = (kchunk + KT - 1) / KT * KT;

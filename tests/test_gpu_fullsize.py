@@ -203,3 +203,23 @@ def test_fp64_chfsi_16cubed_p6_full_block_columns():
         assert rel(Y[cols].cpu().numpy().T, ref) < 1e-10
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("arith", [0, 1], ids=["rr-fp64", "rr-df"])
+def test_cholqr2_long_columns_orthonormal(full, arith):
+    """Cholesky-QR2 of 64 columns of 2,000,000 rows (sums over 2M terms): the result is
+    M-orthonormal to 1e-12 with either Gram arithmetic, and its span is the input's."""
+    import torch
+    from paper_2605_30128_gb300 import rchfsi as R
+    H, g, X = full["H"], full["g"], full["X"]
+    R.rcf_set_rr_arith(g.ctx, arith)
+    try:
+        Y = X[:64].clone()
+        R.rcf_cholqr2(g.ctx, g.op, Y)
+    finally:
+        R.rcf_set_rr_arith(g.ctx, R.RCF_RR_FP64)
+    m = torch.from_numpy(np.repeat(H.mass, 2)).cuda()
+    G = (Y.conj() * m) @ Y.T
+    assert (G - torch.eye(64, dtype=G.dtype, device="cuda")).abs().max().item() < 1e-12
+    C = (Y.conj() * m) @ X[:64].T                      # X = Y (Y^H M X) within the span
+    assert torch.linalg.norm(Y.T @ C - X[:64].T).item() < 1e-10 * torch.linalg.norm(X[:64]).item()
