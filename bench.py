@@ -454,9 +454,26 @@ def run_ours(args):
         torch.cuda.synchronize()
         e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
         e_ms = max_over_ranks(ws, e_ms)
+        # the host link of this machine, pinned buffers, one direction at a time (the
+        # end-to-end time cannot fall below the larger of the two copy times)
+        nl = min(64, ne)
+        dbuf = torch.empty((nl, N), dtype=torch.complex128, device=dev)
+        link = {}
+        for name, dst, src in (("h2d_gbs", dbuf, Xh[:nl]), ("d2h_gbs", Yh[:nl], dbuf)):
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                dst.copy_(src, non_blocking=True)
+            e1.record()
+            torch.cuda.synchronize()
+            link[name] = 3 * dbuf.numel() * 16 / (e0.elapsed_time(e1) * 1e6)
+        del dbuf
         line["e2e"] = {"value": float(N) * ne * q * ws / (e_ms * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": int(Xh.numel() * 16), "d2h_bytes_per_step": int(Yh.numel() * 16),
                        "ms_per_step": e_ms, "sample": sample,
+                       "link": link,
                        "call": "rcf_filter_host (pinned host X and Y; wall clock around the synchronising call)"}
         del Xh, Yh
 
