@@ -233,13 +233,13 @@ int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int
                int block, double* Y, int64_t ldy);
 
 /* rcf_filter with X and Y in HOST memory (c128, leading dimensions ldx, ldy
- * >= 2M; no counterpart in the paper).  Band blocks stream through up to four
- * device slots per direction: blocks are copied in ahead and copied out behind
- * on two copy streams of the context while a block is filtered on its compute
- * stream, so copies and filtering overlap when X and Y are page-locked
- * (pinned) host memory; pageable memory works but its copies do not overlap.
- * Device scratch: up to eight blocks of `block` c128 vectors besides the
- * filter's own.  Synchronises; returns after Y is complete. */
+ * >= 2M; no counterpart in the paper).  Band blocks stream through two
+ * device slots per direction: the next block is copied in and the previous one
+ * copied out on two copy streams of the context while a block is filtered on
+ * its compute stream, so copies and filtering overlap when X and Y are
+ * page-locked (pinned) host memory; pageable memory works but its copies do
+ * not overlap.  Device scratch: up to four blocks of `block` c128 vectors
+ * besides the filter's own.  Synchronises; returns after Y is complete. */
 int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
                     const double* ritz, int degree, const double bounds[3], int mode, int prec,
                     int block, double* Y, int64_t ldy);

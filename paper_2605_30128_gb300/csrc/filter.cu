@@ -32,7 +32,7 @@ int check_block(rcf_ctx* ctx, const rcf_op* op, const void* p, int64_t ld, int n
   return RCF_OK;
 }
 
-constexpr int kHostSlots = 4;   // device slots per direction of rcf_filter_host
+constexpr int kHostSlots = 2;   // device slots per direction of rcf_filter_host
 
 // status of a CUDA call, recorded in the context (for use where RCF_CUDA cannot return)
 int cuda_check(rcf_ctx* ctx, cudaError_t e) {
@@ -623,8 +623,8 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
     if (!*st) RCF_CUDA(ctx, cudaStreamCreateWithFlags(st, cudaStreamNonBlocking));
   const int nb = (block <= 0 || block > nvec) ? nvec : block;
   const int nblk = (nvec + nb - 1) / nb;
-  // S device slots for X blocks and S for Y blocks (ld = 2M): the copies of up to S
-  // blocks ahead (in) and behind (out) proceed while a block is filtered
+  // S device slots for X blocks and S for Y blocks (ld = 2M): the next block is copied
+  // in and the previous one copied out while a block is filtered
   const int S = std::min(nblk, kHostSlots);
   const size_t bytes = sizeof(double) * 2 * size_t(rows) * nb;
   double* dxs = nullptr;
@@ -656,7 +656,7 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
                       ctx->copy_in));
     return cuda_check(ctx, cudaEventRecord(ev_in[b], ctx->copy_in));
   };
-  for (int b = 0; b < S && st == RCF_OK; ++b) st = copy_in(b);
+  st = copy_in(0);
   for (int b = 0; b < nblk && st == RCF_OK; ++b) {
     const int n = count(b);
     st = cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ev_in[b], 0));
@@ -668,12 +668,17 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
                         ys, rows);
     }
     if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_done[b], ctx->stream));
-    // copy the filtered block out while the next ones are filtered
+    // The next block's copy is queued only now, behind this block's own small
+    // host-to-device copy (its coefficient table): host-to-device copies of one device
+    // run in issue order, and with every block copy queued up front each block's filter
+    // waited for them (measured: 966 ms per 1024 vectors against 714 ms for the filter
+    // and 211 ms for all copies).  The copy then runs while this block is filtered.
+    if (st == RCF_OK && b + 1 < nblk) st = copy_in(b + 1);
+    // copy the filtered block out while the next one is filtered
     if (st == RCF_OK) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->copy_out, ev_done[b], 0));
     if (st == RCF_OK)
       st = copy_rows(Y + 2 * int64_t(b) * nb * ldy, ldy, dy(b), rows, n, cudaMemcpyDeviceToHost, ctx->copy_out);
     if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_out[b], ctx->copy_out));
-    if (st == RCF_OK && b + S < nblk) st = copy_in(b + S);
     // the per-block coefficient table is a host vector copied asynchronously
     if (st == RCF_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream));
   }
