@@ -25,10 +25,12 @@ from .lanczos import lanczos_bounds
 from .rr import cholqr, cholqr2, rayleigh_ritz
 from .eigensolver import rchfsi_eigensolver
 from .adjoint import rchfsi_filter_adjoint, ritz_loss_head
+from .bfp import bfp_encode, bfp_decode, bfp_encode_block, bfp_decode_block, bfp_layout, bfp_stream_bytes
 
 __all__ = [
     "gll_nodes_weights", "lagrange_derivative_matrix", "Mesh", "Hamiltonian", "soc_delta",
     "p_orbital_L", "filter_scalars", "ritz_filter_values", "chebyshev_filter_closed_form",
     "chfsi_filter", "rchfsi_filter", "residual", "lanczos_bounds", "cholqr", "cholqr2",
     "rayleigh_ritz", "rchfsi_eigensolver", "rchfsi_filter_adjoint", "ritz_loss_head",
+    "bfp_encode", "bfp_decode", "bfp_encode_block", "bfp_decode_block", "bfp_layout", "bfp_stream_bytes",
 ]
