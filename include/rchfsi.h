@@ -287,6 +287,32 @@ int rcf_adjoint_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t 
                        const double* Ybar, int64_t ldyb, int ckpt_every,
                        double* dV, double* dB, double* dh);
 
+/* ---- block floating-point codec (Section III-C-3) ------------------------ */
+
+/* Four consecutive FP32 values form a block of 4 * nbits bits (nbits = 16, 12
+ * or 10: 8, 6 or 5 bytes).  Its low 8 bits hold the shared biased exponent
+ * e = e_max + 127, with 2^(e_max-1) <= max |x_i| < 2^e_max (e = 0: all four
+ * values zero; a block whose largest magnitude is subnormal takes e_max = -126);
+ * bits [8 + i v, 8 + (i+1) v) hold value i's coefficient
+ * q_i = round_half_even(x_i 2^(v-1-e_max)), v = nbits - 2, two's complement,
+ * clamped to at most 2^(v-1) - 1 (and, at e_max = 128, to at least
+ * -(2^(v-1) - 1)).  Decoding gives q_i 2^(e_max-v+1), exactly.  Block b is the
+ * little-endian word at byte offset b * (4 * nbits / 8) of the stream.
+ *
+ * rcf_bfp_stream_bytes: bytes of the stream for n values (ceil(n/4) blocks; a
+ * last partial block is completed with zeros); -1 for an invalid nbits or n < 0.
+ * rcf_bfp_encode: x (device, float[n], 4-byte aligned; finite values, the code
+ * of a block holding Inf or NaN is unspecified) -> stream (device,
+ * rcf_bfp_stream_bytes(n, nbits) bytes, 8-byte aligned at nbits = 16, 2-byte
+ * at 12).  rcf_bfp_decode: stream -> y (device, float[n], 4-byte aligned).
+ * Values and stream must not overlap.  Both enqueue one kernel on the
+ * context's stream and return without synchronising; results are valid after
+ * rcf_sync.  Errors: RCF_EINVAL for a bad nbits, n < 0, NULL or misaligned
+ * pointers, overlap; RCF_ECUDA for a failed launch.  n = 0 does nothing. */
+int64_t rcf_bfp_stream_bytes(int64_t n, int nbits);
+int rcf_bfp_encode(rcf_ctx* ctx, const float* x, int64_t n, int nbits, void* stream);
+int rcf_bfp_decode(rcf_ctx* ctx, const void* stream, int64_t n, int nbits, float* y);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,264 @@
+// Block floating-point (BFP) codec of Section III-C-3.
+//
+// Four FP32 values form one block of N_bits = 4 n_bits bits: the low 8 bits hold the
+// shared biased exponent e = e_max + 127 (2^(e_max-1) <= max |x_i| < 2^e_max; e = 0
+// marks an all-zero block), the rest four two's-complement coefficients of
+// v = n_bits - 2 bits, q_i = round(x_i 2^(v-1-e_max)) clamped above at 2^(v-1) - 1;
+// decoding gives q_i 2^(e_max-v+1).  n_bits = 16, 12, 10: 8, 6 or 5 bytes per block,
+// written by one thread as one 8-byte, three 2-byte or five 1-byte stores, so no
+// storage word is shared by two blocks (the section's layout).
+//
+// Choices where the section is silent: round to nearest even; coefficient i in bits
+// [8 + i v, 8 + (i+1) v), the word little-endian; a block whose largest magnitude is
+// subnormal takes e_max = -126; at e_max = 128 the lower clamp is -(2^(v-1) - 1), so
+// that no decoded value overflows FP32; a ragged tail block is completed with zeros.
+//
+// All scaling is by powers of two, split into two factors that are normal FP32
+// numbers, so every product is exact (or, when it underflows, far below 1/2, where
+// the rounded coefficient is 0 either way): the only rounding is the rint of the
+// quantisation, and decoding is exact.  The helpers are __host__ __device__ so that
+// their arithmetic can be checked on a CPU as well.
+#include <cstring>
+
+#include "internal.h"
+
+namespace rcf {
+namespace {
+
+__host__ __device__ __forceinline__ uint32_t bits_of(float x) {
+  uint32_t u;
+  memcpy(&u, &x, sizeof(u));
+  return u;
+}
+__host__ __device__ __forceinline__ float float_of(uint32_t u) {
+  float x;
+  memcpy(&x, &u, sizeof(x));
+  return x;
+}
+// 2^k for -126 <= k <= 127
+__host__ __device__ __forceinline__ float pow2i(int k) { return float_of(uint32_t(k + 127) << 23); }
+// x 2^k for |k| <= 252, as two power-of-two products (each factor a normal number)
+__host__ __device__ __forceinline__ float scale_pow2(float x, int k) {
+  const int h = k / 2;
+  return (x * pow2i(h)) * pow2i(k - h);
+}
+
+template <int V>
+__host__ __device__ __forceinline__ uint64_t bfp_encode4(const float x[4]) {
+  constexpr int QMAX = (1 << (V - 1)) - 1;
+  const float m = fmaxf(fmaxf(fabsf(x[0]), fabsf(x[1])), fmaxf(fabsf(x[2]), fabsf(x[3])));
+  if (!(m > 0.0f)) return 0;                                // all zero
+  const int f = int((bits_of(m) >> 23) & 0xFFu);            // biased FP32 exponent of the max
+  int emax = f == 0 ? -126 : f - 126;                       // 2^(emax-1) <= m < 2^emax
+  if (emax > 128) emax = 128;                               // non-finite input: unspecified code
+  const float lo = emax == 128 ? -float(QMAX) : -float(QMAX + 1);
+  uint64_t w = uint64_t(emax + 127);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float s = rintf(scale_pow2(x[i], V - 1 - emax));        // round half to even
+    s = fminf(fmaxf(s, lo), float(QMAX));
+    const int q = int(s);
+    w |= uint64_t(uint32_t(q) & ((1u << V) - 1u)) << (8 + i * V);
+  }
+  return w;
+}
+
+template <int V>
+__host__ __device__ __forceinline__ void bfp_decode4(uint64_t w, float y[4]) {
+  const int e = int(w & 0xFFu);
+  const int k = e - 127 - V + 1;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int fld = int((w >> (8 + i * V)) & ((1u << V) - 1u));
+    const int q = fld >= (1 << (V - 1)) ? fld - (1 << V) : fld;   // restore the sign bits
+    y[i] = e == 0 ? 0.0f : scale_pow2(float(q), k);
+  }
+}
+
+// one block's bytes in the stream: 8 bytes as one word, 6 as three 2-byte words, 5 as bytes
+template <int NB>
+struct BlockIO;
+template <>
+struct BlockIO<16> {
+  static __device__ __forceinline__ void store(unsigned char* s, int64_t b, uint64_t w) {
+    reinterpret_cast<uint64_t*>(s)[b] = w;
+  }
+  static __device__ __forceinline__ uint64_t load(const unsigned char* s, int64_t b) {
+    return __ldg(reinterpret_cast<const unsigned long long*>(s) + b);
+  }
+};
+template <>
+struct BlockIO<12> {
+  static __device__ __forceinline__ void store(unsigned char* s, int64_t b, uint64_t w) {
+    uint16_t* p = reinterpret_cast<uint16_t*>(s) + 3 * b;
+    p[0] = uint16_t(w);
+    p[1] = uint16_t(w >> 16);
+    p[2] = uint16_t(w >> 32);
+  }
+  static __device__ __forceinline__ uint64_t load(const unsigned char* s, int64_t b) {
+    const unsigned short* p = reinterpret_cast<const unsigned short*>(s) + 3 * b;
+    return uint64_t(__ldg(p)) | (uint64_t(__ldg(p + 1)) << 16) | (uint64_t(__ldg(p + 2)) << 32);
+  }
+};
+template <>
+struct BlockIO<10> {
+  static __device__ __forceinline__ void store(unsigned char* s, int64_t b, uint64_t w) {
+    unsigned char* p = s + 5 * b;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) p[j] = static_cast<unsigned char>(w >> (8 * j));
+  }
+  static __device__ __forceinline__ uint64_t load(const unsigned char* s, int64_t b) {
+    const unsigned char* p = s + 5 * b;
+    uint64_t w = 0;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) w |= uint64_t(__ldg(p + j)) << (8 * j);
+    return w;
+  }
+};
+
+constexpr int kBfpThreads = 256;
+constexpr int kBfpUnroll = 4;   // blocks per thread per pass (independent loads in flight)
+
+// Thread t of the grid handles blocks t, t + S, t + 2S, ... (S = threads in the grid),
+// kBfpUnroll of them per pass.  vec4: x is 16-byte aligned (whole blocks load as float4).
+template <int NB>
+__global__ void __launch_bounds__(kBfpThreads) bfp_encode_kernel(const float* __restrict__ x, int64_t n,
+                                                                   unsigned char* __restrict__ s, int vec4) {
+  constexpr int V = NB - 2;
+  const int64_t nblk = (n + 3) / 4;
+  const int64_t S = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t b0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; b0 < nblk; b0 += S * kBfpUnroll) {
+    float v[kBfpUnroll][4];
+#pragma unroll
+    for (int u = 0; u < kBfpUnroll; ++u) {
+      const int64_t b = b0 + u * S;
+      if (b >= nblk) break;
+      if (vec4 && 4 * b + 4 <= n) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(x) + b);
+        v[u][0] = t.x; v[u][1] = t.y; v[u][2] = t.z; v[u][3] = t.w;
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[u][j] = 4 * b + j < n ? x[4 * b + j] : 0.0f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kBfpUnroll; ++u) {
+      const int64_t b = b0 + u * S;
+      if (b >= nblk) break;
+      BlockIO<NB>::store(s, b, bfp_encode4<V>(v[u]));
+    }
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kBfpThreads) bfp_decode_kernel(const unsigned char* __restrict__ s, int64_t n,
+                                                                   float* __restrict__ y, int vec4) {
+  constexpr int V = NB - 2;
+  const int64_t nblk = (n + 3) / 4;
+  const int64_t S = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t b0 = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; b0 < nblk; b0 += S * kBfpUnroll) {
+    uint64_t w[kBfpUnroll];
+#pragma unroll
+    for (int u = 0; u < kBfpUnroll; ++u) {
+      const int64_t b = b0 + u * S;
+      if (b >= nblk) break;
+      w[u] = BlockIO<NB>::load(s, b);
+    }
+#pragma unroll
+    for (int u = 0; u < kBfpUnroll; ++u) {
+      const int64_t b = b0 + u * S;
+      if (b >= nblk) break;
+      float r[4];
+      bfp_decode4<V>(w[u], r);
+      if (vec4 && 4 * b + 4 <= n) {
+        reinterpret_cast<float4*>(y)[b] = make_float4(r[0], r[1], r[2], r[3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (4 * b + j < n) y[4 * b + j] = r[j];
+      }
+    }
+  }
+}
+
+int bfp_bytes_per_block(int nbits) {
+  switch (nbits) {
+    case 16: return 8;
+    case 12: return 6;
+    case 10: return 5;
+    default: return 0;
+  }
+}
+
+// grid: one pass of kBfpUnroll blocks per thread, at most 16 resident-size CTAs per SM of 152
+unsigned bfp_grid(int64_t nblk) {
+  const int64_t per_cta = int64_t(kBfpThreads) * kBfpUnroll;
+  return unsigned(std::min<int64_t>((nblk + per_cta - 1) / per_cta, 152 * 16));
+}
+
+bool ranges_overlap(const void* a, size_t na, const void* b, size_t nb) {
+  const char* a0 = static_cast<const char*>(a);
+  const char* b0 = static_cast<const char*>(b);
+  return a0 < b0 + nb && b0 < a0 + na;
+}
+
+int check_bfp_args(rcf_ctx* ctx, const void* vals, int64_t n, int nbits, const void* stream, const char* vname) {
+  const int nb = bfp_bytes_per_block(nbits);
+  if (nb == 0) return fail(ctx, RCF_EINVAL, "n_bits must be 16, 12 or 10 (got %d)", nbits);
+  if (n < 0) return fail(ctx, RCF_EINVAL, "n < 0");
+  if (n == 0) return RCF_OK;
+  if (!vals || !stream) return fail(ctx, RCF_EINVAL, "NULL %s or stream", vname);
+  if (reinterpret_cast<uintptr_t>(vals) % 4) return fail(ctx, RCF_EINVAL, "%s must be 4-byte aligned", vname);
+  const size_t salign = nbits == 16 ? 8 : nbits == 12 ? 2 : 1;
+  if (reinterpret_cast<uintptr_t>(stream) % salign)
+    return fail(ctx, RCF_EINVAL, "stream must be %zu-byte aligned at %d bits", salign, nbits);
+  const size_t sbytes = size_t((n + 3) / 4) * nb;
+  if (ranges_overlap(vals, sizeof(float) * size_t(n), stream, sbytes))
+    return fail(ctx, RCF_EINVAL, "%s overlaps the stream", vname);
+  return RCF_OK;
+}
+
+}  // namespace
+}  // namespace rcf
+
+using namespace rcf;
+
+extern "C" int64_t rcf_bfp_stream_bytes(int64_t n, int nbits) {
+  const int nb = bfp_bytes_per_block(nbits);
+  if (nb == 0 || n < 0) return -1;
+  return ((n + 3) / 4) * nb;
+}
+
+extern "C" int rcf_bfp_encode(rcf_ctx* ctx, const float* x, int64_t n, int nbits, void* stream) {
+  if (!ctx) return RCF_EINVAL;
+  RCF_TRY(check_bfp_args(ctx, x, n, nbits, stream, "x"));
+  if (n == 0) return RCF_OK;
+  const int64_t nblk = (n + 3) / 4;
+  const int vec4 = (reinterpret_cast<uintptr_t>(x) % 16) == 0;
+  unsigned char* s = static_cast<unsigned char*>(stream);
+  const unsigned grid = bfp_grid(nblk);
+  switch (nbits) {
+    case 16: bfp_encode_kernel<16><<<grid, kBfpThreads, 0, ctx->stream>>>(x, n, s, vec4); break;
+    case 12: bfp_encode_kernel<12><<<grid, kBfpThreads, 0, ctx->stream>>>(x, n, s, vec4); break;
+    default: bfp_encode_kernel<10><<<grid, kBfpThreads, 0, ctx->stream>>>(x, n, s, vec4); break;
+  }
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+
+extern "C" int rcf_bfp_decode(rcf_ctx* ctx, const void* stream, int64_t n, int nbits, float* y) {
+  if (!ctx) return RCF_EINVAL;
+  RCF_TRY(check_bfp_args(ctx, y, n, nbits, stream, "y"));
+  if (n == 0) return RCF_OK;
+  const int64_t nblk = (n + 3) / 4;
+  const int vec4 = (reinterpret_cast<uintptr_t>(y) % 16) == 0;
+  const unsigned char* s = static_cast<const unsigned char*>(stream);
+  const unsigned grid = bfp_grid(nblk);
+  switch (nbits) {
+    case 16: bfp_decode_kernel<16><<<grid, kBfpThreads, 0, ctx->stream>>>(s, n, y, vec4); break;
+    case 12: bfp_decode_kernel<12><<<grid, kBfpThreads, 0, ctx->stream>>>(s, n, y, vec4); break;
+    default: bfp_decode_kernel<10><<<grid, kBfpThreads, 0, ctx->stream>>>(s, n, y, vec4); break;
+  }
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}

@@ -32,6 +32,7 @@ EXPORTS = [
     "rcf_grad_bilinear", "rcf_adjoint_filter", "rcf_cheb_step", "rcf_launch_count",
     "rcf_apply_noalloc", "rcf_set_step_kernel", "rcf_residual_df", "rcf_cholqr2",
     "rcf_rayleigh_ritz_orth", "rcf_filter_host", "rcf_set_rr_arith",
+    "rcf_bfp_stream_bytes", "rcf_bfp_encode", "rcf_bfp_decode",
 ]
 
 _lib = None
@@ -87,6 +88,9 @@ def lib() -> ctypes.CDLL:
         "rcf_cholqr2": (i32, [vp, vp, vp, i64, i32]),
         "rcf_filter_host": (i32, [vp, vp, vp, i64, i32, vp, i32, vp, i32, i32, i32, vp, i64]),
         "rcf_rayleigh_ritz_orth": (i32, [vp, vp, vp, i64, i32, vp, i64, vp]),
+        "rcf_bfp_stream_bytes": (i64, [i64, i32]),
+        "rcf_bfp_encode": (i32, [vp, vp, i64, i32, vp]),
+        "rcf_bfp_decode": (i32, [vp, vp, i64, i32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -413,3 +417,49 @@ def rcf_apply_noalloc(ctx, op, form: int, X, Y, prec: int = RCF_FP64):
     py, ldy = _dev(Y, dt, "Y")
     nvec = X.shape[0] if X.dim() == 2 else 1
     _check(ctx, lib().rcf_apply_noalloc(ctx, op, form, px, ldx, nvec, py, ldy, prec))
+
+
+# ---- block floating-point codec (Section III-C-3) ----------------------------------
+
+RCF_BFP_RATES = (16, 12, 10)
+
+
+def rcf_bfp_stream_bytes(n: int, nbits: int) -> int:
+    """Bytes of the compressed stream of n FP32 values at nbits per value."""
+    r = lib().rcf_bfp_stream_bytes(int(n), int(nbits))
+    if r < 0:
+        raise ValueError(f"invalid n={n} or nbits={nbits} (rates {RCF_BFP_RATES})")
+    return int(r)
+
+
+def _flat(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def rcf_bfp_encode(ctx, x, nbits: int, stream):
+    """Encode the float32 CUDA tensor x (contiguous, any shape) into the uint8 CUDA tensor
+    stream (at least rcf_bfp_stream_bytes(x.numel(), nbits) bytes)."""
+    import torch
+    px = _flat(x, torch.float32, "x")
+    ps = _flat(stream, torch.uint8, "stream")
+    if nbits in RCF_BFP_RATES and stream.numel() < rcf_bfp_stream_bytes(x.numel(), nbits):
+        raise ValueError("stream is too small")
+    _check(ctx, lib().rcf_bfp_encode(ctx, px, x.numel(), int(nbits), ps))
+
+
+def rcf_bfp_decode(ctx, stream, nbits: int, y):
+    """Decode y.numel() values from the uint8 CUDA tensor stream into the float32 CUDA
+    tensor y (contiguous, any shape)."""
+    import torch
+    ps = _flat(stream, torch.uint8, "stream")
+    py = _flat(y, torch.float32, "y")
+    if nbits in RCF_BFP_RATES and stream.numel() < rcf_bfp_stream_bytes(y.numel(), nbits):
+        raise ValueError("stream is too small")
+    _check(ctx, lib().rcf_bfp_decode(ctx, ps, y.numel(), int(nbits), py))

@@ -49,3 +49,15 @@ def test_null_arguments_are_rejected_without_a_gpu(libpath):
     assert L.rcf_create(None, 0, None) == R.RCF_EINVAL
     assert L.rcf_mesh_info(None, None, None, None) == R.RCF_EINVAL
     assert L.rcf_filter(None, None, None, 0, 0, None, 1, None, 0, 0, 0, None, 0) == R.RCF_EINVAL
+
+
+def test_bfp_stream_size_without_a_gpu(libpath):
+    from oracle.bfp import bfp_stream_bytes
+    from paper_2605_30128_gb300 import rchfsi as R
+    for nbits in R.RCF_BFP_RATES:
+        for n in (0, 1, 3, 4, 5, 1023, 1 << 33):
+            assert R.rcf_bfp_stream_bytes(n, nbits) == bfp_stream_bytes(n, nbits)
+    L = R.lib()
+    assert L.rcf_bfp_stream_bytes(4, 8) == -1 and L.rcf_bfp_stream_bytes(-1, 16) == -1
+    assert L.rcf_bfp_encode(None, None, 4, 16, None) == R.RCF_EINVAL
+    assert L.rcf_bfp_decode(None, None, 4, 16, None) == R.RCF_EINVAL

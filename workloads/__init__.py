@@ -166,3 +166,19 @@ def complex_normal(seed: int, shape, dtype=np.complex128) -> np.ndarray:
     a = rng.normal(size=shape)
     b = rng.normal(size=shape)
     return ((a + 1j * b) / np.sqrt(2.0)).astype(dtype)
+
+
+def bfp_values(seed: int, n: int) -> np.ndarray:
+    """float32[n] for the block floating-point codec, from PCG64(seed): each group of four
+    consecutive values shares a scale drawn log-uniformly over the whole FP32 range
+    (2^-149 .. 2^127), and each value a further factor 2^-u, u ~ U(0, 24), and a random
+    sign; one group in 64 is all zero.  Residual blocks behave like this: neighbouring
+    entries have similar magnitudes and the magnitudes span many decades."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = (n + 3) // 4
+    scale = 2.0 ** rng.uniform(-149.0, 127.0, size=(g, 1))
+    spread = 2.0 ** -rng.uniform(0.0, 24.0, size=(g, 4))
+    sign = rng.choice([-1.0, 1.0], size=(g, 4))
+    x = scale * spread * sign
+    x[rng.random(g) < 1.0 / 64.0] = 0.0
+    return x.astype(np.float32).ravel()[:n]
