@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--degree", type=int, default=None)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64, e2e and CPU legs (profiling runs only)")
+    ap.add_argument("--codec-only", action="store_true",
+                    help="time only the block floating-point codec on one residual block (prints its object)")
     return ap.parse_args()
 
 
@@ -243,6 +245,64 @@ def traffic_record():
         return None
 
 
+
+def measured_hbm_peak() -> float:
+    """HBM copy bandwidth (GB/s) measured on this GPU model, else the fallback figure."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path))["hbm_gbs"] if os.path.exists(path) else 6800.0
+
+
+def codec_leg(R, ctx, op, Xb, ritz_b, peak, stream):
+    """The block floating-point codec (Section III-C-3) on the double-float residual of one
+    block Xb (256 vectors of the 20^3 p = 5 workload: 1.02e9 FP32 values, 4.1 GB > L2):
+    encode and decode at each rate, 5 launches each timed with CUDA events on the library's
+    stream; algorithmic bytes = 4 per value + the stream.  Any failure is reported in the
+    returned object (the codec is reported beside the filter, never instead of it)."""
+    import torch
+    try:
+        Rh = torch.empty(Xb.shape, dtype=torch.complex64, device=Xb.device)
+        R.rcf_residual_df(ctx, op, Xb, ritz_b, Rh)
+        rv = Rh.view(torch.float32).reshape(-1)
+        n_r = rv.numel()
+        dec = torch.empty_like(rv)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        out = {}
+        for nbits in R.RCF_BFP_RATES:
+            sbuf = torch.empty(R.rcf_bfp_stream_bytes(n_r, nbits), dtype=torch.uint8, device=Xb.device)
+            R.rcf_bfp_encode(ctx, rv, nbits, sbuf)
+            R.rcf_bfp_decode(ctx, sbuf, nbits, dec)
+            torch.cuda.synchronize()
+            reps = 5
+            ev0.record(stream)
+            for _ in range(reps):
+                R.rcf_bfp_encode(ctx, rv, nbits, sbuf)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            e_ms = ev0.elapsed_time(ev1) / reps
+            ev0.record(stream)
+            for _ in range(reps):
+                R.rcf_bfp_decode(ctx, sbuf, nbits, dec)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            d_ms = ev0.elapsed_time(ev1) / reps
+            moved = 4.0 * n_r + sbuf.numel()
+            num = den = 0.0
+            for c0 in range(0, n_r, 1 << 27):
+                a = rv[c0:c0 + (1 << 27)].double()
+                num += float(((dec[c0:c0 + (1 << 27)].double() - a) ** 2).sum())
+                den += float((a * a).sum())
+            out[str(nbits)] = {
+                "encode_ms": e_ms, "decode_ms": d_ms,
+                "encode_gbs": moved / (e_ms * 1e6), "decode_gbs": moved / (d_ms * 1e6),
+                "encode_frac": moved / (e_ms * 1e6) / peak, "decode_frac": moved / (d_ms * 1e6) / peak,
+                "stream_bytes": int(sbuf.numel()), "rel_error_fro": (num / den) ** 0.5}
+            del sbuf
+        return dict(out, values=n_r, peak_gbs=peak, bound="hbm",
+                    data="double-float residual R of one %d-vector block, as FP32" % Xb.shape[0],
+                    note="algorithmic bytes = 4 per value + the stream; frac of the measured copy bandwidth")
+    except Exception as exc:
+        return {"error": repr(exc)[:300]}
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -272,6 +332,12 @@ def run_ours(args):
     lT = lo + 0.05 * (hi - lo)
     ritz = np.linspace(lo, lT, nvec, endpoint=False)
     bounds = (lo - 1e-3 * abs(lo), lT, hi)
+    if args.codec_only:
+        if rank == 0:
+            obj = codec_leg(R, ctx, op, X[:w.block], ritz[:w.block], measured_hbm_peak(), stream)
+            print(json.dumps({"bfp_codec": obj, "config": {"workload": describe(w)}}), flush=True)
+        prob.close()
+        return 0
 
     def step(prec=R.RCF_FP32_DF):
         R.rcf_filter(ctx, op, X, ritz, q, bounds, R.RCF_RCHFSI, prec, w.block, Y)
@@ -392,9 +458,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     res64_ms = ev0.elapsed_time(ev1)
     del R64
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak = measured_hbm_peak()
     achieved = BYTES_PER_UNIT * N * blk / (k_ms * 1e-3) / 1e9
     tr = traffic_record()
     line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -508,51 +572,8 @@ def run_ours(args):
         pa_.close()
         del Xa, Ya, Yb, dV, dB
 
-        # ---- block floating-point codec (Section III-C-3) on one residual block of this
-        #      workload (256 vectors: 1.02e9 FP32 values, 4.1 GB > L2) ----
-        try:
-            Rh = torch.empty((blk, N), dtype=torch.complex64, device=dev)
-            R.rcf_residual_df(ctx, op, X[:blk], ritz[:blk], Rh)
-            rv = Rh.view(torch.float32).reshape(-1)
-            n_r = rv.numel()
-            dec = torch.empty_like(rv)
-            codec = {}
-            for nbits in R.RCF_BFP_RATES:
-                sbuf = torch.empty(R.rcf_bfp_stream_bytes(n_r, nbits), dtype=torch.uint8, device=dev)
-                R.rcf_bfp_encode(ctx, rv, nbits, sbuf)
-                R.rcf_bfp_decode(ctx, sbuf, nbits, dec)
-                torch.cuda.synchronize()
-                reps = 5
-                ev0.record(stream)
-                for _ in range(reps):
-                    R.rcf_bfp_encode(ctx, rv, nbits, sbuf)
-                ev1.record(stream)
-                torch.cuda.synchronize()
-                e_ms = ev0.elapsed_time(ev1) / reps
-                ev0.record(stream)
-                for _ in range(reps):
-                    R.rcf_bfp_decode(ctx, sbuf, nbits, dec)
-                ev1.record(stream)
-                torch.cuda.synchronize()
-                d_ms = ev0.elapsed_time(ev1) / reps
-                moved = 4.0 * n_r + sbuf.numel()          # algorithmic bytes per launch, either way
-                num = den = 0.0
-                for c0 in range(0, n_r, 1 << 27):
-                    a = rv[c0:c0 + (1 << 27)].double()
-                    num += float(((dec[c0:c0 + (1 << 27)].double() - a) ** 2).sum())
-                    den += float((a * a).sum())
-                codec[str(nbits)] = {
-                    "encode_ms": e_ms, "decode_ms": d_ms,
-                    "encode_gbs": moved / (e_ms * 1e6), "decode_gbs": moved / (d_ms * 1e6),
-                    "encode_frac": moved / (e_ms * 1e6) / peak, "decode_frac": moved / (d_ms * 1e6) / peak,
-                    "stream_bytes": int(sbuf.numel()), "rel_error_fro": (num / den) ** 0.5}
-                del sbuf
-            line["bfp_codec"] = dict(codec, values=n_r, peak_gbs=peak, bound="hbm",
-                                     data="double-float residual R of the first 256-vector block, as FP32",
-                                     note="algorithmic bytes = 4 per value + the stream; frac of the measured copy bandwidth")
-            del Rh, rv, dec
-        except Exception as exc:   # the codec is reported beside the filter, never instead of it
-            line["bfp_codec"] = {"error": repr(exc)[:300]}
+        # ---- block floating-point codec (Section III-C-3) on one residual block ----
+        line["bfp_codec"] = codec_leg(R, ctx, op, X[:blk], ritz[:blk], peak, stream)
 
         # ---- CPU oracle on a bounded sample (rank 0, one GPU only) ----
         if ws == 1 and rank == 0:
