@@ -3,7 +3,7 @@
 Steps in the paper's order: while max_j ||H x_j - eps_j M x_j|| >= tau:
 residual (FP64); filter (Eq. rChFSIrecurrence); recover Y_q; Rayleigh-Ritz
 (projected eigenproblem, subspace rotation); update lambda_min and lambda_T
-from the new Ritz values.  Readings (stated in the design doc): the initial Ritz
+from the new Ritz values.  Readings where the paper is silent: the initial Ritz
 pairs come from a Rayleigh-Ritz step on the start block, and after each cycle
 lambda_min = min Lambda, lambda_T = max Lambda; lambda_max is fixed; the
 block carries a buffer of extra vectors above the wanted ones, and the

@@ -9,8 +9,8 @@ nodes.  With the spinor row 2I + alpha (Section III-A) the potential adds the
 H_nloc (Eq. hnloc, Section III-B-3 stage iv): separable, per atom a,
 H_nloc = sum_a P_a Delta_a P_a^H with P_a the (2M x 12) cell-assembled
 projector matrix and Delta_a a 12 x 12 Hermitian spin-orbit coupling matrix.
-The paper does not give the projector form; the reading used here (stated in
-the design doc) is three real p-type Gaussians per channel j in {1/2, 3/2},
+The paper does not give the projector form; the reading used here is three
+real p-type Gaussians per channel j in {1/2, 3/2},
 beta_{j,i}(r) = N_j d_i exp(-|d|^2 / (2 s_j^2)) (d the minimum-image offset,
 cut at |d| < 5 s_j, int beta^2 = 1), and Delta_a = h_{1/2} P_{1/2} (+)
 h_{3/2} P_{3/2} with the l = 1 spin-orbit projectors
