@@ -43,6 +43,8 @@ def rchfsi_eigensolver(Hop, X0: np.ndarray, q: int, lmax: float, tol: float, max
             break
         if mode == "rchfsi":
             Y = rchfsi_filter(Hop, X, lam, lo, lT, lmax, q)
+        elif mode == "chfsi_exact_mass":
+            Y = chfsi_filter(Hop, X, lo, lT, lmax, q, exact_mass=True)
         else:
             Y = chfsi_filter(Hop, X, lo, lT, lmax, q)
         X, lam = rayleigh_ritz(Hop, Y)

@@ -5,9 +5,10 @@ Y_1 = sigma_1 (M^{-1} H - c I) X / e; here M is the GLL-lumped diagonal so
 M^{-1} is applied exactly.
 
 rchfsi_filter: Eq. rChFSIrecurrence with Z_0 = 0, Z_1 = sigma_1 R / e,
-R = H X - M X Lambda computed in FP64, Lambda_k propagated in FP64 by the
-same recurrence, and the recovery Y_q = D^{-1} Z_q + X Lambda_q
-(Algorithm 1, the recover step).  D defaults to M.
+R = H X - M X Lambda computed in FP64 (with the full mass where the operator
+has one), Lambda_k propagated in FP64 by the same recurrence, and the recovery
+Y_q = D^{-1} Z_q + X Lambda_q (Algorithm 1, the recover step).  D defaults to
+the operator's diagonal (M itself on the lumped mesh).
 
 Parity: R-ChFSI equals ChFSI exactly when D = M (a closed-form identity of the
 two recurrences); both reproduce Y_q = X C_q(Lambda) on exact eigenvectors
@@ -20,17 +21,31 @@ import numpy as np
 from .chebyshev import filter_scalars, ritz_filter_values
 
 
+def mass_times(Hop, X: np.ndarray) -> np.ndarray:
+    """M X: the full mass where the operator has one (``mass_apply``), else the diagonal M."""
+    if hasattr(Hop, "mass_apply"):
+        return Hop.mass_apply(X)
+    return Hop.Mdiag[:, None] * X if X.ndim == 2 else Hop.Mdiag * X
+
+
 def residual(Hop, X: np.ndarray, lam: np.ndarray) -> np.ndarray:
     """R = H X - M X Lambda (Algorithm 1, residual step)."""
-    return Hop.apply(X) - Hop.Mdiag[:, None] * X * np.asarray(lam)[None, :]
+    return Hop.apply(X) - mass_times(Hop, X) * np.asarray(lam)[None, :]
 
 
-def chfsi_filter(Hop, X: np.ndarray, lmin: float, lT: float, lmax: float, q: int) -> np.ndarray:
-    """Y_q = C_q(M^{-1} H) X by Eq. ChFSIrecurrence (FP64)."""
+def chfsi_filter(Hop, X: np.ndarray, lmin: float, lT: float, lmax: float, q: int,
+                 exact_mass: bool = False) -> np.ndarray:
+    """Y_q = C_q(M^{-1} H) X by Eq. ChFSIrecurrence (FP64).
+
+    M^{-1} is applied as the inverse of the operator's diagonal (``Mdiag``: M itself
+    on the lumped mesh, the diagonal D in place of a full M); with exact_mass the
+    full mass is solved exactly (``mass_solve``)."""
     c, e, sigma = filter_scalars(lmin, lT, lmax, q)
     Minv = 1.0 / Hop.Mdiag[:, None]
 
     def op(Y):  # (M^{-1} H - c) Y
+        if exact_mass:
+            return Hop.mass_solve(Hop.apply(Y)) - c * Y
         return Minv * Hop.apply(Y) - c * Y
 
     Yprev = X.copy()

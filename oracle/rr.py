@@ -27,9 +27,21 @@ def cholqr2(Y: np.ndarray, Mdiag: np.ndarray) -> np.ndarray:
     return cholqr(cholqr(Y, Mdiag), Mdiag)
 
 
+def cholqr_full(Y: np.ndarray, mass_apply) -> np.ndarray:
+    """Cholesky-QR with a full mass: S = Y^H (M Y) = L L^H, Y <- Y L^{-H}."""
+    S = Y.conj().T @ mass_apply(Y)
+    S = 0.5 * (S + S.conj().T)
+    L = np.linalg.cholesky(S)
+    return sla.solve_triangular(L, Y.conj().T, lower=True).conj().T
+
+
 def rayleigh_ritz(Hop, Y: np.ndarray):
-    """Return (X, theta): Y is M-orthonormalised by CholQR2, then A = Y^H H Y is diagonalised."""
-    Yo = cholqr2(Y, Hop.Mdiag)
+    """Return (X, theta): Y is M-orthonormalised by CholQR2 (the full M where the operator
+    has one), then A = Y^H H Y is diagonalised."""
+    if hasattr(Hop, "mass_apply"):
+        Yo = cholqr_full(cholqr_full(Y, Hop.mass_apply), Hop.mass_apply)
+    else:
+        Yo = cholqr2(Y, Hop.Mdiag)
     A = Yo.conj().T @ Hop.apply(Yo)
     A = 0.5 * (A + A.conj().T)
     theta, Q = np.linalg.eigh(A)
