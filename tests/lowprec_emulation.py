@@ -1,4 +1,5 @@
-"""CPU emulation of the R-ChFSI filter with its recurrence vectors stored in 16 bits (test helper).
+"""CPU emulation of the R-ChFSI filter with its recurrence vectors stored in 16 bits or in the
+block floating-point format of Section III-C-3 (test helper).
 
 Z_k, Z_{k-1} and R are rounded to binary16 / bfloat16 (round to nearest even) each time they are
 stored, R scaled per column by the power of two that puts its largest entry in [1/2, 1); the
@@ -38,3 +39,51 @@ def rchfsi_filter_16(Hop, X, lam, lmin, lT, lmax, q, fmt):
         Zn = a * Hop.apply(Dinv * Z) - a * c * Z - sigma[k] * sigma[k + 1] * Zprev + a * Rs * Lk[k][None, :]
         Zprev, Z = Z, round16(Zn, fmt)
     return Dinv * Z * s[None, :] + X * Lk[q][None, :]
+
+
+def bfp_round(x: np.ndarray, nbits: int) -> np.ndarray:
+    """Complex (2M, nvec) multivector rounded to FP32 and then through the block floating-point
+    format of Section III-C-3, one block per node and vector: the node's (re_up, im_up, re_dn,
+    im_dn).  Vectorised restatement of oracle.bfp (checked against it bit for bit)."""
+    v = nbits - 2
+    x = np.asarray(x)
+    n2, nv = x.shape
+    r = np.empty((n2 // 2, 4, nv), dtype=np.float32)
+    r[:, 0], r[:, 1] = x[0::2].real, x[0::2].imag
+    r[:, 2], r[:, 3] = x[1::2].real, x[1::2].imag
+    y = bfp_round_blocks(r.transpose(0, 2, 1).reshape(-1, 4), nbits).reshape(n2 // 2, nv, 4)
+    out = np.empty_like(x, dtype=np.complex128)
+    out[0::2] = y[:, :, 0] + 1j * y[:, :, 1]
+    out[1::2] = y[:, :, 2] + 1j * y[:, :, 3]
+    return out
+
+
+def bfp_round_blocks(b: np.ndarray, nbits: int) -> np.ndarray:
+    """(nblocks, 4) float32 -> the decoded values of their BFP encoding (float64)."""
+    v = nbits - 2
+    b = np.asarray(b, dtype=np.float32).astype(np.float64)
+    m = np.abs(b).max(axis=1)
+    _, ex = np.frexp(np.where(m > 0, m, 1.0))
+    emax = np.maximum(ex, -126)
+    qmax = 2.0 ** (v - 1) - 1
+    q = np.rint(np.ldexp(b, (v - 1 - emax)[:, None])) + 0.0     # integer coefficients: no -0
+    q = np.minimum(q, qmax)
+    q = np.where((emax == 128)[:, None], np.maximum(q, -qmax), q)
+    y = np.ldexp(q, (emax - v + 1)[:, None])
+    return np.where((m > 0)[:, None], y, 0.0)
+
+
+def rchfsi_filter_bfp(Hop, X, lam, lmin, lT, lmax, q, nbits):
+    """R-ChFSI with Z_k, Z_{k-1} and R stored in BFP at nbits per value (FP64 arithmetic)."""
+    c, e, sigma = filter_scalars(lmin, lT, lmax, q)
+    lam = np.asarray(lam, dtype=np.float64)
+    Dinv = 1.0 / Hop.Mdiag[:, None]
+    R = Hop.apply(X) - Hop.Mdiag[:, None] * X * lam[None, :]
+    Rs = bfp_round(R, nbits)
+    Lk = ritz_filter_values(lam, lmin, lT, lmax, q)
+    Zprev, Z = np.zeros_like(X), bfp_round((sigma[1] / e) * Rs, nbits)
+    for k in range(1, q):
+        a = 2.0 * sigma[k + 1] / e
+        Zn = a * Hop.apply(Dinv * Z) - a * c * Z - sigma[k] * sigma[k + 1] * Zprev + a * Rs * Lk[k][None, :]
+        Zprev, Z = Z, bfp_round(Zn, nbits)
+    return Dinv * Z + X * Lk[q][None, :]
