@@ -87,3 +87,17 @@ def rchfsi_filter_bfp(Hop, X, lam, lmin, lT, lmax, q, nbits):
         Zn = a * Hop.apply(Dinv * Z) - a * c * Z - sigma[k] * sigma[k + 1] * Zprev + a * Rs * Lk[k][None, :]
         Zprev, Z = Z, bfp_round(Zn, nbits)
     return Dinv * Z + X * Lk[q][None, :]
+
+
+def rayleigh_ritz_mixed_rotation(Hop, Y):
+    """Rayleigh-Ritz whose subspace rotation X = Y Q is split as in Section III-C-4:
+    Y Q_diag in FP64 plus Y Q_offdiag in FP32 (complex64 operands and products, rounded
+    back), Q_diag the diagonal of Q."""
+    from oracle.rr import cholqr2
+    Yo = cholqr2(Y, Hop.Mdiag)
+    A = Yo.conj().T @ Hop.apply(Yo)
+    A = 0.5 * (A + A.conj().T)
+    theta, Q = np.linalg.eigh(A)
+    Qd = np.diag(np.diag(Q))
+    Xo = (Yo.astype(np.complex64) @ (Q - Qd).astype(np.complex64)).astype(np.complex128)
+    return Yo @ Qd + Xo, theta

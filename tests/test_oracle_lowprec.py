@@ -119,3 +119,31 @@ def test_bfp_storage_eigensolver_follows_the_fp64_loop(near_converged):
     assert h64[-1] < 0.2 * h64[0]
     np.testing.assert_allclose(hb, h64, rtol=1e-3)
     np.testing.assert_allclose(runs["bfp12"][1][:28], runs["fp64"][1][:28], atol=1e-9)
+
+
+# ---- mixed-precision subspace rotation (Section III-C-4) ----
+
+def _loop(H, X0, rr, cycles, hi):
+    from oracle import residual
+    X, lam = rayleigh_ritz(H, X0)
+    hist = []
+    for _ in range(cycles):
+        hist.append(np.linalg.norm(residual(H, X, lam), axis=0)[:28].max())
+        Y = rchfsi_filter(H, X, lam, float(lam.min()), float(lam.max()), hi, 10)
+        X, lam = rr(H, Y)
+    return np.array(hist), lam
+
+
+def test_mixed_precision_rotation_follows_the_fp64_loop(near_converged):
+    """X = Y Q_diag (FP64) + Y Q_offdiag (FP32): from the start block and from a converged block,
+    Algorithm 1's residual history and Ritz values match the all-FP64 rotation."""
+    from lowprec_emulation import rayleigh_ritz_mixed_rotation
+    H, Xc, lam_c, b, _ = near_converged
+    w = workloads.workload("cfg1")
+    X0 = workloads.complex_normal(w.seed + 100, (H.N, w.nvec))
+    for start, cycles, rtol in ((X0, 16, 1e-6), (Xc, 6, 1e-3)):
+        h64, l64 = _loop(H, start, rayleigh_ritz, cycles, b[2])
+        hmx, lmx = _loop(H, start, rayleigh_ritz_mixed_rotation, cycles, b[2])
+        assert h64[-1] < h64[0]
+        np.testing.assert_allclose(hmx, h64, rtol=rtol)
+        np.testing.assert_allclose(lmx[:28], l64[:28], atol=1e-12)
