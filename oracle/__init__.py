@@ -26,6 +26,7 @@ from .rr import cholqr, cholqr2, rayleigh_ritz
 from .eigensolver import rchfsi_eigensolver
 from .adjoint import rchfsi_filter_adjoint, ritz_loss_head
 from .fullmass import FullMassHamiltonian, lagrange_tables
+from .poisson import laplacian, poisson_rhs, chebyshev_jacobi, pcg
 from .bfp import bfp_encode, bfp_decode, bfp_encode_block, bfp_decode_block, bfp_layout, bfp_stream_bytes
 
 __all__ = [
@@ -33,6 +34,6 @@ __all__ = [
     "p_orbital_L", "filter_scalars", "ritz_filter_values", "chebyshev_filter_closed_form",
     "chfsi_filter", "rchfsi_filter", "residual", "lanczos_bounds", "cholqr", "cholqr2",
     "rayleigh_ritz", "rchfsi_eigensolver", "rchfsi_filter_adjoint", "ritz_loss_head",
-    "FullMassHamiltonian", "lagrange_tables",
+    "FullMassHamiltonian", "lagrange_tables", "laplacian", "poisson_rhs", "chebyshev_jacobi", "pcg",
     "bfp_encode", "bfp_decode", "bfp_encode_block", "bfp_decode_block", "bfp_layout", "bfp_stream_bytes",
 ]
