@@ -101,3 +101,23 @@ def rayleigh_ritz_mixed_rotation(Hop, Y):
     Qd = np.diag(np.diag(Q))
     Xo = (Yo.astype(np.complex64) @ (Q - Qd).astype(np.complex64)).astype(np.complex128)
     return Yo @ Qd + Xo, theta
+
+
+def rchfsi_filter_fp32(Hop, X, lam, lmin, lT, lmax, q):
+    """R-ChFSI with the recurrence in FP32 (complex64 Z_k, Z_{k-1}, R; each product H D^-1 Z_k
+    rounded to FP32), the residual R = H X - M X Lambda in FP64 with the operator's own M
+    (the full mass where it has one) and D^-1 = 1 / Mdiag: Section III-C's split, on any
+    operator of the oracle."""
+    from oracle.filters import residual
+    c, e, sigma = filter_scalars(lmin, lT, lmax, q)
+    Dinv = 1.0 / Hop.Mdiag[:, None]
+    R32 = residual(Hop, X, lam).astype(np.complex64)
+    Lk = ritz_filter_values(np.asarray(lam, dtype=np.float64), lmin, lT, lmax, q)
+    Zp, Z = np.zeros_like(R32), ((sigma[1] / e) * R32).astype(np.complex64)
+    for k in range(1, q):
+        a = 2.0 * sigma[k + 1] / e
+        HZ = Hop.apply(Dinv * Z.astype(np.complex128)).astype(np.complex64)
+        Zn = (np.float32(a) * HZ - np.float32(a * c) * Z - np.float32(sigma[k] * sigma[k + 1]) * Zp
+              + np.float32(a) * R32 * Lk[k][None, :].astype(np.float32))
+        Zp, Z = Z, Zn.astype(np.complex64)
+    return Dinv * Z.astype(np.complex128) + X * Lk[q][None, :]
