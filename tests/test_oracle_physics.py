@@ -167,3 +167,53 @@ def test_projector_normalisation_converges():
         errs.append(np.max(np.abs(n2 - 1.0)))
     assert errs[2] < errs[0]
     assert errs[2] < 1e-3
+
+
+def test_projector_matrix_moments_converge_to_the_closed_form():
+    """The assembled projector columns of Eq. hnloc (Section III-B-3 stage iv) against an
+    integral in closed form.  Column (j, i, sigma) of P holds the quadrature weight of
+    int N_I beta_{j,i}, i.e. M_I beta_{j,i}(x_I) in row 2I + sigma (GLL quadrature, lumped
+    mass).  So sum_I P[2I + sigma, col] (x_I - X)_i is the GLL quadrature of
+    int beta_{j,i}(x) (x - X)_i dx = N_j s_j^2 (2 pi s_j^2)^(3/2), which converges
+    spectrally in p.  Dropping or squaring M_I, permuting the orbitals i, the channels j
+    (distinct widths) or the spin rows breaks one of the checks below by O(1)."""
+    L, X = 10.0, np.array([5.1, 4.9, 5.0])
+    widths = np.array([[0.5, 0.6]])
+    errs = []
+    errs_bound = {4: 1.6e-2, 5: 2.2e-3, 6: 2.2e-4}
+    for p in (4, 5, 6):
+        m = Mesh(5, L, p)
+        H = Hamiltonian(m, np.zeros((m.ncells, m.nloc)), None, X[None, :], widths,
+                        np.array([[0.05, 0.08]]), rcut_factor=7.0, assemble=False)
+        pr = H.projectors[0]
+        P = pr["P"]
+        d = m.node_coords()[pr["support"]] - X          # support inside the box: no wrap
+        assert P.shape == (2 * pr["support"].size, 12)
+        worst = 0.0
+        for j in range(2):
+            s = widths[0, j]
+            Nj = np.sqrt(2.0 / (np.pi ** 1.5 * s ** 5))
+            exact = Nj * s ** 2 * (2 * np.pi * s ** 2) ** 1.5
+            for i in range(3):
+                up, dn = P[:, 6 * j + 2 * i], P[:, 6 * j + 2 * i + 1]
+                # spin sigma lives in rows 2I + sigma only, with the same spatial weights
+                assert not up[1::2].any() and not dn[0::2].any()
+                assert np.array_equal(up[0::2], dn[1::2])
+                worst = max(worst, abs(up[0::2] @ d[:, i] - exact) / exact)
+                for o in range(3):                      # odd in the other coordinates
+                    if o != i:
+                        assert abs(up[0::2] @ d[:, o]) < 3 * errs_bound[p] * exact
+        errs.append(worst)
+        # centred on a cell centre the node set is symmetric: the odd moments vanish exactly
+        Hc = Hamiltonian(m, np.zeros((m.ncells, m.nloc)), None, np.array([[5.0, 5.0, 5.0]]), widths,
+                         np.array([[0.05, 0.08]]), rcut_factor=7.0, assemble=False)
+        prc = Hc.projectors[0]
+        dc = m.node_coords()[prc["support"]] - 5.0
+        for f in range(12):
+            col = prc["P"][f % 2::2, f]
+            i = (f % 6) // 2
+            for o in range(3):
+                if o != i:
+                    assert abs(col @ dc[:, o]) < 1e-13
+    # measured 1.6e-2, 2.2e-3, 2.2e-4; a missing or squared mass weight is off by a factor >> 2
+    assert errs[0] > 3 * errs[1] > 9 * errs[2] and errs[2] < 1e-3
