@@ -4,11 +4,12 @@
 Workload (default): periodic 20^3 cells, p = 5 (100^3 nodes, 2,000,000 complex
 spinor DoF), 32 atoms with spin-orbit projectors, 1024 spinor vectors filtered
 in band blocks of 256 at degree 40.  The recurrence runs in complex64 (FP32
-stencil products); X and the recovery are complex128; the residual is evaluated
-in double-float arithmetic (RCF_FP32_DF: FP64-class accuracy on the FP32 pipes).
-A step is one rcf_filter call over all 1024 vectors: X -> Y_q including the
-residual and the recovery.  Units per step = 2M * nvec * degree.  The same
-filter with the residual in native FP64 (RCF_FP32) is reported beside it.
+stencil products); X, the residual R = HX - MX Lambda and the recovery are
+complex128 (RCF_FP32: the paper's split, R in FP64).  A step is one rcf_filter
+call over all 1024 vectors: X -> Y_q including the residual and the recovery.
+Units per step = 2M * nvec * degree.  The same filter with R evaluated in
+double-float arithmetic (RCF_FP32_DF) and with 16-bit storage is reported
+beside it.
 
 Also reported on the same JSON line: the dominant kernel (the FP32 recurrence
 step) against the measured HBM copy bandwidth, the FP64 ChFSI filter on the
@@ -246,10 +247,96 @@ def traffic_record():
 
 
 
-def measured_hbm_peak() -> float:
-    """HBM copy bandwidth (GB/s) measured on this GPU model, else the fallback figure."""
+def measured_hbm_peak():
+    """(GB/s, source): the HBM copy bandwidth measured on this GPU model ("measured"), else the
+    fallback figure of an earlier GB300 measurement ("fallback")."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    return json.load(open(path))["hbm_gbs"] if os.path.exists(path) else 6800.0
+    if os.path.exists(path):
+        return float(json.load(open(path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+HEADLINE_PRECISION = ("recurrence and stencil products complex64 (FP32); X, the residual R = HX - MX Lambda "
+                      "and the recovery complex128 (FP64), R rounded to complex64 for the recurrence "
+                      "(RCF_FP32: the paper's split)")
+
+
+def assemble_line(w, ws: int, steps: int, warmup: int, m: dict) -> dict:
+    """The bench's JSON line from the measurements in m (times in ms, per rank maxima).
+
+    Keys of m: ms (headline step), launches, clocks, N, nvec, degree, l2_gb, peak (GB/s, source),
+    traffic (record or None), variants_ms {df_residual, fp16_storage, bf16_storage}, kernel
+    {blk, k_ms, step_ms, k16_ms}, residual {df_ms, fp64_ms}; optional fp64_chfsi {blk, f64_ms,
+    mix_ms}, e2e {ms, ne, h2d, d2h, sample, link}, adjoint, bfp_codec, cpu_baseline {value, dt}."""
+    N, nvec, q = m["N"], m["nvec"], m["degree"]
+    units = float(N) * nvec * q
+    rate = lambda ms: units * ws / (ms * 1e-3)
+    peak, peak_source = m["peak"]
+    line = {
+        "metric": METRIC, "value": rate(m["ms"]), "unit": UNIT, "n_gpus": ws, "steps": steps,
+        "warmup": warmup, "ms_per_step": m["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": describe(w), "precision": HEADLINE_PRECISION,
+                   "l2": "inputs larger than L2 (X and Y are %.1f GB each)" % m["l2_gb"],
+                   "parallelism": "band partitioning, one GPU per column group (no filter communication)"
+                                  if ws > 1 else "single GPU"},
+        "gpu_launches": int(m["launches"]),
+        "clocks": m["clocks"],
+    }
+    vm = m["variants_ms"]
+    line["variants"] = {
+        "df_residual": {"value": rate(vm["df_residual"]), "unit": UNIT, "ms_per_step": vm["df_residual"],
+                        "precision": "as the headline with R evaluated in double-float arithmetic (pairs of "
+                                     "FP32, about 2^-46 of the term magnitudes; RCF_FP32_DF)"},
+        "fp16_storage": {"value": rate(vm["fp16_storage"]), "unit": UNIT, "ms_per_step": vm["fp16_storage"],
+                         "precision": "Z_k, Z_{k-1}, R stored as binary16 pairs (R scaled per column), "
+                                      "products in FP32, double-float residual (RCF_FP16)"},
+        "bf16_storage": {"value": rate(vm["bf16_storage"]), "unit": UNIT, "ms_per_step": vm["bf16_storage"],
+                         "precision": "as fp16_storage with bfloat16 (RCF_BF16)"},
+    }
+    k = m["kernel"]
+    blk = k["blk"]
+    alg = BYTES_PER_UNIT * N * blk
+    achieved = alg / (k["k_ms"] * 1e-3) / 1e9
+    tr = m["traffic"]
+    line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": (tr["bytes_per_launch_full_block"] if tr else None),
+                        "kernel": "step_kernel<float,%d> (FP32 R-ChFSI recurrence step, %d vectors)" % (w.p, blk),
+                        "kernel_ms": k["k_ms"], "algorithmic_bytes": alg, "peak_source": peak_source,
+                        "step_with_projectors_ms": k["step_ms"]}
+    a16 = 16.0 * N * blk / (k["k16_ms"] * 1e-3) / 1e9
+    line["roofline_fp16_step"] = {"bound": "hbm", "achieved": a16, "peak": peak, "unit": "GB/s",
+                                  "frac": a16 / peak, "kernel_ms": k["k16_ms"], "algorithmic_bytes": 16.0 * N * blk,
+                                  "kernel": "step_kernel<float,__half,%d> (recurrence step, vectors stored as "
+                                            "binary16)" % w.p}
+    r = m["residual"]
+    line["residual"] = {"fp64_ms": r["fp64_ms"], "double_float_ms": r["df_ms"], "vectors": blk,
+                        "note": "R = H X - M X Lambda of one block, spin-orbit terms included"}
+    if "fp64_chfsi" in m:
+        f = m["fp64_chfsi"]
+        line["fp64_chfsi"] = {"value": float(N) * f["blk"] * q * ws / (f["f64_ms"] * 1e-3), "unit": UNIT,
+                              "ms_one_block": f["f64_ms"], "mixed_rchfsi_ms_one_block": f["mix_ms"],
+                              "speedup_mixed_over_fp64": f["f64_ms"] / f["mix_ms"],
+                              "sample": "one block of %d vectors, degree %d; mixed = the headline "
+                                        "arithmetic (RCF_FP32)" % (f["blk"], q)}
+    if "e2e" in m:
+        e = m["e2e"]
+        line["e2e"] = {"value": float(N) * e["ne"] * q * ws / (e["ms"] * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": int(e["h2d"]), "d2h_bytes_per_step": int(e["d2h"]),
+                       "ms_per_step": e["ms"], "sample": e["sample"], "link": e["link"],
+                       "call": "rcf_filter_host, RCF_FP32 (pinned host X and Y; wall clock around the "
+                               "synchronising call)"}
+    for key in ("adjoint", "bfp_codec"):
+        if key in m:
+            line[key] = m[key]
+    if "cpu_baseline" in m:
+        c = m["cpu_baseline"]
+        line["cpu_baseline"] = {"value": c["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"oracle R-ChFSI filter (NumPy/SciPy FP64, single-threaded CSR "
+                                          f"products) on the full mesh, {ORACLE_NV} vectors, degree "
+                                          f"{ORACLE_Q}: {c['dt']:.1f} s",
+                                "host_cores": os.cpu_count()}
+    return line
 
 
 def codec_leg(R, ctx, op, Xb, ritz_b, peak, stream):
@@ -332,22 +419,34 @@ def run_ours(args):
     lT = lo + 0.05 * (hi - lo)
     ritz = np.linspace(lo, lT, nvec, endpoint=False)
     bounds = (lo - 1e-3 * abs(lo), lT, hi)
+    peak = measured_hbm_peak()
     if args.codec_only:
         if rank == 0:
-            obj = codec_leg(R, ctx, op, X[:w.block], ritz[:w.block], measured_hbm_peak(), stream)
+            obj = codec_leg(R, ctx, op, X[:w.block], ritz[:w.block], peak[0], stream)
             print(json.dumps({"bfp_codec": obj, "config": {"workload": describe(w)}}), flush=True)
         prob.close()
         return 0
 
-    def step(prec=R.RCF_FP32_DF):
+    def step(prec=R.RCF_FP32):
         R.rcf_filter(ctx, op, X, ritz, q, bounds, R.RCF_RCHFSI, prec, w.block, Y)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        """Average ms of fn over reps calls, CUDA events on the library's stream."""
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     barrier(ws)
     l0 = R.rcf_launch_count(ctx)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
         barrier(ws)
@@ -357,48 +456,21 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier(ws)
-    launches = (R.rcf_launch_count(ctx) - l0)
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ms = max_over_ranks(ws, ms)
-    units = float(N) * nvec * q
-    value = units * ws / (ms * 1e-3)
+    m = {"launches": R.rcf_launch_count(ctx) - l0, "clocks": clk.summary(),
+         "ms": max_over_ranks(ws, ev0.elapsed_time(ev1) / args.steps),
+         "N": N, "nvec": nvec, "degree": q, "l2_gb": X.numel() * 16 / 1e9, "peak": peak,
+         "traffic": traffic_record()}
 
-    # the same filter with the residual in native FP64, and with the recurrence stored in 16 bits
+    # the same filter with the residual in double-float arithmetic, and with the recurrence
+    # stored in 16 bits
     def time_variant(prec):
         step(prec)
-        torch.cuda.synchronize()
         barrier(ws)
-        ev0.record(stream)
-        for _ in range(max(1, args.steps - 1)):
-            step(prec)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        return max_over_ranks(ws, ev0.elapsed_time(ev1) / max(1, args.steps - 1))
+        return max_over_ranks(ws, timed(lambda: step(prec), max(1, args.steps - 1)))
 
-    ms64 = time_variant(R.RCF_FP32)
-    ms16 = time_variant(R.RCF_FP16)
-    msb16 = time_variant(R.RCF_BF16)
-
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": describe(w),
-                   "precision": "recurrence and stencil products complex64 (FP32); X and recovery complex128; "
-                                "residual in double-float arithmetic (pairs of FP32, FP64-class), rounded to complex64",
-                   "l2": "inputs larger than L2 (X and Y are %.1f GB each)" % (X.numel() * 16 / 1e9),
-                   "parallelism": "band partitioning, one GPU per column group (no filter communication)"
-                                  if ws > 1 else "single GPU"},
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
-        "variants": {"fp64_residual": {"value": units * ws / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
-                                       "precision": "as above with the residual in native FP64 (RCF_FP32)"},
-                     "fp16_storage": {"value": units * ws / (ms16 * 1e-3), "unit": UNIT, "ms_per_step": ms16,
-                                      "precision": "Z_k, Z_{k-1}, R stored as binary16 pairs (R scaled per column), "
-                                                   "products in FP32, double-float residual (RCF_FP16)"},
-                     "bf16_storage": {"value": units * ws / (msb16 * 1e-3), "unit": UNIT, "ms_per_step": msb16,
-                                      "precision": "as fp16_storage with bfloat16 (RCF_BF16)"}},
-    }
+    m["variants_ms"] = {"df_residual": time_variant(R.RCF_FP32_DF),
+                        "fp16_storage": time_variant(R.RCF_FP16),
+                        "bf16_storage": time_variant(R.RCF_BF16)}
 
     # ---- dominant kernel: one FP32 recurrence step on a block, timed alone ----
     blk = min(w.block, nvec)
@@ -408,93 +480,40 @@ def run_ours(args):
     Zm = torch.randn((blk, N), dtype=torch.complex64, device=dev, generator=gen)
     Rr = torch.randn((blk, N), dtype=torch.complex64, device=dev, generator=gen)
     g = torch.full((blk,), 0.25, dtype=torch.float64, device=dev)
-    nrep = 10
-    for _ in range(3):
-        R.rcf_cheb_step(ctx, op1, R.RCF_FORM_H_DINV, R.RCF_FP32, Zk, Zm, Rr, 0.1, -0.5, -1.0, g, Zm)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(nrep):
-        R.rcf_cheb_step(ctx, op1, R.RCF_FORM_H_DINV, R.RCF_FP32, Zk, Zm, Rr, 0.1, -0.5, -1.0, g, Zm)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    k_ms = ev0.elapsed_time(ev1) / nrep
-    # the same step with the projectors (four launches)
-    ev0.record(stream)
-    for _ in range(nrep):
-        R.rcf_cheb_step(ctx, op, R.RCF_FORM_H_DINV, R.RCF_FP32, Zk, Zm, Rr, 0.1, -0.5, -1.0, g, Zm)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    step_ms = ev0.elapsed_time(ev1) / nrep
+    st = lambda o: R.rcf_cheb_step(ctx, o, R.RCF_FORM_H_DINV, R.RCF_FP32, Zk, Zm, Rr, 0.1, -0.5, -1.0, g, Zm)
+    timed(lambda: st(op1), 3)
+    kern = {"blk": blk, "k_ms": timed(lambda: st(op1), 10),
+            "step_ms": timed(lambda: st(op), 10)}       # with the projectors (four launches)
     # the same step with the vectors stored as binary16 (16 B per unit)
     zk16 = torch.view_as_real(Zk).reshape(blk, -1).to(torch.float16)
     zm16 = torch.view_as_real(Zm).reshape(blk, -1).to(torch.float16)
     rr16 = torch.view_as_real(Rr).reshape(blk, -1).to(torch.float16)
-    for _ in range(3):
-        R.rcf_cheb_step(ctx, op1, R.RCF_FORM_H_DINV, R.RCF_FP16, zk16, zm16, rr16, 0.1, -0.5, -1.0, g, zm16)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(nrep):
-        R.rcf_cheb_step(ctx, op1, R.RCF_FORM_H_DINV, R.RCF_FP16, zk16, zm16, rr16, 0.1, -0.5, -1.0, g, zm16)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    k16_ms = ev0.elapsed_time(ev1) / nrep
+    st16 = lambda: R.rcf_cheb_step(ctx, op1, R.RCF_FORM_H_DINV, R.RCF_FP16, zk16, zm16, rr16,
+                                   0.1, -0.5, -1.0, g, zm16)
+    timed(st16, 3)
+    kern["k16_ms"] = timed(st16, 10)
+    m["kernel"] = kern
     del zk16, zm16, rr16
     R.rcf_op_destroy(op1)
     del Zk, Zm, Rr
-    # the residual of one block: double-float (the headline path) and native FP64
+    # the residual of one block: native FP64 (the headline path) and double-float
+    R64 = torch.empty((blk, N), dtype=torch.complex128, device=dev)
+    R.rcf_residual(ctx, op, X[:blk], ritz[:blk], R64)
+    res64 = timed(lambda: R.rcf_residual(ctx, op, X[:blk], ritz[:blk], R64), 1)
+    del R64
     Rh = torch.empty((blk, N), dtype=torch.complex64, device=dev)
     R.rcf_residual_df(ctx, op, X[:blk], ritz[:blk], Rh)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    R.rcf_residual_df(ctx, op, X[:blk], ritz[:blk], Rh)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    res_df_ms = ev0.elapsed_time(ev1)
+    m["residual"] = {"fp64_ms": res64,
+                     "df_ms": timed(lambda: R.rcf_residual_df(ctx, op, X[:blk], ritz[:blk], Rh), 1)}
     del Rh
-    R64 = torch.empty((blk, N), dtype=torch.complex128, device=dev)
-    ev0.record(stream)
-    R.rcf_residual(ctx, op, X[:blk], ritz[:blk], R64)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    res64_ms = ev0.elapsed_time(ev1)
-    del R64
-    peak = measured_hbm_peak()
-    achieved = BYTES_PER_UNIT * N * blk / (k_ms * 1e-3) / 1e9
-    tr = traffic_record()
-    line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": (tr["bytes_per_launch_full_block"] if tr else None),
-                        "kernel": "step_kernel<float,5> (FP32 R-ChFSI recurrence step, %d vectors)" % blk,
-                        "kernel_ms": k_ms, "algorithmic_bytes": BYTES_PER_UNIT * N * blk,
-                        "peak_source": "measured" if peaks else "fallback",
-                        "step_with_projectors_ms": step_ms}
-    line["roofline_fp16_step"] = {"bound": "hbm", "achieved": 16.0 * N * blk / (k16_ms * 1e-3) / 1e9, "peak": peak,
-                                  "unit": "GB/s", "frac": 16.0 * N * blk / (k16_ms * 1e-3) / 1e9 / peak,
-                                  "kernel_ms": k16_ms, "algorithmic_bytes": 16.0 * N * blk,
-                                  "kernel": "step_kernel<float,__half,5> (recurrence step, vectors stored as binary16)"}
-    line["residual"] = {"double_float_ms": res_df_ms, "fp64_ms": res64_ms, "vectors": blk,
-                        "note": "R = H X - M X Lambda of one block, spin-orbit terms included"}
 
     if not args.no_extras:
-        # ---- FP64 ChFSI on one block, same mesh and degree ----
-        Xb = X[:blk]
-        Yb = Y[:blk]
-        R.rcf_filter(ctx, op, Xb, ritz[:blk], q, bounds, R.RCF_CHFSI, R.RCF_FP64, blk, Yb)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        R.rcf_filter(ctx, op, Xb, ritz[:blk], q, bounds, R.RCF_CHFSI, R.RCF_FP64, blk, Yb)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        f64_ms = ev0.elapsed_time(ev1)
-        f64_val = float(N) * blk * q / (f64_ms * 1e-3)
-        # the mixed filter on the same single block, for a like-for-like ratio
-        ev0.record(stream)
-        R.rcf_filter(ctx, op, Xb, ritz[:blk], q, bounds, R.RCF_RCHFSI, R.RCF_FP32_DF, blk, Yb)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        mix_ms = ev0.elapsed_time(ev1)
-        line["fp64_chfsi"] = {"value": f64_val * ws, "unit": UNIT, "ms_one_block": f64_ms,
-                              "mixed_rchfsi_ms_one_block": mix_ms, "speedup_mixed_over_fp64": f64_ms / mix_ms,
-                              "sample": f"one block of {blk} vectors, degree {q}"}
+        # ---- FP64 ChFSI on one block, same mesh and degree, beside the headline filter ----
+        Xb, Yb = X[:blk], Y[:blk]
+        f64 = lambda: R.rcf_filter(ctx, op, Xb, ritz[:blk], q, bounds, R.RCF_CHFSI, R.RCF_FP64, blk, Yb)
+        mix = lambda: R.rcf_filter(ctx, op, Xb, ritz[:blk], q, bounds, R.RCF_RCHFSI, R.RCF_FP32, blk, Yb)
+        f64()
+        m["fp64_chfsi"] = {"blk": blk, "f64_ms": timed(f64, 1), "mix_ms": timed(mix, 1)}
 
         # ---- end to end through the C ABI with host buffers ----
         try:
@@ -510,14 +529,14 @@ def run_ours(args):
         ne = Xh.shape[0]
         # the C ABI's host-buffer filter: band blocks stream through device slots, copies in
         # and out overlapping the filtering of the neighbouring blocks
-        R.rcf_filter_host(ctx, op, Xh, ritz[:ne], q, bounds, R.RCF_RCHFSI, R.RCF_FP32_DF, w.block, Yh)
+        host = lambda: R.rcf_filter_host(ctx, op, Xh, ritz[:ne], q, bounds, R.RCF_RCHFSI, R.RCF_FP32, w.block, Yh)
+        host()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(max(1, args.steps)):
-            R.rcf_filter_host(ctx, op, Xh, ritz[:ne], q, bounds, R.RCF_RCHFSI, R.RCF_FP32_DF, w.block, Yh)
+            host()
         torch.cuda.synchronize()
-        e_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
-        e_ms = max_over_ranks(ws, e_ms)
+        e_ms = max_over_ranks(ws, (time.perf_counter() - t0) * 1e3 / max(1, args.steps))
         # the host link of this machine, pinned buffers, one direction at a time (the
         # end-to-end time cannot fall below the larger of the two copy times)
         nl = min(64, ne)
@@ -534,11 +553,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             link[name] = 3 * dbuf.numel() * 16 / (e0.elapsed_time(e1) * 1e6)
         del dbuf
-        line["e2e"] = {"value": float(N) * ne * q * ws / (e_ms * 1e-3), "unit": UNIT,
-                       "h2d_bytes_per_step": int(Xh.numel() * 16), "d2h_bytes_per_step": int(Yh.numel() * 16),
-                       "ms_per_step": e_ms, "sample": sample,
-                       "link": link,
-                       "call": "rcf_filter_host (pinned host X and Y; wall clock around the synchronising call)"}
+        m["e2e"] = {"ms": e_ms, "ne": ne, "h2d": Xh.numel() * 16, "d2h": Yh.numel() * 16,
+                    "sample": sample, "link": link}
         del Xh, Yh
 
         # ---- the adjoint filter on the 8^3-cell p = 4 workload (64 vectors, degree 15,
@@ -552,40 +568,32 @@ def run_ours(args):
         ra = np.linspace(la, la + 0.05 * (ha - la), wa.nvec, endpoint=False)
         ba = (la - 1e-3 * abs(la), la + 0.05 * (ha - la), ha)
         Ya = torch.empty_like(Xa)
-        Yb = torch.randn_like(Xa)
+        Ybar = torch.randn_like(Xa)
         dV = torch.zeros((pa_.ncells, pa_.nloc), dtype=torch.float64, device=dev)
         dB = torch.zeros((3, pa_.ncells, pa_.nloc), dtype=torch.float64, device=dev)
         adj = {}
         for pname, prec in (("fp64", R.RCF_FP64), ("fp32", R.RCF_FP32)):
             fwd = lambda: R.rcf_filter(pa_.ctx, pa_.op, Xa, ra, wa.degree, ba, R.RCF_RCHFSI, prec, wa.nvec, Ya)
-            bwd = lambda: R.rcf_adjoint_filter(pa_.ctx, pa_.op, Xa, ra, wa.degree, ba, R.RCF_RCHFSI, prec, Yb,
+            bwd = lambda: R.rcf_adjoint_filter(pa_.ctx, pa_.op, Xa, ra, wa.degree, ba, R.RCF_RCHFSI, prec, Ybar,
                                                wa.ckpt, dV, dB, None)
             fwd(); bwd()
-            torch.cuda.synchronize()
-            ev0.record(stream); fwd(); ev1.record(stream); torch.cuda.synchronize()
-            f_ms = ev0.elapsed_time(ev1)
-            ev0.record(stream); bwd(); ev1.record(stream); torch.cuda.synchronize()
-            b_ms = ev0.elapsed_time(ev1)
+            f_ms, b_ms = timed(fwd, 1), timed(bwd, 1)
             adj[pname] = {"forward_ms": f_ms, "adjoint_ms": b_ms, "ratio": b_ms / f_ms}
-        line["adjoint"] = dict(adj, workload=describe(wa), note="adjoint w.r.t. V, B at all quadrature "
-                               "points, checkpoints every %d steps" % wa.ckpt)
+        m["adjoint"] = dict(adj, workload=describe(wa), note="adjoint w.r.t. V, B at all quadrature "
+                            "points, checkpoints every %d steps" % wa.ckpt)
         pa_.close()
-        del Xa, Ya, Yb, dV, dB
+        del Xa, Ya, Ybar, dV, dB
 
         # ---- block floating-point codec (Section III-C-3) on one residual block ----
-        line["bfp_codec"] = codec_leg(R, ctx, op, X[:blk], ritz[:blk], peak, stream)
+        m["bfp_codec"] = codec_leg(R, ctx, op, X[:blk], ritz[:blk], peak[0], stream)
 
         # ---- CPU oracle on a bounded sample (rank 0, one GPU only) ----
         if ws == 1 and rank == 0:
             H = oracle_setup(w)
             v, dt = oracle_sample(H, ORACLE_NV, ORACLE_Q, 700)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": f"oracle R-ChFSI filter (NumPy/SciPy FP64, single-threaded CSR "
-                                              f"products) on the full mesh, {ORACLE_NV} vectors, degree "
-                                              f"{ORACLE_Q}: {dt:.1f} s",
-                                    "host_cores": os.cpu_count()}
+            m["cpu_baseline"] = {"value": v, "dt": dt}
     if rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(assemble_line(w, ws, args.steps, args.warmup, m)), flush=True)
     prob.close()
     return 0
 
