@@ -182,6 +182,16 @@ int64_t rcf_launch_count(const rcf_ctx* ctx);
  * RCF_EINVAL for an unknown kind.  Takes effect at the next launch. */
 int rcf_set_step_kernel(rcf_ctx* ctx, int kind);
 
+/* Limit, in polls, of every bounded device-side wait of this context's kernels
+ * (the mbarrier waits of the TMA step kernel; library-specific, the paper has
+ * no counterpart).  Default 2^24.  A wait that reaches the limit makes its
+ * kernel record a time-out in the context's device error word and return early
+ * (after its own copies in flight have landed, under a separate fixed limit);
+ * the next synchronising call then returns RCF_ETIMEOUT and clears the word, and
+ * the context stays usable.  0 makes every such wait give up at once (used to
+ * test this path).  Returns RCF_EINVAL for a negative limit. */
+int rcf_set_wait_limit(rcf_ctx* ctx, int64_t polls);
+
 /* Arithmetic of the Gram matrix of Cholesky-QR and of the projected matrix
  * Y^H H Y of Rayleigh-Ritz (library-specific; the paper has no counterpart).
  * RCF_RR_FP64 (default): cuBLAS ZHERK / ZGEMM in FP64.  RCF_RR_DF: this
@@ -273,6 +283,22 @@ int rcf_rayleigh_ritz_orth(rcf_ctx* ctx, const rcf_op* op, const double* Y, int6
 int rcf_grad_bilinear(rcf_ctx* ctx, const rcf_op* op, const double* W, int64_t ldw,
                       const double* U, int64_t ldu, int nvec, double weight,
                       double* dV, double* dB, double* dh);
+
+/* Cotangent of the Rayleigh-Ritz values (derivative of the eigenvalues of the
+ * projected pencil; the paper has no counterpart).  Given Y (c128, nvec columns)
+ * and its Rayleigh-Ritz pairs (theta: host [nvec], X: c128, X = Y Q with X
+ * M-orthonormal, as returned by rcf_rayleigh_ritz for the Y it started from),
+ * and thetabar = dL/dtheta (host [nvec]), writes
+ *   Ybar = dL/dY = sum_j 2 thetabar_j (H - theta_j M) x_j q_j^H
+ * (c128, must not overlap Y or X), with Q = (Y^H M Y)^{-1} Y^H M X (FP64; the
+ * Gram matrix must be positive definite, else RCF_ENOTSPD), and, when dV and dB
+ * are given (device, layouts as in rcf_potential_set; dh host [natoms][2] or
+ * NULL), accumulates (+=) the direct term sum_j thetabar_j x_j^H (dH) x_j.
+ * Synchronises. */
+int rcf_ritz_cotangent(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy,
+                       const double* X, int64_t ldx, int nvec, const double* theta,
+                       const double* thetabar, double* Ybar, int64_t ldb, double* dV,
+                       double* dB, double* dh);
 
 /* Reverse-mode derivative of the R-ChFSI filter (X, Lambda and the bounds held
  * constant): given Ybar = dL/dY (c128), accumulate (+=) dL/dV, dL/dB (device,

@@ -6,9 +6,7 @@ its backward is one ``rcf_adjoint_filter`` call (the reverse recurrence with
 checkpoints, all in the library's kernels).  ``RitzValues`` maps a block Y (and
 the operator) to its Rayleigh-Ritz values; its backward gives
 dtheta_j = 2 Re x_j^H (H - theta_j M) dY q_j + x_j^H dH x_j, with x_j = Y q_j the
-M-normalised Ritz vectors (the residual and the dH term come from
-``rcf_residual`` and ``rcf_grad_bilinear``; only the small N_e x N_e solve for
-q_j and the N x N_e rotation run as torch matrix products).
+M-normalised Ritz vectors, all of it in one ``rcf_ritz_cotangent`` call.
 """
 from __future__ import annotations
 
@@ -83,19 +81,11 @@ class RitzValues(torch.autograd.Function):
         Y, Xr, th, V, B, h = ctx.saved_tensors
         opw = ctx.opw
         opw.set(V, B, h)
-        # q_j: Y Q = Xr  ->  Q = (Y^H M Y)^{-1} Y^H M Xr   (rows of the tensors are vectors)
-        MY = Y * opw.mdiag[None, :]
-        S = MY.conj() @ Y.T                       # S[i, j] = y_i^H M y_j
-        T = MY.conj() @ Xr.T                      # T[i, j] = y_i^H M x_j
-        Q = torch.linalg.solve(S, T)              # columns q_j
-        Rx = torch.empty_like(Xr)
-        R.rcf_residual(opw.ctx, opw.op, Xr, th.cpu().numpy(), Rx, None)   # (H - theta_j M) x_j
-        w = thbar.to(Rx.dtype)
-        Ybar = 2.0 * (Q.conj() * w[None, :]) @ Rx  # Ybar_i = sum_j 2 thbar_j conj(Q_ij) r_j
+        Ybar = torch.empty_like(Y)
         dV = torch.zeros_like(V)
         dB = torch.zeros_like(B)
         dh = np.zeros((max(opw.natoms, 1), 2))
-        W = Xr * thbar.to(Xr.dtype)[:, None]
-        R.rcf_grad_bilinear(opw.ctx, opw.op, W.contiguous(), Xr, 1.0, dV, dB, dh if opw.natoms else None)
+        R.rcf_ritz_cotangent(opw.ctx, opw.op, Y.detach().contiguous(), Xr, th.cpu().numpy(),
+                             thbar.detach().cpu().numpy(), Ybar, dV, dB, dh if opw.natoms else None)
         dht = torch.from_numpy(dh[:opw.natoms]).to(h.device, h.dtype) if opw.natoms else torch.zeros_like(h)
         return Ybar, dV, dB, dht, None

@@ -230,6 +230,13 @@ extern "C" int rcf_set_rr_arith(rcf_ctx* ctx, int kind) {
   return RCF_OK;
 }
 
+extern "C" int rcf_set_wait_limit(rcf_ctx* ctx, int64_t polls) {
+  if (!ctx) return RCF_EINVAL;
+  if (polls < 0) return fail(ctx, RCF_EINVAL, "wait limit must be >= 0 polls");
+  ctx->wait_limit = polls;
+  return RCF_OK;
+}
+
 extern "C" int rcf_destroy(rcf_ctx* ctx) {
   if (!ctx) return RCF_OK;
   cudaStreamSynchronize(ctx->stream);

@@ -101,10 +101,16 @@ int cholqr_pass(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int n, b
   RCF_TRY(workspace(ctx, WS_RR_WORK, sizeof(cuDoubleComplex) * size_t(std::max(lwork, 1)), reinterpret_cast<void**>(&work)));
   RCF_SOLVER(ctx, cusolverDnZpotrf(ctx->solver, CUBLAS_FILL_MODE_LOWER, n, S, n, work, lwork, info));
   int hinfo = 0;
+  std::vector<cuDoubleComplex> diag(n);   // the factor's diagonal: a NaN in Y leaves it non-finite
+  RCF_CUDA(ctx, cudaMemcpy2DAsync(diag.data(), sizeof(cuDoubleComplex), S, sizeof(cuDoubleComplex) * (n + 1),
+                                  sizeof(cuDoubleComplex), n, cudaMemcpyDeviceToHost, ctx->stream));
   RCF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   if (hinfo != 0)
     return fail(ctx, RCF_ENOTSPD, "Cholesky-QR: Gram matrix not positive definite (pivot %d)", hinfo);
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(diag[i].x) || !(diag[i].x > 0.0))
+      return fail(ctx, RCF_ENOTSPD, "Cholesky-QR: Gram factor not finite and positive (column %d)", i + 1);
   const cuDoubleComplex onec = make_cuDoubleComplex(1.0, 0.0);
   RCF_BLAS(ctx, cublasZtrsm(ctx->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C,
                             CUBLAS_DIAG_NON_UNIT, int(N), n, &onec, S, n,
@@ -226,4 +232,134 @@ extern "C" int rcf_rayleigh_ritz(rcf_ctx* ctx, const rcf_op* op, double* Y, int6
   RCF_TRY(check_xy(ctx, op, Y, ldy, nvec, X_out, ldx, ritz_out));
   RCF_TRY(cholqr2(ctx, op, Y, ldy, nvec));
   return rr_orth(ctx, op, Y, ldy, nvec, X_out, ldx, ritz_out);
+}
+
+// ---------------------------------------------------------------------------
+// cotangent of the Ritz values (no counterpart in the paper)
+// ---------------------------------------------------------------------------
+namespace rcf {
+namespace {
+
+// W[v][r] = M_I Y[v][r0 + r], I = (r0 + r) / 2, for complex rows r < cr
+__global__ void mass_rows_kernel(const double* __restrict__ mass, const double* __restrict__ Y,
+                                 int64_t ldy, int64_t r0, int64_t cr, double* __restrict__ W) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (r >= cr) return;
+  const double s = mass[(r0 + r) >> 1];
+  const double2 y = reinterpret_cast<const double2*>(Y + 2 * int64_t(v) * ldy)[r0 + r];
+  reinterpret_cast<double2*>(W + 2 * int64_t(v) * cr)[r] = make_double2(s * y.x, s * y.y);
+}
+
+// y[v][r] = s[v] x[v][r] (complex rows r < rows)
+__global__ void scale_cols_kernel(int64_t rows, const double* __restrict__ x, int64_t ldx,
+                                  const double* __restrict__ s, double* __restrict__ y, int64_t ldy) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (r >= rows) return;
+  const double2 a = reinterpret_cast<const double2*>(x + 2 * int64_t(v) * ldx)[r];
+  reinterpret_cast<double2*>(y + 2 * int64_t(v) * ldy)[r] = make_double2(s[v] * a.x, s[v] * a.y);
+}
+
+// C (m x n) = A^H M B over all rows (A, B c128 column blocks), FP64 ZGEMM over row chunks
+int gemm_tn_mass(rcf_ctx* ctx, const rcf_op* op, const double* A, int64_t lda, int m, const double* B,
+                 int64_t ldb, int n, cuDoubleComplex* C) {
+  const int64_t N = 2 * op->mesh->nnodes;
+  int64_t cr = std::max<int64_t>(1024, (int64_t(1) << 26) / std::max(n, 1));
+  cr = std::min<int64_t>(cr, N);
+  double* W = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_W, sizeof(double) * 2 * size_t(cr) * n, reinterpret_cast<void**>(&W)));
+  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+  for (int64_t r0 = 0; r0 < N; r0 += cr) {
+    const int64_t c = std::min(cr, N - r0);
+    mass_rows_kernel<<<dim3(unsigned((c + 255) / 256), n), 256, 0, ctx->stream>>>(
+        op->mesh->d_mass, B, ldb, r0, c, W);            // W = M B on rows r0 .. r0 + c
+    RCF_CHECK_LAUNCH(ctx);
+    RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, n, int(c), &one,
+                              reinterpret_cast<const cuDoubleComplex*>(A + 2 * r0), int(lda),
+                              reinterpret_cast<const cuDoubleComplex*>(W), int(c),
+                              r0 == 0 ? &zero : &one, C, m));
+  }
+  return RCF_OK;
+}
+
+}  // namespace
+}  // namespace rcf
+
+extern "C" int rcf_ritz_cotangent(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy,
+                                  const double* X, int64_t ldx, int nvec, const double* theta,
+                                  const double* thetabar, double* Ybar, int64_t ldb, double* dV,
+                                  double* dB, double* dh) {
+  if (!ctx || !op) return RCF_EINVAL;
+  RCF_TRY(check_y(ctx, op, Y, ldy, nvec));
+  RCF_TRY(check_y(ctx, op, X, ldx, nvec));
+  RCF_TRY(check_y(ctx, op, Ybar, ldb, nvec));
+  if (!theta || !thetabar) return fail(ctx, RCF_EINVAL, "theta and thetabar must be host arrays");
+  if ((dV == nullptr) != (dB == nullptr)) return fail(ctx, RCF_EINVAL, "dV and dB must both be given or both NULL");
+  const int n = nvec;
+  const int64_t N = 2 * op->mesh->nnodes;
+  auto overl = [&](const double* a, int64_t la, const double* b, int64_t lb) {
+    const char* a0 = reinterpret_cast<const char*>(a);
+    const char* b0 = reinterpret_cast<const char*>(b);
+    return a0 < b0 + size_t(lb) * n * 16 && b0 < a0 + size_t(la) * n * 16;
+  };
+  if (overl(Ybar, ldb, Y, ldy) || overl(Ybar, ldb, X, ldx)) return fail(ctx, RCF_EINVAL, "Ybar overlaps Y or X");
+  // S = Y^H M Y and T = Y^H M X (n x n); Q = S^-1 T, so that X = Y Q
+  cuDoubleComplex *S = nullptr, *T = nullptr, *Cm = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_S, sizeof(cuDoubleComplex) * 3 * size_t(n) * n, reinterpret_cast<void**>(&S)));
+  T = S + size_t(n) * n;
+  Cm = T + size_t(n) * n;
+  RCF_TRY(gemm_tn_mass(ctx, op, Y, ldy, n, Y, ldy, n, S));
+  RCF_TRY(gemm_tn_mass(ctx, op, Y, ldy, n, X, ldx, n, T));
+  int* info = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_INFO, sizeof(int) * 4, reinterpret_cast<void**>(&info)));
+  int lwork = 0;
+  RCF_SOLVER(ctx, cusolverDnZpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_LOWER, n, S, n, &lwork));
+  cuDoubleComplex* work = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_WORK, sizeof(cuDoubleComplex) * size_t(std::max(lwork, 1)), reinterpret_cast<void**>(&work)));
+  RCF_SOLVER(ctx, cusolverDnZpotrf(ctx->solver, CUBLAS_FILL_MODE_LOWER, n, S, n, work, lwork, info));
+  int hinfo = 0;
+  RCF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (hinfo != 0) return fail(ctx, RCF_ENOTSPD, "Ritz cotangent: Y^H M Y not positive definite (pivot %d)", hinfo);
+  RCF_SOLVER(ctx, cusolverDnZpotrs(ctx->solver, CUBLAS_FILL_MODE_LOWER, n, n, S, n, T, n, info));
+  // Cm[j][i] = 2 thetabar_j conj(Q[i][j])  (column-major: Cm(j, i) at j + i n)
+  std::vector<cuDoubleComplex> Qh(size_t(n) * n), Ch(size_t(n) * n);
+  RCF_CUDA(ctx, cudaMemcpyAsync(Qh.data(), T, sizeof(cuDoubleComplex) * Qh.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  RCF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  if (hinfo != 0) return fail(ctx, RCF_ECUDA, "ZPOTRS failed (info %d)", hinfo);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const cuDoubleComplex q = Qh[size_t(j) * n + i];   // Q(i, j)
+      Ch[size_t(i) * n + j] = make_cuDoubleComplex(2.0 * thetabar[j] * q.x, -2.0 * thetabar[j] * q.y);
+    }
+  RCF_CUDA(ctx, cudaMemcpyAsync(Cm, Ch.data(), sizeof(cuDoubleComplex) * Ch.size(), cudaMemcpyHostToDevice, ctx->stream));
+  // Ybar = sum over column chunks of (H - theta M) X_chunk  Cm[chunk rows, :]
+  const int cb = std::min(n, 256);
+  double* Rx = nullptr;
+  RCF_TRY(workspace(ctx, WS_RR_T, sizeof(double) * 2 * size_t(N) * cb, reinterpret_cast<void**>(&Rx)));
+  double* sc = nullptr;
+  if (dV) {
+    RCF_TRY(workspace(ctx, WS_NORM, sizeof(double) * n, reinterpret_cast<void**>(&sc)));
+    RCF_CUDA(ctx, cudaMemcpyAsync(sc, thetabar, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+  for (int c0 = 0; c0 < n; c0 += cb) {
+    const int nc = std::min(cb, n - c0);
+    RCF_TRY(rcf_residual(ctx, op, X + 2 * int64_t(c0) * ldx, ldx, nc, theta + c0, Rx, N, nullptr));
+    RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, int(N), n, nc, &one,
+                              reinterpret_cast<const cuDoubleComplex*>(Rx), int(N), Cm + c0, n,
+                              c0 == 0 ? &zero : &one, reinterpret_cast<cuDoubleComplex*>(Ybar), int(ldb)));
+    if (dV) {
+      // direct term: sum_j thetabar_j x_j^H dH x_j, with W = X_chunk diag(thetabar) written
+      // over Rx (stream order puts it after the product that read Rx)
+      scale_cols_kernel<<<dim3(unsigned((N + 255) / 256), nc), 256, 0, ctx->stream>>>(
+          N, X + 2 * int64_t(c0) * ldx, ldx, sc + c0, Rx, N);
+      RCF_CHECK_LAUNCH(ctx);
+      RCF_TRY(rcf_grad_bilinear(ctx, op, Rx, N, X + 2 * int64_t(c0) * ldx, ldx, nc, 1.0, dV, dB, dh));
+    }
+  }
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return RCF_OK;
 }

@@ -23,7 +23,11 @@
 namespace rcf {
 namespace {
 
-constexpr long kWaitLimit = 1L << 24;   // try_wait polls before a wait is declared timed out
+// Pipeline waits give up after the context's limit of try_wait polls (rcf_set_wait_limit,
+// default 2^24).  The wait for a block's own copies in flight before it exits uses a separate,
+// fixed limit, so that a small pipeline limit never lets a block exit with a copy still
+// writing to its shared memory.
+constexpr long kDrainLimit = 1L << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -46,9 +50,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// bounded wait; false after kWaitLimit polls
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (long it = 0; it < kWaitLimit; ++it)
+// bounded wait; false after `limit` polls (at once for limit 0)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long limit) {
+  for (long it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -88,7 +92,7 @@ constexpr int tma_minb() {
 template <int P, int TX, int TY, int NST>
 __global__ void __launch_bounds__((((TX * TY) + 31) / 32 + 1) * 32, tma_minb<TX, TY>())
     step_kernel_tma(const StepArgs<float> a, const KTab<float, P> tab, const __grid_constant__ Maps maps,
-                    const int Gx, const int Gy, const int Gz, int* err) {
+                    const int Gx, const int Gy, const int Gz, int* err, const long wait_limit) {
   using V4 = R4<float>;
   using ST_ = Stage<P, TX, TY>;
   constexpr int NT = TX * TY;
@@ -126,7 +130,7 @@ __global__ void __launch_bounds__((((TX * TY) + 31) / 32 + 1) * 32, tma_minb<TX,
       bool ok = true;
       for (int z = 0; z < Gz && ok; ++z) {
         const int s = z % NST, k = z / NST;
-        if (k >= 1 && !mbar_wait(smem_u32(bars + NST + s), (k - 1) & 1)) {
+        if (k >= 1 && !mbar_wait(smem_u32(bars + NST + s), (k - 1) & 1, wait_limit)) {
           ok = false;
           break;
         }
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__((((TX * TY) + 31) / 32 + 1) * 32, tma_minb<TX,
         *abort_flag = 1;
         // let the copies already issued land before the block's shared memory goes away
         for (int z = (issued > NST ? issued - NST : 0); z < issued; ++z)
-          mbar_wait(smem_u32(bars + z % NST), (z / NST) & 1);
+          mbar_wait(smem_u32(bars + z % NST), (z / NST) & 1, kDrainLimit);
       }
     }
     return;
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__((((TX * TY) + 31) / 32 + 1) * 32, tma_minb<TX,
     for (int c = 0; c < P; ++c) {
       const int z = ez * P + c;
       const int s = z % NST;
-      if (!mbar_wait(smem_u32(bars + s), (z / NST) & 1) || *abort_flag) {
+      if (!mbar_wait(smem_u32(bars + s), (z / NST) & 1, wait_limit) || *abort_flag) {
         ok = false;
         break;
       }
@@ -368,7 +372,8 @@ int launch_tma_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArg
   if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   const int threads = ((TX * TY + 31) / 32 + 1) * 32;
   dim3 grid((m->G[0] / TX) * (m->G[1] / TY), a.nvec);
-  kern<<<grid, threads, smem, ctx->stream>>>(a, kt, maps, m->G[0], m->G[1], m->G[2], ctx->d_err);
+  kern<<<grid, threads, smem, ctx->stream>>>(a, kt, maps, m->G[0], m->G[1], m->G[2], ctx->d_err,
+                                             long(ctx->wait_limit));
   RCF_CHECK_LAUNCH(ctx);
   *used = true;
   return RCF_OK;

@@ -32,7 +32,8 @@ EXPORTS = [
     "rcf_grad_bilinear", "rcf_adjoint_filter", "rcf_cheb_step", "rcf_launch_count",
     "rcf_apply_noalloc", "rcf_set_step_kernel", "rcf_residual_df", "rcf_cholqr2",
     "rcf_rayleigh_ritz_orth", "rcf_filter_host", "rcf_set_rr_arith",
-    "rcf_bfp_stream_bytes", "rcf_bfp_encode", "rcf_bfp_decode",
+    "rcf_bfp_stream_bytes", "rcf_bfp_encode", "rcf_bfp_decode", "rcf_ritz_cotangent",
+    "rcf_set_wait_limit",
 ]
 
 _lib = None
@@ -91,6 +92,8 @@ def lib() -> ctypes.CDLL:
         "rcf_bfp_stream_bytes": (i64, [i64, i32]),
         "rcf_bfp_encode": (i32, [vp, vp, i64, i32, vp]),
         "rcf_bfp_decode": (i32, [vp, vp, i64, i32, vp]),
+        "rcf_set_wait_limit": (i32, [vp, i64]),
+        "rcf_ritz_cotangent": (i32, [vp, vp, vp, i64, vp, i64, i32, vp, vp, vp, i64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -368,6 +371,24 @@ def rcf_grad_bilinear(ctx, op, W, U, weight: float, dV, dB, dh=None):
                                         _np_ptr(dh) if dh is not None else None))
 
 
+def rcf_ritz_cotangent(ctx, op, Y, X, theta, thetabar, Ybar, dV=None, dB=None, dh=None):
+    """Ybar <- dL/dY of L = sum_j thetabar_j theta_j(Y) for the Rayleigh-Ritz pairs (theta, X = Y Q)
+    of Y; dV, dB (device) and dh (host) += the direct derivative sum_j thetabar_j x_j^H dH x_j."""
+    import torch
+    py, ldy = _dev(Y, torch.complex128, "Y")
+    px, ldx = _dev(X, torch.complex128, "X")
+    pb, ldb = _dev(Ybar, torch.complex128, "Ybar")
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    tb = np.ascontiguousarray(thetabar, dtype=np.float64)
+    n = Y.shape[0]
+    if X.shape[0] != n or Ybar.shape[0] != n or th.size != n or tb.size != n:
+        raise ValueError("Y, X, Ybar, theta and thetabar must have the same number of vectors")
+    _check(ctx, lib().rcf_ritz_cotangent(ctx, op, py, ldy, px, ldx, n, _np_ptr(th), _np_ptr(tb), pb, ldb,
+                                         ctypes.c_void_p(dV.data_ptr()) if dV is not None else None,
+                                         ctypes.c_void_p(dB.data_ptr()) if dB is not None else None,
+                                         _np_ptr(dh) if dh is not None else None))
+
+
 def rcf_adjoint_filter(ctx, op, X, ritz, degree: int, bounds, mode: int, prec: int, Ybar,
                        ckpt_every: int, dV, dB, dh=None):
     import torch
@@ -402,6 +423,10 @@ def rcf_launch_count(ctx) -> int:
 def rcf_set_rr_arith(ctx, kind: int) -> None:
     """Gram / projection GEMMs of this context: RCF_RR_FP64 (cuBLAS, default) or RCF_RR_DF."""
     _check(ctx, lib().rcf_set_rr_arith(ctx, int(kind)))
+
+
+def rcf_set_wait_limit(ctx, polls: int) -> None:
+    _check(ctx, lib().rcf_set_wait_limit(ctx, int(polls)))
 
 
 def rcf_set_step_kernel(ctx, kind: int) -> None:

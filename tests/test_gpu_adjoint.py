@@ -122,3 +122,35 @@ def test_adjoint_workload_finite_differences():
     err = np.linalg.norm(fd - an) / np.linalg.norm(fd)
     g.close()
     assert err < 1e-6, err
+
+
+def test_ritz_cotangent_matches_oracle(small):
+    """rcf_ritz_cotangent against the oracle's Ritz-value loss head: for L = sum of the lowest
+    nlow Ritz values of span(Y) (+ Re <G, Y>, added on the host since it is linear in Y), the
+    cotangent Ybar and the direct derivative sum_j x_j^H dH x_j in V, B and the couplings."""
+    import torch
+    from oracle import ritz_loss_head
+    from paper_2605_30128_gb300 import rchfsi as R
+    H = small.H
+    nv, nlow = 6, 4
+    Y = workloads.complex_normal(43, (H.N, nv))
+    G = np.zeros_like(Y)
+    _, oYbar, (gV, gB, gh) = ritz_loss_head(H, Y, G, nlow)
+    oV = H.node_to_quadrature(gV)
+    oB = np.stack([H.node_to_quadrature(gB[d]) for d in range(3)])
+    Yd = to_dev(Y)
+    Xr = torch.empty_like(Yd)
+    theta = R.rcf_rayleigh_ritz(small.g.ctx, small.g.op, Yd.clone(), Xr)
+    tb = np.zeros(nv)
+    tb[:nlow] = 1.0
+    Ybar = torch.empty_like(Yd)
+    dV = torch.zeros(small.V.shape, dtype=torch.float64, device="cuda")
+    dB = torch.zeros(small.B.shape, dtype=torch.float64, device="cuda")
+    dh = np.zeros((2, 2))
+    for _ in range(2):                       # the derivative parts accumulate; Ybar is overwritten
+        R.rcf_ritz_cotangent(small.g.ctx, small.g.op, Yd, Xr, theta, tb, Ybar, dV, dB, dh)
+    assert rel(to_host(Ybar), oYbar) < 1e-10
+    assert np.abs(to_host(Ybar) - oYbar).max() < 1e-10 * np.abs(oYbar).max()
+    assert rel(dV.cpu().numpy() / 2, oV) < 1e-10
+    assert rel(dB.cpu().numpy() / 2, oB) < 1e-10
+    assert rel(dh / 2, gh) < 1e-10

@@ -230,3 +230,28 @@ def test_invalid_arguments_are_rejected(cfg1):
     with pytest.raises(R.RcfError) as e:
         R.rcf_set_step_kernel(cfg1.g.ctx, 7)                                             # unknown kernel
     assert e.value.status == R.RCF_EINVAL
+
+
+def test_rchfsi_at_the_papers_degree_p7():
+    """p = 7 (the paper's production degree, Section IV-B): FP64 R-ChFSI and ChFSI to 1e-10 of
+    the oracle and the FP32 recurrence within its residual-proportional bound, on a 3 x 2 x 2
+    cell mesh (Gx = 21: one ragged FP32 tile) with two spin-orbit atoms."""
+    from paper_2605_30128_gb300 import rchfsi as R
+    pr = Pair((3, 2, 2), (6.0, 4.0, 4.0), 7, natoms=2, seed=31)
+    try:
+        H = pr.H
+        X, lam = rayleigh_ritz(H, workloads.complex_normal(50, (H.N, 6)))
+        lo, hi, *_ = lanczos_bounds(H, workloads.complex_normal(51, H.N), 10)
+        bounds = (float(lam.min()), float(lam.max()), hi)
+        q = 8
+        ref = rchfsi_filter(H, X, lam, *bounds, q)
+        assert rel(_gpu_filter(pr, X, lam, bounds, q, R.RCF_RCHFSI, R.RCF_FP64), ref) < 1e-10
+        refc = chfsi_filter(H, X, *bounds, q)
+        assert rel(_gpu_filter(pr, X, lam, bounds, q, R.RCF_CHFSI, R.RCF_FP64), refc) < 1e-10
+        # FP32 recurrence: error proportional to the residual of the start block
+        from oracle.filters import residual
+        rn = np.linalg.norm(residual(H, X, lam)) / np.linalg.norm(H.apply(X))
+        err = rel(_gpu_filter(pr, X, lam, bounds, q, R.RCF_RCHFSI, R.RCF_FP32), ref)
+        assert err < 1e-4 * max(rn, 1e-3), (err, rn)
+    finally:
+        pr.close()

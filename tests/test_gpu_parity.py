@@ -2,10 +2,12 @@
 
 Meshes span several stencil tiles with a ragged tail in x and y (FP32 tiles
 are 24-25 nodes wide and one element high, FP64 tiles about 8 x 8), single-cell
-directions, and degrees p = 1 .. 6.  Tolerances: FP64 products 1e-12 relative (rounding of ~30-term
-sums); FP64 filters 1e-10 relative Frobenius (the target for filtered
-blocks); FP32 products 2e-6 relative (float rounding of the same sums,
-about 30 eps_32 in the worst row).
+directions, and degrees p = 1 .. 8 (p = 7 is the paper's production degree).  Tolerances:
+FP64 products 1e-12 relative (rounding of ~30-term sums); FP64 filters 1e-10 relative
+Frobenius (the target for filtered blocks); FP32 products 2e-6 relative (float rounding of
+the same sums, about 30 eps_32 in the worst row) and, entry by entry, 64 eps_32 times the
+sum of the magnitudes of the entry's terms (|H| |X|): a bound on the rounding of sums of up
+to ~50 terms with FP32 coefficients, which a wrong term at a tile seam would exceed.
 """
 import numpy as np
 import pytest
@@ -26,6 +28,9 @@ MESHES = [
     ((5, 3, 2), (10.0, 6.0, 4.0), 6),    # p = 6, Gx = 30: ragged
     ((1, 2, 3), (2.0, 4.0, 6.0), 2),     # one cell along x: a node is its own periodic image
     ((9, 2, 1), (9.0, 2.0, 1.0), 1),     # p = 1
+    ((5, 3, 2), (10.0, 6.0, 4.0), 7),    # p = 7: Gx = 35 (FP32 tiles 28 x 7: a full and a ragged
+                                         # tile), Gy = 21; FP64 tiles 14 x 14
+    ((4, 2, 2), (8.0, 4.0, 4.0), 8),     # p = 8: Gx = 32 (FP32 tiles 24 x 8: ragged), Gy = 16
     # meshes that the FP32 tiles divide, run with the TMA step kernel selected: one tile
     # per plane (its strips wrap onto itself) and several tiles; p = 5 (25 x 5 tiles),
     # p = 4 (24 x 8) and p = 6 (24 x 6)
@@ -92,6 +97,16 @@ def test_apply_fp32(pair, form):
     R.rcf_apply(pair.g.ctx, pair.g.op, form, Xd, Yd, R.RCF_FP32)
     Y = to_host(Yd)
     assert rel(Y, ref) < 2e-6
+    # entry by entry against the magnitudes of the terms of each entry
+    A = np.abs(X32) / H.Mdiag[:, None] if form == 2 else np.abs(X32)
+    S = abs(H.Hloc) @ A
+    for pr in H.projectors:
+        S[pr["rows"]] += np.abs(pr["P"]) @ (np.abs(pr["Delta"]) @ (np.abs(pr["P"]).T @ A[pr["rows"]]))
+    if form == 1:
+        S = S / H.Mdiag[:, None]
+    eps32 = 2.0 ** -24
+    worst = np.max(np.abs(Y - ref) / (S + 1e-300))
+    assert worst < 64 * eps32, worst
 
 
 def test_apply_strided_leading_dimension(pair):
