@@ -192,15 +192,45 @@ int rcf_set_step_kernel(rcf_ctx* ctx, int kind);
  * test this path).  Returns RCF_EINVAL for a negative limit. */
 int rcf_set_wait_limit(rcf_ctx* ctx, int64_t polls);
 
-/* Arithmetic of the Gram matrix of Cholesky-QR and of the projected matrix
- * Y^H H Y of Rayleigh-Ritz (library-specific; the paper has no counterpart).
- * RCF_RR_FP64 (default): cuBLAS ZHERK / ZGEMM in FP64.  RCF_RR_DF: this
- * library's split-K GEMM in double-float arithmetic on the FP32 pipes (about
- * 2^-46 relative to the magnitudes of the terms), for GPUs whose FP64 rate is a
- * small fraction of their FP32 rate.  The triangular solves, the eigensolve
- * and the rotation stay FP64. */
-typedef enum { RCF_RR_FP64 = 0, RCF_RR_DF = 1 } rcf_rr_arith;
+/* Arithmetic of the tall products of Cholesky-QR and Rayleigh-Ritz: the Gram
+ * matrix Y^H M Y, the projected matrix Y^H (H Y), the triangular update
+ * Y L^{-H} and the rotation Y Q (library-specific; the paper has no
+ * counterpart, it uses FP64 Level-3 BLAS).
+ *   RCF_RR_FP64: cuBLAS ZHERK / ZGEMM / ZTRSM in FP64.
+ *   RCF_RR_DF: the Gram and projected matrices in double-float arithmetic on
+ *     the FP32 pipes (about 2^-46 relative to the magnitudes of the terms);
+ *     the triangular update and the rotation stay cuBLAS FP64.
+ *   RCF_RR_TC: all four on the bf16 tensor cores, FP64-accurate: every row of
+ *     the left and column of the right operand is scaled by a power of two
+ *     and split into 7 signed 8-bit digits (Ozaki-Ogita-Oishi-Rump error-free
+ *     splitting, 56 bits), the 28 digit products with s + t <= 8 are summed
+ *     exactly in FP32 over windows of 1024 terms and accumulated in 64-bit
+ *     fixed point; the triangular update applies L^{-H} (cuSOLVER TRTRI on the
+ *     n x n factor) as a rotation.  Error about 2^-55 of max|row| max|column|
+ *     per term, against 2^-53 |term| for FP64.
+ * The n x n factorisations (POTRF, TRTRI, HEEVD) are cuSOLVER FP64 in every
+ * mode.  Default RCF_RR_FP64. */
+typedef enum { RCF_RR_FP64 = 0, RCF_RR_DF = 1, RCF_RR_TC = 2 } rcf_rr_arith;
 int rcf_set_rr_arith(rcf_ctx* ctx, int kind);
+
+/* C (n x nz complex, column-major, ldc >= n) = Y^H diag(w) Z over nrows
+ * complex rows: Y (nrows x n) and Z (nrows x nz) c128 with leading dimensions
+ * ldy, ldz >= nrows (even), w device [nrows / 2] (the weight of both spinor
+ * rows of a node; NULL: 1; nrows even when given).  arith as rcf_rr_arith.
+ * Device buffers; C must not overlap Y or Z.  Asynchronous on the context's
+ * stream.  (The building block of the Gram and projected matrices, Algorithm 1
+ * RR step; the paper has no separate call.) */
+int rcf_inner(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Z, int64_t ldz, int nz,
+              int64_t nrows, const double* w, double* C, int64_t ldc, int arith);
+
+/* X (nrows x n complex, ldx) = Y Q for Y (nrows x n, ldy) and Q (n x n
+ * complex, column-major, ldq >= n), all device c128.  arith RCF_RR_FP64
+ * (cuBLAS ZGEMM; X must not overlap Y) or RCF_RR_TC (X may equal Y, with
+ * ldx == ldy: the rotation in place; n <= 4096).  Asynchronous on the
+ * context's stream.  (The subspace rotation of Algorithm 1 / Section
+ * III-C-4.) */
+int rcf_rotate(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Q, int64_t ldq,
+               int64_t nrows, double* X, int64_t ldx, int arith);
 
 /* ---- filter bounds (Section III-B-2; Lanczos as in Section III-C-1) --- */
 

@@ -133,7 +133,7 @@ int workspace(rcf_ctx* ctx, int slot, size_t bytes, void** out);
 enum WsSlot {
   WS_R64 = 0, WS_R32, WS_ZA, WS_ZB, WS_COEF, WS_NLC, WS_NLC2, WS_LANCZOS, WS_RR_W, WS_RR_S,
   WS_RR_T, WS_RR_INFO, WS_RR_WORK, WS_GRAD, WS_CKPT, WS_ADJ_A, WS_ADJ_B, WS_ADJ_C, WS_ADJ_U,
-  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HY0, WS_R16, WS_SCALE, WS_GEMM_PART, WS_COUNT
+  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HY0, WS_R16, WS_SCALE, WS_GEMM_PART, WS_TC_A, WS_TC_B, WS_TC_E, WS_TC_C, WS_TC_Q, WS_COUNT
 };
 
 // ---------------------------------------------------------------------------
@@ -187,6 +187,13 @@ int launch_residual_df(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t 
 // the tiles on or below the diagonal of a square C (Hermitian A^H A)  (gemm_df.cu)
 int launch_gemm_tn_df(rcf_ctx* ctx, const double* A, int64_t lda, const double* B, int64_t ldb,
                       const double* w, int64_t K, int m, int n, int lower, double* C, int64_t ldc);
+// FP64-accurate products on the bf16 tensor cores (gemm_tc.cu):
+// C (n x nz complex, ldc) = Y^H diag(w) Z over nrows complex rows (w[r / 2], null: 1;
+// lower: only C(i, j), i >= j, when Z == Y), and X (nrows x n) = Y Q (X may equal Y)
+int tc_gemm_tn(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* w, const double* Z, int64_t ldz,
+               int nz, int64_t nrows, double* C, int64_t ldc, int lower);
+int tc_rotate(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Q, int64_t ldq, int64_t nrows,
+              double* X, int64_t ldx);
 // hi[i], lo[i] = double-float split of x[i] (integer operations only)
 int launch_split_f64(rcf_ctx* ctx, int64_t n, const double* x, float* hi, float* lo);
 

@@ -11,6 +11,7 @@
 // library's kernels.
 #include <algorithm>
 #include <cmath>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -52,27 +53,92 @@ const char* cublas_name(cublasStatus_t s) {
       return fail((ctx), RCF_ECUDA, "cuSOLVER %s failed: status %d", #expr, int(_s));        \
   } while (0)
 
+// W[v][r] = w_I Y[v][r0 + r], I = (r0 + r) / 2 (w null: copy), for complex rows r < cr
+__global__ void weight_rows_kernel(const double* __restrict__ w, const double* __restrict__ Y, int64_t ldy,
+                                   int64_t r0, int64_t cr, double* __restrict__ W) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (r >= cr) return;
+  const double s = w ? w[(r0 + r) >> 1] : 1.0;
+  const double2 y = reinterpret_cast<const double2*>(Y + 2 * int64_t(v) * ldy)[r0 + r];
+  reinterpret_cast<double2*>(W + 2 * int64_t(v) * cr)[r] = make_double2(s * y.x, s * y.y);
+}
+
+// C (n x nz, ldc) = Y^H diag(w) Z in the given arithmetic; lower: Z == Y and only C(i, j),
+// i >= j, is needed (the Hermitian Gram matrix)
+int inner_product(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Z, int64_t ldz, int nz,
+                  int64_t nrows, const double* w, double* C, int64_t ldc, int arith, int lower) {
+  if (arith == RCF_RR_TC) return tc_gemm_tn(ctx, Y, ldy, n, w, Z, ldz, nz, nrows, C, ldc, lower);
+  if (arith == RCF_RR_DF) {
+    if (ldc != n) return fail(ctx, RCF_ENOTSUP, "double-float products need ldc == n");
+    return launch_gemm_tn_df(ctx, Y, ldy, Z, ldz, w, nrows, n, nz, lower && Z == Y && nz == n, C, ldc);
+  }
+  if (nrows > INT32_MAX || ldy > INT32_MAX || ldz > INT32_MAX || ldc > INT32_MAX)
+    return fail(ctx, RCF_ENOTSUP, "dimensions above 2^31 are not supported by the BLAS path");
+  int64_t cr = std::max<int64_t>(1024, (int64_t(1) << 26) / std::max(nz, 1));   // ~1 GiB chunks
+  cr = std::min<int64_t>(cr, nrows);
+  double* W = nullptr;
+  const bool herk = lower && Z == Y && nz == n && w != nullptr;
+  const int wc = herk ? n : nz;
+  RCF_TRY(workspace(ctx, WS_RR_W, sizeof(double) * 2 * size_t(cr) * wc, reinterpret_cast<void**>(&W)));
+  const double one = 1.0, zero = 0.0;
+  const cuDoubleComplex onec = make_cuDoubleComplex(1.0, 0.0), zeroc = make_cuDoubleComplex(0.0, 0.0);
+  auto* Cz = reinterpret_cast<cuDoubleComplex*>(C);
+  for (int64_t r0 = 0; r0 < nrows; r0 += cr) {
+    const int64_t c = std::min(cr, nrows - r0);
+    if (herk) {   // W = M^{1/2} Y, S = W^H W
+      sqrt_mass_rows_kernel<<<dim3(unsigned((c + 255) / 256), n), 256, 0, ctx->stream>>>(w, Y, ldy, r0, c, W);
+      RCF_CHECK_LAUNCH(ctx);
+      RCF_BLAS(ctx, cublasZherk(ctx->blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, n, int(c), &one,
+                                reinterpret_cast<const cuDoubleComplex*>(W), int(c), r0 == 0 ? &zero : &one, Cz,
+                                int(ldc)));
+    } else {
+      weight_rows_kernel<<<dim3(unsigned((c + 255) / 256), nz), 256, 0, ctx->stream>>>(w, Z, ldz, r0, c, W);
+      RCF_CHECK_LAUNCH(ctx);
+      RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_C, CUBLAS_OP_N, n, nz, int(c), &onec,
+                                reinterpret_cast<const cuDoubleComplex*>(Y + 2 * r0), int(ldy),
+                                reinterpret_cast<const cuDoubleComplex*>(W), int(c), r0 == 0 ? &zeroc : &onec, Cz,
+                                int(ldc)));
+    }
+  }
+  return RCF_OK;
+}
+
+// X = Y Q (n x n complex Q, ldq) in the given arithmetic; TC allows X == Y
+int rotate(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Q, int64_t ldq, int64_t nrows,
+           double* X, int64_t ldx, int arith) {
+  if (arith == RCF_RR_TC) return tc_rotate(ctx, Y, ldy, n, Q, ldq, nrows, X, ldx);
+  if (nrows > INT32_MAX || ldy > INT32_MAX || ldx > INT32_MAX)
+    return fail(ctx, RCF_ENOTSUP, "dimensions above 2^31 are not supported by the BLAS path");
+  const char* x0 = reinterpret_cast<const char*>(X);
+  const char* y0 = reinterpret_cast<const char*>(Y);
+  if (x0 < y0 + size_t(ldy) * n * 16 && y0 < x0 + size_t(ldx) * n * 16)
+    return fail(ctx, RCF_EINVAL, "the FP64 rotation cannot write over its input");
+  const cuDoubleComplex onec = make_cuDoubleComplex(1.0, 0.0), zeroc = make_cuDoubleComplex(0.0, 0.0);
+  RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, int(nrows), n, n, &onec,
+                            reinterpret_cast<const cuDoubleComplex*>(Y), int(ldy),
+                            reinterpret_cast<const cuDoubleComplex*>(Q), int(ldq), &zeroc,
+                            reinterpret_cast<cuDoubleComplex*>(X), int(ldx)));
+  return RCF_OK;
+}
+
+// U(i, j) = conj(Linv(j, i)) for i <= j, 0 below: U = L^{-H} from the lower factor Linv = L^{-1}
+__global__ void inverse_adjoint_kernel(const double* __restrict__ Li, int n, double* __restrict__ U) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n) return;
+  double2 v = make_double2(0.0, 0.0);
+  if (i <= j) {
+    const double2 l = reinterpret_cast<const double2*>(Li)[j + int64_t(i) * n];
+    v = make_double2(l.x, -l.y);
+  }
+  reinterpret_cast<double2*>(U)[i + int64_t(j) * n] = v;
+}
+
 // S = Y^H M Y  (lower triangle), S: n x n
 int gram(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int n, cuDoubleComplex* S) {
   const int64_t N = 2 * op->mesh->nnodes;
-  if (ctx->rr_arith == RCF_RR_DF)   // lower triangle of Y^H M Y in double-float arithmetic
-    return launch_gemm_tn_df(ctx, Y, ldy, Y, ldy, op->mesh->d_mass, N, n, n, 1,
-                             reinterpret_cast<double*>(S), n);
-  int64_t cr = std::max<int64_t>(1024, (int64_t(1) << 26) / std::max(n, 1));   // ~1 GiB chunks
-  cr = std::min<int64_t>(cr, N);
-  double* W = nullptr;
-  RCF_TRY(workspace(ctx, WS_RR_W, sizeof(double) * 2 * size_t(cr) * n, reinterpret_cast<void**>(&W)));
-  const double one = 1.0, zero = 0.0;
-  for (int64_t r0 = 0; r0 < N; r0 += cr) {
-    const int64_t c = std::min(cr, N - r0);
-    sqrt_mass_rows_kernel<<<dim3(unsigned((c + 255) / 256), n), 256, 0, ctx->stream>>>(
-        op->mesh->d_mass, Y, ldy, r0, c, W);
-    RCF_CHECK_LAUNCH(ctx);
-    RCF_BLAS(ctx, cublasZherk(ctx->blas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C, n, int(c), &one,
-                              reinterpret_cast<const cuDoubleComplex*>(W), int(c),
-                              r0 == 0 ? &zero : &one, S, n));
-  }
-  return RCF_OK;
+  return inner_product(ctx, Y, ldy, n, Y, ldy, n, N, op->mesh->d_mass, reinterpret_cast<double*>(S), n,
+                       ctx->rr_arith, 1);
 }
 
 // one Cholesky-QR pass; returns RCF_ENOTSPD (without touching Y) on breakdown unless shifted
@@ -111,6 +177,27 @@ int cholqr_pass(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int n, b
   for (int i = 0; i < n; ++i)
     if (!std::isfinite(diag[i].x) || !(diag[i].x > 0.0))
       return fail(ctx, RCF_ENOTSPD, "Cholesky-QR: Gram factor not finite and positive (column %d)", i + 1);
+  if (ctx->rr_arith == RCF_RR_TC) {
+    // Y <- Y L^{-H}: invert the n x n factor (TRTRI), apply its adjoint as a rotation in place
+    size_t dbytes = 0, hbytes = 0;
+    RCF_SOLVER(ctx, cusolverDnXtrtri_bufferSize(ctx->solver, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, n,
+                                                CUDA_C_64F, S, n, &dbytes, &hbytes));
+    void* dwork = nullptr;
+    RCF_TRY(workspace(ctx, WS_RR_WORK, std::max<size_t>(dbytes, 16), &dwork));
+    std::vector<unsigned char> hwork(std::max<size_t>(hbytes, 16));
+    RCF_SOLVER(ctx, cusolverDnXtrtri(ctx->solver, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, n, CUDA_C_64F, S,
+                                     n, dwork, dbytes, hwork.data(), hbytes, info));
+    double* U = nullptr;
+    RCF_TRY(workspace(ctx, WS_TC_Q, sizeof(cuDoubleComplex) * size_t(n) * n, reinterpret_cast<void**>(&U)));
+    inverse_adjoint_kernel<<<dim3(unsigned((n + 127) / 128), n), 128, 0, ctx->stream>>>(
+        reinterpret_cast<const double*>(S), n, U);
+    RCF_CHECK_LAUNCH(ctx);
+    RCF_TRY(tc_rotate(ctx, Y, ldy, n, U, n, N, Y, ldy));
+    RCF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // hwork is host memory of this frame
+    if (hinfo != 0) return fail(ctx, RCF_ENOTSPD, "Cholesky-QR: triangular factor singular (%d)", hinfo);
+    return RCF_OK;
+  }
   const cuDoubleComplex onec = make_cuDoubleComplex(1.0, 0.0);
   RCF_BLAS(ctx, cublasZtrsm(ctx->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_C,
                             CUBLAS_DIAG_NON_UNIT, int(N), n, &onec, S, n,
@@ -158,19 +245,11 @@ int rr_orth(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nv
   const int cb = std::min(nvec, 256);
   double* T = nullptr;
   RCF_TRY(workspace(ctx, WS_RR_T, sizeof(double) * 2 * size_t(N) * cb, reinterpret_cast<void**>(&T)));
-  const cuDoubleComplex onec = make_cuDoubleComplex(1.0, 0.0), zeroc = make_cuDoubleComplex(0.0, 0.0);
   for (int c0 = 0; c0 < nvec; c0 += cb) {
     const int nc = std::min(cb, nvec - c0);
     RCF_TRY(rcf_apply(ctx, op, RCF_FORM_H, Y + 2 * int64_t(c0) * ldy, ldy, nc, T, N, RCF_FP64));
-    if (ctx->rr_arith == RCF_RR_DF) {
-      RCF_TRY(launch_gemm_tn_df(ctx, Y, ldy, T, N, nullptr, N, nvec, nc, 0,
-                                reinterpret_cast<double*>(A + size_t(c0) * nvec), nvec));
-    } else {
-      RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_C, CUBLAS_OP_N, nvec, nc, int(N), &onec,
-                                reinterpret_cast<const cuDoubleComplex*>(Y), int(ldy),
-                                reinterpret_cast<const cuDoubleComplex*>(T), int(N), &zeroc,
-                                A + size_t(c0) * nvec, nvec));
-    }
+    RCF_TRY(inner_product(ctx, Y, ldy, nvec, T, N, nc, N, nullptr, reinterpret_cast<double*>(A + size_t(c0) * nvec),
+                          nvec, ctx->rr_arith, 0));
   }
   double* w = nullptr;
   int* info = nullptr;
@@ -183,9 +262,8 @@ int rr_orth(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nv
   RCF_TRY(workspace(ctx, WS_RR_WORK, sizeof(cuDoubleComplex) * size_t(std::max(lwork, 1)), reinterpret_cast<void**>(&work)));
   RCF_SOLVER(ctx, cusolverDnZheevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nvec, A,
                                    nvec, w, work, lwork, info));
-  RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, int(N), nvec, nvec, &onec,
-                            reinterpret_cast<const cuDoubleComplex*>(Y), int(ldy), A, nvec, &zeroc,
-                            reinterpret_cast<cuDoubleComplex*>(X_out), int(ldx)));
+  RCF_TRY(rotate(ctx, Y, ldy, nvec, reinterpret_cast<const double*>(A), nvec, N, X_out, ldx,
+                 ctx->rr_arith == RCF_RR_TC ? RCF_RR_TC : RCF_RR_FP64));
   int hinfo = 0;
   RCF_CUDA(ctx, cudaMemcpyAsync(ritz_out, w, sizeof(double) * nvec, cudaMemcpyDeviceToHost, ctx->stream));
   RCF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -240,17 +318,6 @@ extern "C" int rcf_rayleigh_ritz(rcf_ctx* ctx, const rcf_op* op, double* Y, int6
 namespace rcf {
 namespace {
 
-// W[v][r] = M_I Y[v][r0 + r], I = (r0 + r) / 2, for complex rows r < cr
-__global__ void mass_rows_kernel(const double* __restrict__ mass, const double* __restrict__ Y,
-                                 int64_t ldy, int64_t r0, int64_t cr, double* __restrict__ W) {
-  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int v = blockIdx.y;
-  if (r >= cr) return;
-  const double s = mass[(r0 + r) >> 1];
-  const double2 y = reinterpret_cast<const double2*>(Y + 2 * int64_t(v) * ldy)[r0 + r];
-  reinterpret_cast<double2*>(W + 2 * int64_t(v) * cr)[r] = make_double2(s * y.x, s * y.y);
-}
-
 // y[v][r] = s[v] x[v][r] (complex rows r < rows)
 __global__ void scale_cols_kernel(int64_t rows, const double* __restrict__ x, int64_t ldx,
                                   const double* __restrict__ s, double* __restrict__ y, int64_t ldy) {
@@ -259,28 +326,6 @@ __global__ void scale_cols_kernel(int64_t rows, const double* __restrict__ x, in
   if (r >= rows) return;
   const double2 a = reinterpret_cast<const double2*>(x + 2 * int64_t(v) * ldx)[r];
   reinterpret_cast<double2*>(y + 2 * int64_t(v) * ldy)[r] = make_double2(s[v] * a.x, s[v] * a.y);
-}
-
-// C (m x n) = A^H M B over all rows (A, B c128 column blocks), FP64 ZGEMM over row chunks
-int gemm_tn_mass(rcf_ctx* ctx, const rcf_op* op, const double* A, int64_t lda, int m, const double* B,
-                 int64_t ldb, int n, cuDoubleComplex* C) {
-  const int64_t N = 2 * op->mesh->nnodes;
-  int64_t cr = std::max<int64_t>(1024, (int64_t(1) << 26) / std::max(n, 1));
-  cr = std::min<int64_t>(cr, N);
-  double* W = nullptr;
-  RCF_TRY(workspace(ctx, WS_RR_W, sizeof(double) * 2 * size_t(cr) * n, reinterpret_cast<void**>(&W)));
-  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
-  for (int64_t r0 = 0; r0 < N; r0 += cr) {
-    const int64_t c = std::min(cr, N - r0);
-    mass_rows_kernel<<<dim3(unsigned((c + 255) / 256), n), 256, 0, ctx->stream>>>(
-        op->mesh->d_mass, B, ldb, r0, c, W);            // W = M B on rows r0 .. r0 + c
-    RCF_CHECK_LAUNCH(ctx);
-    RCF_BLAS(ctx, cublasZgemm(ctx->blas, CUBLAS_OP_C, CUBLAS_OP_N, m, n, int(c), &one,
-                              reinterpret_cast<const cuDoubleComplex*>(A + 2 * r0), int(lda),
-                              reinterpret_cast<const cuDoubleComplex*>(W), int(c),
-                              r0 == 0 ? &zero : &one, C, m));
-  }
-  return RCF_OK;
 }
 
 }  // namespace
@@ -309,8 +354,10 @@ extern "C" int rcf_ritz_cotangent(rcf_ctx* ctx, const rcf_op* op, const double* 
   RCF_TRY(workspace(ctx, WS_RR_S, sizeof(cuDoubleComplex) * 3 * size_t(n) * n, reinterpret_cast<void**>(&S)));
   T = S + size_t(n) * n;
   Cm = T + size_t(n) * n;
-  RCF_TRY(gemm_tn_mass(ctx, op, Y, ldy, n, Y, ldy, n, S));
-  RCF_TRY(gemm_tn_mass(ctx, op, Y, ldy, n, X, ldx, n, T));
+  RCF_TRY(inner_product(ctx, Y, ldy, n, Y, ldy, n, N, op->mesh->d_mass, reinterpret_cast<double*>(S), n,
+                        ctx->rr_arith, 0));
+  RCF_TRY(inner_product(ctx, Y, ldy, n, X, ldx, n, N, op->mesh->d_mass, reinterpret_cast<double*>(T), n,
+                        ctx->rr_arith, 0));
   int* info = nullptr;
   RCF_TRY(workspace(ctx, WS_RR_INFO, sizeof(int) * 4, reinterpret_cast<void**>(&info)));
   int lwork = 0;
@@ -362,4 +409,41 @@ extern "C" int rcf_ritz_cotangent(rcf_ctx* ctx, const rcf_op* op, const double* 
   }
   RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return RCF_OK;
+}
+
+extern "C" int rcf_inner(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Z, int64_t ldz, int nz,
+                         int64_t nrows, const double* w, double* C, int64_t ldc, int arith) {
+  if (!ctx) return RCF_EINVAL;
+  if (!Y || !Z || !C) return fail(ctx, RCF_EINVAL, "NULL argument");
+  if (n <= 0 || nz <= 0 || nrows <= 0) return fail(ctx, RCF_EINVAL, "sizes must be >= 1");
+  if (ldy < nrows || ldz < nrows || (ldy & 1) || (ldz & 1) || ldc < n)
+    return fail(ctx, RCF_EINVAL, "bad leading dimension");
+  if (w && (nrows & 1)) return fail(ctx, RCF_EINVAL, "a node weight needs an even number of rows");
+  if (arith != RCF_RR_FP64 && arith != RCF_RR_DF && arith != RCF_RR_TC)
+    return fail(ctx, RCF_EINVAL, "unknown arithmetic %d", arith);
+  if (((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(Z) | reinterpret_cast<uintptr_t>(C)) & 15) != 0)
+    return fail(ctx, RCF_EINVAL, "buffers must be 16-byte aligned");
+  const char* c0 = reinterpret_cast<const char*>(C);
+  const size_t cb = size_t(ldc) * nz * 16;
+  for (auto [p, ld, m] : {std::tuple<const double*, int64_t, int>{Y, ldy, n}, {Z, ldz, nz}}) {
+    const char* p0 = reinterpret_cast<const char*>(p);
+    if (c0 < p0 + size_t(ld) * m * 16 && p0 < c0 + cb) return fail(ctx, RCF_EINVAL, "C overlaps an input");
+  }
+  return inner_product(ctx, Y, ldy, n, Z, ldz, nz, nrows, w, C, ldc, arith, 0);
+}
+
+extern "C" int rcf_rotate(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Q, int64_t ldq,
+                          int64_t nrows, double* X, int64_t ldx, int arith) {
+  if (!ctx) return RCF_EINVAL;
+  if (!Y || !Q || !X) return fail(ctx, RCF_EINVAL, "NULL argument");
+  if (n <= 0 || nrows <= 0) return fail(ctx, RCF_EINVAL, "sizes must be >= 1");
+  if (ldy < nrows || ldx < nrows || (ldy & 1) || (ldx & 1) || ldq < n)
+    return fail(ctx, RCF_EINVAL, "bad leading dimension");
+  if (arith != RCF_RR_FP64 && arith != RCF_RR_TC) return fail(ctx, RCF_EINVAL, "unknown arithmetic %d", arith);
+  if (((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(Q) | reinterpret_cast<uintptr_t>(X)) & 15) != 0)
+    return fail(ctx, RCF_EINVAL, "buffers must be 16-byte aligned");
+  const char* q0 = reinterpret_cast<const char*>(Q);
+  const char* x0 = reinterpret_cast<const char*>(X);
+  if (q0 < x0 + size_t(ldx) * n * 16 && x0 < q0 + size_t(ldq) * n * 16) return fail(ctx, RCF_EINVAL, "X overlaps Q");
+  return rotate(ctx, Y, ldy, n, Q, ldq, nrows, X, ldx, arith);
 }

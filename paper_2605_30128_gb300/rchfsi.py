@@ -21,7 +21,7 @@ RCF_FP64, RCF_FP32, RCF_FP32_DF, RCF_FP16, RCF_BF16 = 0, 1, 2, 3, 4
 RCF_CHFSI, RCF_RCHFSI = 0, 1
 RCF_FORM_H, RCF_FORM_DINV_H, RCF_FORM_H_DINV = 0, 1, 2
 RCF_STEP_CPASYNC, RCF_STEP_TMA = 0, 1
-RCF_RR_FP64, RCF_RR_DF = 0, 1
+RCF_RR_FP64, RCF_RR_DF, RCF_RR_TC = 0, 1, 2
 
 EXPORTS = [
     "rcf_create", "rcf_destroy", "rcf_status_string", "rcf_last_error", "rcf_sync",
@@ -33,7 +33,7 @@ EXPORTS = [
     "rcf_apply_noalloc", "rcf_set_step_kernel", "rcf_residual_df", "rcf_cholqr2",
     "rcf_rayleigh_ritz_orth", "rcf_filter_host", "rcf_set_rr_arith",
     "rcf_bfp_stream_bytes", "rcf_bfp_encode", "rcf_bfp_decode", "rcf_ritz_cotangent",
-    "rcf_set_wait_limit",
+    "rcf_set_wait_limit", "rcf_inner", "rcf_rotate",
 ]
 
 _lib = None
@@ -93,6 +93,8 @@ def lib() -> ctypes.CDLL:
         "rcf_bfp_encode": (i32, [vp, vp, i64, i32, vp]),
         "rcf_bfp_decode": (i32, [vp, vp, i64, i32, vp]),
         "rcf_set_wait_limit": (i32, [vp, i64]),
+        "rcf_inner": (i32, [vp, vp, i64, i32, vp, i64, i32, i64, vp, vp, i64, i32]),
+        "rcf_rotate": (i32, [vp, vp, i64, i32, vp, i64, i64, vp, i64, i32]),
         "rcf_ritz_cotangent": (i32, [vp, vp, vp, i64, vp, i64, i32, vp, vp, vp, i64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -421,8 +423,37 @@ def rcf_launch_count(ctx) -> int:
 
 
 def rcf_set_rr_arith(ctx, kind: int) -> None:
-    """Gram / projection GEMMs of this context: RCF_RR_FP64 (cuBLAS, default) or RCF_RR_DF."""
+    """Tall products of Cholesky-QR and Rayleigh-Ritz: RCF_RR_FP64 (cuBLAS), RCF_RR_DF or RCF_RR_TC."""
     _check(ctx, lib().rcf_set_rr_arith(ctx, int(kind)))
+
+
+def rcf_inner(ctx, Y, Z, C, w=None, arith: int = 2, nrows=None):
+    """C (nz, n) complex128 tensor receives Y^H diag(w) Z (C[j, i] = C(i, j): rows of the tensors are
+    columns); Y (n, rows), Z (nz, rows) complex128; w a float64 CUDA tensor of rows / 2 node weights."""
+    import torch
+    py, ldy = _dev(Y, torch.complex128, "Y")
+    pz, ldz = _dev(Z, torch.complex128, "Z")
+    pc, ldc = _dev(C, torch.complex128, "C")
+    rows = Y.shape[1] if nrows is None else int(nrows)
+    if C.shape[0] < Z.shape[0] or C.shape[1] < Y.shape[0]:
+        raise ValueError("C must be (nz, >= n)")
+    pw = None
+    if w is not None:
+        if w.dtype != torch.float64 or not w.is_cuda:
+            raise TypeError("w must be a float64 CUDA tensor")
+        pw = ctypes.c_void_p(w.data_ptr())
+    _check(ctx, lib().rcf_inner(ctx, py, ldy, Y.shape[0], pz, ldz, Z.shape[0], rows, pw, pc, ldc, int(arith)))
+
+
+def rcf_rotate(ctx, Y, Q, X, arith: int = 2, nrows=None):
+    """X (n, rows) complex128 receives Y Q for Y (n, rows) and Q (n, n) complex128 (Q[j, i] = Q(i, j));
+    X may be Y for arith = RCF_RR_TC."""
+    import torch
+    py, ldy = _dev(Y, torch.complex128, "Y")
+    pq, ldq = _dev(Q, torch.complex128, "Q")
+    px, ldx = _dev(X, torch.complex128, "X")
+    rows = Y.shape[1] if nrows is None else int(nrows)
+    _check(ctx, lib().rcf_rotate(ctx, py, ldy, Y.shape[0], pq, ldq, rows, px, ldx, int(arith)))
 
 
 def rcf_set_wait_limit(ctx, polls: int) -> None:
