@@ -330,14 +330,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
           }
-          // exact integers |v| <= 2^24; shifted into the fixed-point sum (right shifts
-          // drop bits below 2^-FIX of the leading digit products)
+          // exact integers |v| <= 2^24; shifted into the fixed-point sum (right shifts round
+          // to nearest the bits below 2^-FIX of the leading digit products: flooring them
+          // would add a bias growing with the number of windows)
           if (sh >= 0) {
 #pragma unroll
             for (int c = 0; c < 32; ++c) F[32 * h + c] += (long long)__float2int_rn(v[c]) << sh;
           } else {
+            const int half_ulp = 1 << (-sh - 1);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) F[32 * h + c] += (long long)(__float2int_rn(v[c]) >> (-sh));
+            for (int c = 0; c < 32; ++c) F[32 * h + c] += (long long)((__float2int_rn(v[c]) + half_ulp) >> (-sh));
           }
         }
       }
