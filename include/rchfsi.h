@@ -209,7 +209,7 @@ int rcf_set_wait_limit(rcf_ctx* ctx, int64_t polls);
  *     n x n factor) as a rotation.  Error about 2^-55 of max|row| max|column|
  *     per term, against 2^-53 |term| for FP64.
  * The n x n factorisations (POTRF, TRTRI, HEEVD) are cuSOLVER FP64 in every
- * mode.  Default RCF_RR_FP64. */
+ * mode.  Default RCF_RR_TC. */
 typedef enum { RCF_RR_FP64 = 0, RCF_RR_DF = 1, RCF_RR_TC = 2 } rcf_rr_arith;
 int rcf_set_rr_arith(rcf_ctx* ctx, int kind);
 

@@ -20,7 +20,7 @@
 //
 // Kernel: one CTA per 128 x 128 output tile and K range, persistent over its
 // windows.  Warp 0 issues the TMA loads of the two operand tiles (128 rows x 64 k,
-// bf16, 128-byte swizzle) into a 4-stage shared-memory ring; warp 1 (one thread)
+// bf16, 128-byte swizzle) into a 6-stage shared-memory ring; warp 1 (one thread)
 // issues tcgen05.mma (M = N = 128, K = 16, FP32 accumulate) into one of two
 // 128-column accumulators in tensor memory; warps 2..9 drain the other accumulator
 // (tcgen05.ld) into the fixed-point sums they hold in registers (each warp: 32
@@ -43,7 +43,7 @@ constexpr int NPROD = T * (T + 1) / 2;   // digit products with s + t <= T + 1
 constexpr int WIN = 1024;        // k per exact FP32 window
 constexpr int BK = 64;           // k per staged tile (128 bytes of bf16: one swizzle row)
 constexpr int TM = 128, TN = 128;
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 6;
 constexpr int FIX = 34;          // fixed-point position of the weight-2 digit products
 constexpr int LAUNCH_WINDOWS = 8;   // windows per CTA per launch (bounds |F| < 2^63)
 constexpr int NTHREADS = 320;
@@ -54,13 +54,15 @@ struct Prod {
   unsigned char s[NPROD], t[NPROD];
 };
 
+// products in slice-major order: the T + 1 - s products of left slice s follow one another,
+// so its window tiles are re-read from L2 rather than from HBM
 __host__ __device__ constexpr Prod make_products() {
   Prod p{};
   int n = 0;
-  for (int w = 2; w <= T + 1; ++w)
-    for (int s = 1; s < w; ++s) {
+  for (int s = 1; s <= T; ++s)
+    for (int t = 1; s + t <= T + 1; ++t) {
       p.s[n] = (unsigned char)(s - 1);
-      p.t[n] = (unsigned char)(w - s - 1);
+      p.t[n] = (unsigned char)(t - 1);
       ++n;
     }
   return p;
@@ -387,32 +389,53 @@ __device__ __forceinline__ int scale_exponent(double mx) {
   return x + 1;
 }
 
-// T balanced digits of x 2^-e (|x| <= 2^(e-1)): each step is exact in FP64
+// T balanced digits of x 2^-e (|x| <= 2^(e-1)) in integer arithmetic on the bits of x
+// (GB300 runs FP64 at a small fraction of its integer rate): X = round(x 2^(8T - e)) is a
+// 64-bit integer with |X| <= 2^(8T - 1) (error <= 2^(e - 8T - 1), the truncation bound of
+// T digits), written as X = sum_s d_s 2^(8 (T - 1 - s)) with the low digits in
+// [-128, 127] and the top one in [-128, 128].
 __device__ __forceinline__ void digits(double x, int e, float (&d)[T]) {
-  double r = ldexp(x, -e);
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int ex = int((b >> 52) & 0x7FF);
+  unsigned long long m = b & ((1ull << 52) - 1);
+  if (ex != 0) m |= 1ull << 52;                 // value = m 2^(max(ex, 1) - 1075)
+  const int sh = (ex != 0 ? ex : 1) - 1075 + BETA * T - e;
+  long long X;
+  if (sh >= 0)
+    X = static_cast<long long>(m << sh);        // sh <= 3 when |x| <= 2^(e-1)
+  else if (sh < -62)
+    X = 0;
+  else
+    X = static_cast<long long>((m + (1ull << (-sh - 1))) >> (-sh));
+  if (b >> 63) X = -X;
 #pragma unroll
-  for (int s = 0; s < T; ++s) {
-    const double y = r * double(1 << BETA);
-    const double q = rint(y);
-    d[s] = float(q);
-    r = y - q;
+  for (int s = T - 1; s > 0; --s) {
+    const long long q = ((X + 128) & 255) - 128;
+    d[s] = float(int(q));
+    X = (X - q) >> BETA;
   }
+  d[0] = float(int(X));
 }
 
-__device__ __forceinline__ double block_max(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+// |x| as ordered integer bits (non-negative doubles compare like their bit patterns)
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+__device__ __forceinline__ double block_max(unsigned long long v, unsigned long long* red) {
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   if (l == 0) red[w] = v;
   __syncthreads();
   if (w == 0) {
-    v = l < int(blockDim.x >> 5) ? red[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    v = l < int(blockDim.x >> 5) ? red[l] : 0ull;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (l == 0) red[0] = v;
   }
   __syncthreads();
   v = red[0];
   __syncthreads();
-  return v;
+  return __longlong_as_double(static_cast<long long>(v));
 }
 
 // Column operand of a product over the complex rows r0 .. r0 + nr - 1 of X (column j:
@@ -424,10 +447,10 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 __global__ void slice_cols_kernel(const double* __restrict__ X, int64_t ldx, int ncol, int64_t r0, int64_t nr,
                                   const double* __restrict__ w, int pair_rows, int64_t ldk, int rows_total,
                                   __nv_bfloat16* __restrict__ D, int* __restrict__ e_out) {
-  __shared__ double red[32];
+  __shared__ unsigned long long red[32];
   const int j = blockIdx.x;
   const double2* x = reinterpret_cast<const double2*>(X + 2 * int64_t(j) * ldx) + r0;
-  double mx = 0.0;
+  unsigned long long mb = 0;
   for (int64_t r = threadIdx.x; r < nr; r += blockDim.x) {
     double2 v = x[r];
     if (w) {
@@ -435,9 +458,9 @@ __global__ void slice_cols_kernel(const double* __restrict__ X, int64_t ldx, int
       v.x *= m;
       v.y *= m;
     }
-    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    mb = max(mb, max(abs_bits(v.x), abs_bits(v.y)));
   }
-  mx = block_max(mx, red);
+  const double mx = block_max(mb, red);
   const int e = scale_exponent(mx);
   if (threadIdx.x == 0) {
     e_out[j] = e;
@@ -476,12 +499,12 @@ __global__ void row_exponent_kernel(const double* __restrict__ Y, int64_t ldy, i
                                     int* __restrict__ e_out) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= nr) return;
-  double mx = 0.0;
+  unsigned long long mb = 0;
   for (int i = 0; i < n; ++i) {
     const double2 v = reinterpret_cast<const double2*>(Y + 2 * int64_t(i) * ldy)[r0 + r];
-    mx = fmax(mx, fmax(fabs(v.x), fabs(v.y)));
+    mb = max(mb, max(abs_bits(v.x), abs_bits(v.y)));
   }
-  e_out[r] = scale_exponent(mx);
+  e_out[r] = scale_exponent(__longlong_as_double(static_cast<long long>(mb)));
 }
 
 // digits of a 32-row x 32-column tile of Y, transposed through shared memory so that
@@ -530,12 +553,12 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
 // [Re y, Im y] . col 2j = Re (y Q)_j and . col 2j + 1 = Im (y Q)_j.  One block per j.
 __global__ void slice_rotation_kernel(const double* __restrict__ Q, int64_t ldq, int n, int64_t ldk,
                                       __nv_bfloat16* __restrict__ D, int* __restrict__ e_out) {
-  __shared__ double red[32];
+  __shared__ unsigned long long red[32];
   const int j = blockIdx.x;
   const double2* q = reinterpret_cast<const double2*>(Q + 2 * int64_t(j) * ldq);
-  double mx = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, fmax(fabs(q[i].x), fabs(q[i].y)));
-  mx = block_max(mx, red);
+  unsigned long long mb = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mb = max(mb, max(abs_bits(q[i].x), abs_bits(q[i].y)));
+  const double mx = block_max(mb, red);
   const int e = scale_exponent(mx);
   if (threadIdx.x == 0) e_out[2 * j] = e_out[2 * j + 1] = e;
   const int64_t slice = int64_t(2 * n) * ldk;

@@ -39,7 +39,7 @@ struct rcf_ctx {
   int64_t launches = 0;     // kernels launched by this library on this context
   int* d_err = nullptr;     // device error word: set by a kernel whose bounded wait timed out
   int step_kernel = RCF_STEP_CPASYNC;   // FP32 step kernel (rcf_set_step_kernel)
-  int rr_arith = RCF_RR_FP64;           // Gram / projection GEMMs (rcf_set_rr_arith)
+  int rr_arith = RCF_RR_TC;             // tall products of Cholesky-QR and Rayleigh-Ritz (rcf_set_rr_arith)
   int64_t wait_limit = int64_t(1) << 24;   // polls of a bounded device-side wait (rcf_set_wait_limit)
   cudaStream_t copy_in = nullptr;       // host-to-device and device-to-host streams of
   cudaStream_t copy_out = nullptr;      // rcf_filter_host (created on first use)

@@ -98,13 +98,13 @@ def test_rchfsi_fp32_error_scales_with_residual(cfg1):
     assert errs_ch[1] > 1e2 * errs32[1]          # plain FP32 ChFSI keeps its eps_32 floor
 
 
-@pytest.fixture(params=[0, 1], ids=["rr-fp64", "rr-df"])
+@pytest.fixture(params=[0, 1, 2], ids=["rr-fp64", "rr-df", "rr-tc"])
 def rr_arith(request, cfg1):
-    """Run with the cuBLAS FP64 and the double-float Gram / projection GEMMs."""
+    """Run with the cuBLAS FP64, the double-float and the tensor-core tall products."""
     from paper_2605_30128_gb300 import rchfsi as R
     R.rcf_set_rr_arith(cfg1.g.ctx, request.param)
     yield request.param
-    R.rcf_set_rr_arith(cfg1.g.ctx, R.RCF_RR_FP64)
+    R.rcf_set_rr_arith(cfg1.g.ctx, R.RCF_RR_TC)
 
 
 def test_rayleigh_ritz_matches_oracle(cfg1, rr_arith):
@@ -189,7 +189,7 @@ def test_eigensolver_loop_reaches_oracle_eigenvalues(cfg1):
     try:
         lam, hist = _gpu_loop(cfg1, X0, 10, cfg1.hi, 1e-9, 150, R.RCF_RCHFSI, R.RCF_FP32_DF, nw)
     finally:
-        R.rcf_set_rr_arith(cfg1.g.ctx, R.RCF_RR_FP64)
+        R.rcf_set_rr_arith(cfg1.g.ctx, R.RCF_RR_TC)
     assert hist[-1] < 1e-9
     assert np.max(np.abs(lam[:nw] - ref[:nw])) < 1e-7
 

@@ -205,10 +205,11 @@ def test_fp64_chfsi_16cubed_p6_full_block_columns():
         g.close()
 
 
-@pytest.mark.parametrize("arith", [0, 1], ids=["rr-fp64", "rr-df"])
+@pytest.mark.parametrize("arith", [0, 1, 2], ids=["rr-fp64", "rr-df", "rr-tc"])
 def test_cholqr2_long_columns_orthonormal(full, arith):
     """Cholesky-QR2 of 64 columns of 2,000,000 rows (sums over 2M terms): the result is
-    M-orthonormal to 1e-12 with either Gram arithmetic, and its span is the input's."""
+    M-orthonormal to 1e-12 in every arithmetic of the tall products, and its span is the
+    input's."""
     import torch
     from paper_2605_30128_gb300 import rchfsi as R
     H, g, X = full["H"], full["g"], full["X"]
@@ -217,7 +218,7 @@ def test_cholqr2_long_columns_orthonormal(full, arith):
         Y = X[:64].clone()
         R.rcf_cholqr2(g.ctx, g.op, Y)
     finally:
-        R.rcf_set_rr_arith(g.ctx, R.RCF_RR_FP64)
+        R.rcf_set_rr_arith(g.ctx, R.RCF_RR_TC)
     m = torch.from_numpy(np.repeat(H.mass, 2)).cuda()
     G = (Y.conj() * m) @ Y.T
     assert (G - torch.eye(64, dtype=G.dtype, device="cuda")).abs().max().item() < 1e-12

@@ -148,7 +148,7 @@ def test_rayleigh_ritz_tc_matches_oracle_and_fp64(cfg1):
         Yd = to_dev(Y0)
         X = torch.empty_like(Yd)
         res[arith] = (R.rcf_rayleigh_ritz(cfg1.g.ctx, cfg1.g.op, Yd, X), to_host(X))
-    R.rcf_set_rr_arith(cfg1.g.ctx, R.RCF_RR_FP64)
+    R.rcf_set_rr_arith(cfg1.g.ctx, R.RCF_RR_TC)
     lt, Xt = res[R.RCF_RR_TC]
     np.testing.assert_allclose(lt, lo, atol=1e-10 * np.abs(lo).max())
     np.testing.assert_allclose(lt, res[R.RCF_RR_FP64][0], atol=1e-11 * np.abs(lo).max())
