@@ -208,9 +208,13 @@ int rcf_set_wait_limit(rcf_ctx* ctx, int64_t polls);
  *     fixed point; the triangular update applies L^{-H} (cuSOLVER TRTRI on the
  *     n x n factor) as a rotation.  Error about 2^-55 of max|row| max|column|
  *     per term, against 2^-53 |term| for FP64.
+ *   RCF_RR_MIXED: as RCF_RR_TC, except the Rayleigh-Ritz rotation X = Y Q,
+ *     split as in Section III-C-4: Y Q_offdiag (Q with its diagonal set to zero)
+ *     at FP32-level accuracy (3 digits of 8 bits, 6 digit products) plus
+ *     Y diag(Q) in FP64.
  * The n x n factorisations (POTRF, TRTRI, HEEVD) are cuSOLVER FP64 in every
  * mode.  Default RCF_RR_TC. */
-typedef enum { RCF_RR_FP64 = 0, RCF_RR_DF = 1, RCF_RR_TC = 2 } rcf_rr_arith;
+typedef enum { RCF_RR_FP64 = 0, RCF_RR_DF = 1, RCF_RR_TC = 2, RCF_RR_MIXED = 3 } rcf_rr_arith;
 int rcf_set_rr_arith(rcf_ctx* ctx, int kind);
 
 /* C (n x nz complex, column-major, ldc >= n) = Y^H diag(w) Z over nrows
@@ -225,9 +229,10 @@ int rcf_inner(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Z
 
 /* X (nrows x n complex, ldx) = Y Q for Y (nrows x n, ldy) and Q (n x n
  * complex, column-major, ldq >= n), all device c128.  arith RCF_RR_FP64
- * (cuBLAS ZGEMM; X must not overlap Y) or RCF_RR_TC (X may equal Y, with
- * ldx == ldy: the rotation in place; n <= 4096).  Asynchronous on the
- * context's stream.  (The subspace rotation of Algorithm 1 / Section
+ * (cuBLAS ZGEMM; X must not overlap Y), RCF_RR_TC (X may equal Y, with
+ * ldx == ldy: the rotation in place; n <= 4096) or RCF_RR_MIXED (the
+ * off-diagonal part at FP32-level accuracy plus the diagonal part in FP64;
+ * X must not overlap Y).  Asynchronous on the context's stream.  (The subspace rotation of Algorithm 1 / Section
  * III-C-4.) */
 int rcf_rotate(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Q, int64_t ldq,
                int64_t nrows, double* X, int64_t ldx, int arith);

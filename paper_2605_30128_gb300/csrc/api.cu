@@ -225,7 +225,7 @@ extern "C" int rcf_set_step_kernel(rcf_ctx* ctx, int kind) {
 
 extern "C" int rcf_set_rr_arith(rcf_ctx* ctx, int kind) {
   if (!ctx) return RCF_EINVAL;
-  if (kind != RCF_RR_FP64 && kind != RCF_RR_DF && kind != RCF_RR_TC)
+  if (kind != RCF_RR_FP64 && kind != RCF_RR_DF && kind != RCF_RR_TC && kind != RCF_RR_MIXED)
     return fail(ctx, RCF_EINVAL, "unknown Rayleigh-Ritz arithmetic %d", kind);
   ctx->rr_arith = kind;
   return RCF_OK;

@@ -38,8 +38,8 @@ namespace rcf {
 namespace tc {
 
 constexpr int BETA = 8;          // bits per digit
-constexpr int T = 7;             // digits per operand entry (56 bits)
-constexpr int NPROD = T * (T + 1) / 2;   // digit products with s + t <= T + 1
+constexpr int T = 7;             // digits per operand entry (56 bits): FP64-accurate products
+constexpr int T_LOW = 3;         // 24 bits: the FP32-accurate off-diagonal rotation of Section III-C-4
 constexpr int WIN = 1024;        // k per exact FP32 window
 constexpr int BK = 64;           // k per staged tile (128 bytes of bf16: one swizzle row)
 constexpr int TM = 128, TN = 128;
@@ -49,18 +49,22 @@ constexpr int LAUNCH_WINDOWS = 8;   // windows per CTA per launch (bounds |F| < 
 constexpr int NTHREADS = 320;
 constexpr int TILE_BYTES = TM * BK * 2;   // 16 KB per operand tile
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // every wait gives up after 2 s
+constexpr int E_NONFINITE = 1 << 14;   // exponent of a row or column holding an Inf or a NaN
 
+template <int TD>
 struct Prod {
-  unsigned char s[NPROD], t[NPROD];
+  static constexpr int N = TD * (TD + 1) / 2;   // digit products with s + t <= TD + 1
+  unsigned char s[N], t[N];
 };
 
 // products in slice-major order: the T + 1 - s products of left slice s follow one another,
 // so its window tiles are re-read from L2 rather than from HBM
-__host__ __device__ constexpr Prod make_products() {
-  Prod p{};
+template <int TD>
+__host__ __device__ constexpr Prod<TD> make_products() {
+  Prod<TD> p{};
   int n = 0;
-  for (int s = 1; s <= T; ++s)
-    for (int t = 1; s + t <= T + 1; ++t) {
+  for (int s = 1; s <= TD; ++s)
+    for (int t = 1; s + t <= TD + 1; ++t) {
       p.s[n] = (unsigned char)(s - 1);
       p.t[n] = (unsigned char)(t - 1);
       ++n;
@@ -68,7 +72,18 @@ __host__ __device__ constexpr Prod make_products() {
   return p;
 }
 
-__constant__ Prod kProd = make_products();
+__constant__ Prod<T> kProdFull = make_products<T>();
+__constant__ Prod<T_LOW> kProdLow = make_products<T_LOW>();
+template <int TD>
+__device__ __forceinline__ const Prod<TD>& products();
+template <>
+__device__ __forceinline__ const Prod<T>& products<T>() {
+  return kProdFull;
+}
+template <>
+__device__ __forceinline__ const Prod<T_LOW>& products<T_LOW>() {
+  return kProdLow;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -177,9 +192,12 @@ struct GemmArgs {
   int* err;
 };
 
+template <int TD>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                       const GemmArgs g) {
+  constexpr int NPROD = Prod<TD>::N;
+  const Prod<TD>& kProd = products<TD>();
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-aligned operand ring, then barriers
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -356,8 +374,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int c = 0; c < 64; c += 2) {
         const int col = col0 + 64 * half + c;
         if (col >= g.n) break;
-        const double v0 = ldexp(double(F[c]), e_r + g.eb[col] - FIX - 2 * BETA);
-        const double v1 = col + 1 < g.n ? ldexp(double(F[c + 1]), e_r + g.eb[col + 1] - FIX - 2 * BETA) : 0.0;
+        const int e0 = e_r + g.eb[col], e1 = col + 1 < g.n ? e_r + g.eb[col + 1] : 0;
+        const double v0 = e0 >= E_NONFINITE ? __longlong_as_double(0x7FF8000000000000ll)
+                                            : ldexp(double(F[c]), e0 - FIX - 2 * BETA);
+        const double v1 = e1 >= E_NONFINITE ? __longlong_as_double(0x7FF8000000000000ll)
+                                            : (col + 1 < g.n ? ldexp(double(F[c + 1]), e1 - FIX - 2 * BETA) : 0.0);
         double* dst = o + int64_t(col >> 1) * g.cs2;
         if (g.accumulate) {
           dst[0] += v0;
@@ -381,8 +402,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // operand digits
 // ---------------------------------------------------------------------------------------
 
-// e with max <= 2^(e - 1) (max = f 2^x, f in [1/2, 1): e = x + 1); 0 for max = 0
+// e with max <= 2^(e - 1) (max = f 2^x, f in [1/2, 1): e = x + 1); 0 for max = 0;
+// E_NONFINITE for an Inf or NaN maximum (its digits come out zero, its outputs NaN)
 __device__ __forceinline__ int scale_exponent(double mx) {
+  if (!(mx <= 1.7976931348623157e308)) return E_NONFINITE;
   if (!(mx > 0.0)) return 0;
   int x;
   frexp(mx, &x);
@@ -394,12 +417,13 @@ __device__ __forceinline__ int scale_exponent(double mx) {
 // 64-bit integer with |X| <= 2^(8T - 1) (error <= 2^(e - 8T - 1), the truncation bound of
 // T digits), written as X = sum_s d_s 2^(8 (T - 1 - s)) with the low digits in
 // [-128, 127] and the top one in [-128, 128].
-__device__ __forceinline__ void digits(double x, int e, float (&d)[T]) {
+template <int TD>
+__device__ __forceinline__ void digits(double x, int e, float (&d)[TD]) {
   const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
   const int ex = int((b >> 52) & 0x7FF);
   unsigned long long m = b & ((1ull << 52) - 1);
   if (ex != 0) m |= 1ull << 52;                 // value = m 2^(max(ex, 1) - 1075)
-  const int sh = (ex != 0 ? ex : 1) - 1075 + BETA * T - e;
+  const int sh = (ex != 0 ? ex : 1) - 1075 + BETA * TD - e;
   long long X;
   if (sh >= 0)
     X = static_cast<long long>(m << sh);        // sh <= 3 when |x| <= 2^(e-1)
@@ -409,7 +433,7 @@ __device__ __forceinline__ void digits(double x, int e, float (&d)[T]) {
     X = static_cast<long long>((m + (1ull << (-sh - 1))) >> (-sh));
   if (b >> 63) X = -X;
 #pragma unroll
-  for (int s = T - 1; s > 0; --s) {
+  for (int s = TD - 1; s > 0; --s) {
     const long long q = ((X + 128) & 255) - 128;
     d[s] = float(int(q));
     X = (X - q) >> BETA;
@@ -478,8 +502,8 @@ __global__ void slice_cols_kernel(const double* __restrict__ X, int64_t ldx, int
         v.x *= m;
         v.y *= m;
       }
-      digits(v.x, e, dr);
-      digits(v.y, e, di);
+      digits<T>(v.x, e, dr);
+      digits<T>(v.y, e, di);
     } else {
 #pragma unroll
       for (int s = 0; s < T; ++s) dr[s] = di[s] = 0.f;
@@ -509,27 +533,28 @@ __global__ void row_exponent_kernel(const double* __restrict__ Y, int64_t ldy, i
 
 // digits of a 32-row x 32-column tile of Y, transposed through shared memory so that
 // each row's digits are written contiguously along k.  Grid (row tiles, column tiles).
+template <int TD>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restrict__ Y, int64_t ldy, int n,
                                                          int64_t r0, int64_t nr, const int* __restrict__ e_row,
                                                          int64_t ldk, __nv_bfloat16* __restrict__ D) {
-  __shared__ __nv_bfloat16 sd[T][32][66];   // [s][row][k: 32 re then 32 im] (+2 padding)
+  __shared__ __nv_bfloat16 sd[TD][32][66];   // [s][row][k: 32 re then 32 im] (+2 padding)
   const int rt = blockIdx.x, it = blockIdx.y;
   const int lr = threadIdx.x & 31, ib = threadIdx.x >> 5;
   const int64_t r = int64_t(rt) * 32 + lr;
   const int e = r < nr ? e_row[r] : 0;
   for (int jj = 0; jj < 4; ++jj) {
     const int li = ib + 8 * jj, i = it * 32 + li;
-    float dr[T], di[T];
+    float dr[TD], di[TD];
     if (r < nr && i < n) {
       const double2 v = reinterpret_cast<const double2*>(Y + 2 * int64_t(i) * ldy)[r0 + r];
-      digits(v.x, e, dr);
-      digits(v.y, e, di);
+      digits<TD>(v.x, e, dr);
+      digits<TD>(v.y, e, di);
     } else {
 #pragma unroll
-      for (int s = 0; s < T; ++s) dr[s] = di[s] = 0.f;
+      for (int s = 0; s < TD; ++s) dr[s] = di[s] = 0.f;
     }
 #pragma unroll
-    for (int s = 0; s < T; ++s) {
+    for (int s = 0; s < TD; ++s) {
       sd[s][lr][li] = __float2bfloat16_rn(dr[s]);
       sd[s][lr][32 + li] = __float2bfloat16_rn(di[s]);
     }
@@ -537,7 +562,7 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
   __syncthreads();
   // write: per (s, row, part) 32 bf16, as 2-element pieces
   const int64_t slice = int64_t(nr) * ldk;
-  for (int t = threadIdx.x; t < T * 32 * 2 * 16; t += 256) {
+  for (int t = threadIdx.x; t < TD * 32 * 2 * 16; t += 256) {
     const int piece = t & 15, part = (t >> 4) & 1, lrow = (t >> 5) & 31, s = t >> 10;
     const int64_t rr = int64_t(rt) * 32 + lrow;
     const int i0 = it * 32 + piece * 2;
@@ -550,14 +575,17 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const double* __restric
 
 // Column operand of Y Q for a complex n x n matrix Q (column-major, Q(i, j) at i + j ldq):
 // output column 2j = (Re Q(:, j); -Im Q(:, j)), 2j + 1 = (Im Q(:, j); Re Q(:, j)), so that
-// [Re y, Im y] . col 2j = Re (y Q)_j and . col 2j + 1 = Im (y Q)_j.  One block per j.
-__global__ void slice_rotation_kernel(const double* __restrict__ Q, int64_t ldq, int n, int64_t ldk,
+// [Re y, Im y] . col 2j = Re (y Q)_j and . col 2j + 1 = Im (y Q)_j.  offdiag: Q(j, j) is
+// taken as zero (the off-diagonal part of Section III-C-4).  One block per j.
+template <int TD>
+__global__ void slice_rotation_kernel(const double* __restrict__ Q, int64_t ldq, int n, int64_t ldk, int offdiag,
                                       __nv_bfloat16* __restrict__ D, int* __restrict__ e_out) {
   __shared__ unsigned long long red[32];
   const int j = blockIdx.x;
   const double2* q = reinterpret_cast<const double2*>(Q + 2 * int64_t(j) * ldq);
   unsigned long long mb = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) mb = max(mb, max(abs_bits(q[i].x), abs_bits(q[i].y)));
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (!(offdiag && i == j)) mb = max(mb, max(abs_bits(q[i].x), abs_bits(q[i].y)));
   const double mx = block_max(mb, red);
   const int e = scale_exponent(mx);
   if (threadIdx.x == 0) e_out[2 * j] = e_out[2 * j + 1] = e;
@@ -565,17 +593,18 @@ __global__ void slice_rotation_kernel(const double* __restrict__ Q, int64_t ldq,
   __nv_bfloat16* c0 = D + int64_t(2 * j) * ldk;
   __nv_bfloat16* c1 = D + int64_t(2 * j + 1) * ldk;
   for (int k = threadIdx.x; k < ldk; k += blockDim.x) {
-    float a[T], b[T];
-    if (k < 2 * n) {
-      const double2 v = q[k < n ? k : k - n];
-      digits(k < n ? v.x : -v.y, e, a);   // column 2j
-      digits(k < n ? v.y : v.x, e, b);    // column 2j + 1
+    float a[TD], b[TD];
+    const int i = k < n ? k : k - n;
+    if (k < 2 * n && !(offdiag && i == j)) {
+      const double2 v = q[i];
+      digits<TD>(k < n ? v.x : -v.y, e, a);   // column 2j
+      digits<TD>(k < n ? v.y : v.x, e, b);    // column 2j + 1
     } else {
 #pragma unroll
-      for (int s = 0; s < T; ++s) a[s] = b[s] = 0.f;
+      for (int s = 0; s < TD; ++s) a[s] = b[s] = 0.f;
     }
 #pragma unroll
-    for (int s = 0; s < T; ++s) {
+    for (int s = 0; s < TD; ++s) {
       c0[s * slice + k] = __float2bfloat16_rn(a[s]);
       c1[s * slice + k] = __float2bfloat16_rn(b[s]);
     }
@@ -595,6 +624,19 @@ __global__ void gram_reduce_kernel(const double* __restrict__ C, int nslot, int 
     im += c[nz + j];
   }
   reinterpret_cast<double2*>(S)[i + int64_t(j) * lds] = make_double2(re, im);
+}
+
+// X(r, j) += Q(j, j) Y(r, j) in FP64 (the diagonal part of the rotation, Section III-C-4)
+__global__ void add_diag_kernel(const double* __restrict__ Y, int64_t ldy, const double* __restrict__ Q,
+                                int64_t ldq, int64_t nrows, double* __restrict__ X, int64_t ldx) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (r >= nrows) return;
+  const double2 q = reinterpret_cast<const double2*>(Q)[j + int64_t(j) * ldq];
+  const double2 y = reinterpret_cast<const double2*>(Y + 2 * int64_t(j) * ldy)[r];
+  double2* x = reinterpret_cast<double2*>(X + 2 * int64_t(j) * ldx) + r;
+  const double2 o = *x;
+  *x = make_double2(o.x + (q.x * y.x - q.y * y.y), o.y + (q.x * y.y + q.y * y.x));
 }
 
 }  // namespace tc
@@ -626,12 +668,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // digits [T][rows][ldk] bf16 viewed as (k < kdim, row, s) with (64, 128, 1) boxes and the
 // 128-byte swizzle; k >= kdim and rows beyond `rows` read as zero
 int encode_digits(rcf_ctx* ctx, CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t ldk,
-                  int64_t kdim) {
+                  int64_t kdim, int td = T) {
   auto fn = encode_fn();
   if (!fn) return fail(ctx, RCF_ECUDA, "cuTensorMapEncodeTiled is unavailable");
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || ldk % BK != 0)
     return fail(ctx, RCF_EINVAL, "digit buffer misaligned");
-  const cuuint64_t dims[3] = {cuuint64_t(kdim), cuuint64_t(rows), cuuint64_t(T)};
+  const cuuint64_t dims[3] = {cuuint64_t(kdim), cuuint64_t(rows), cuuint64_t(td)};
   const cuuint64_t strides[2] = {cuuint64_t(ldk) * 2, cuuint64_t(rows) * cuuint64_t(ldk) * 2};
   const cuuint32_t box[3] = {BK, TM, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
@@ -645,12 +687,14 @@ int encode_digits(rcf_ctx* ctx, CUtensorMap* map, const __nv_bfloat16* base, int
 constexpr size_t kSmem = 1024 + 2 * NSTAGE * TILE_BYTES + 256;
 
 // C (+)= A B^T over k in [k0, kend) for the digit maps; splits CTAs per tile along k
+template <int TD>
 int launch_gemm(rcf_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, int m, int n, int64_t k0,
                 int64_t kend, int splits, const int* ea, const int* eb, double* out, int64_t ss, int64_t rs,
                 int64_t cs2, int lower_n, bool overwrite) {
   static bool attr = false;
   if (!attr) {
-    RCF_CUDA(ctx, cudaFuncSetAttribute(ozaki_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmem)));
+    RCF_CUDA(ctx, cudaFuncSetAttribute(ozaki_gemm_kernel<TD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(kSmem)));
     attr = true;
   }
   const int tiles = ((m + TM - 1) / TM) * ((n + TN - 1) / TN);
@@ -673,7 +717,7 @@ int launch_gemm(rcf_ctx* ctx, const CUtensorMap& ma, const CUtensorMap& mb, int 
     g.accumulate = (overwrite && k == k0) ? 0 : 1;
     g.lower_n = lower_n;
     g.err = ctx->d_err;
-    ozaki_gemm_kernel<<<dim3(tiles, ny), NTHREADS, kSmem, ctx->stream>>>(ma, mb, g);
+    ozaki_gemm_kernel<TD><<<dim3(tiles, ny), NTHREADS, kSmem, ctx->stream>>>(ma, mb, g);
     RCF_CHECK_LAUNCH(ctx);
     k += int64_t(ny) * nwin * WIN;
   }
@@ -725,8 +769,8 @@ int tc_gemm_tn(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* 
     RCF_CHECK_LAUNCH(ctx);
     slice_cols_kernel<<<nz, 512, 0, ctx->stream>>>(Z, ldz, nz, r0, nr, w, 1, ldk, 2 * nz, DB, E + n);
     RCF_CHECK_LAUNCH(ctx);
-    RCF_TRY(launch_gemm(ctx, ma, mb, n, 2 * nz, 0, 2 * nr, splits, E, E + n, P, int64_t(slot), 2 * int64_t(nz), 2,
-                        lower ? n : 0, false));
+    RCF_TRY(launch_gemm<T>(ctx, ma, mb, n, 2 * nz, 0, 2 * nr, splits, E, E + n, P, int64_t(slot), 2 * int64_t(nz),
+                           2, lower ? n : 0, false));
   }
   gram_reduce_kernel<<<dim3((n + 127) / 128, nz), 128, 0, ctx->stream>>>(P, splits, n, nz, int64_t(slot), C, ldc,
                                                                         lower);
@@ -734,47 +778,68 @@ int tc_gemm_tn(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* 
   return RCF_OK;
 }
 
-// X (nrows x n complex, ldx) = Y Q for a device n x n complex Q (ldq); X may equal Y
-int tc_rotate(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Q, int64_t ldq, int64_t nrows,
-              double* X, int64_t ldx) {
-  using namespace tc;
-  if (!ctx->d_err) return fail(ctx, RCF_ENOTSUP, "tensor-core products need the device error word");
-  if (2 * n > LAUNCH_WINDOWS * WIN)
-    return fail(ctx, RCF_ENOTSUP, "tensor-core rotation supports up to %d vectors", LAUNCH_WINDOWS * WIN / 2);
-  if (X != Y) {
-    const char* x0 = reinterpret_cast<const char*>(X);
-    const char* y0 = reinterpret_cast<const char*>(Y);
-    if (x0 < y0 + size_t(ldy) * n * 16 && y0 < x0 + size_t(ldx) * n * 16)
-      return fail(ctx, RCF_EINVAL, "rotation output overlaps its input (only X == Y is allowed)");
-  } else if (ldx != ldy) {
-    return fail(ctx, RCF_EINVAL, "in-place rotation needs equal leading dimensions");
-  }
+namespace tc {
+namespace {
+
+// X = Y Q with TD digits per entry (offdiag: Q's diagonal taken as zero), row chunks of Y
+template <int TD>
+int rotate_chunks(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Q, int64_t ldq, int64_t nrows,
+                  double* X, int64_t ldx, int offdiag) {
   const int64_t ldk = (2 * int64_t(n) + BK - 1) / BK * BK;
-  int64_t rc = (int64_t(6) << 30) / (int64_t(T) * 2 * ldk);
+  int64_t rc = (int64_t(6) << 30) / (int64_t(TD) * 2 * ldk);
   rc = std::max<int64_t>(TM, rc / TM * TM);
   rc = std::min<int64_t>(rc, (nrows + TM - 1) / TM * TM);
   __nv_bfloat16 *DA = nullptr, *DB = nullptr;
   int* E = nullptr;
-  RCF_TRY(workspace(ctx, WS_TC_A, sizeof(__nv_bfloat16) * T * size_t(rc) * ldk, reinterpret_cast<void**>(&DA)));
-  RCF_TRY(workspace(ctx, WS_TC_B, sizeof(__nv_bfloat16) * T * size_t(2 * n) * ldk, reinterpret_cast<void**>(&DB)));
+  RCF_TRY(workspace(ctx, WS_TC_A, sizeof(__nv_bfloat16) * TD * size_t(rc) * ldk, reinterpret_cast<void**>(&DA)));
+  RCF_TRY(workspace(ctx, WS_TC_B, sizeof(__nv_bfloat16) * TD * size_t(2 * n) * ldk, reinterpret_cast<void**>(&DB)));
   RCF_TRY(workspace(ctx, WS_TC_E, sizeof(int) * size_t(rc + 2 * n), reinterpret_cast<void**>(&E)));
-  slice_rotation_kernel<<<n, 256, 0, ctx->stream>>>(Q, ldq, n, ldk, DB, E + rc);
+  slice_rotation_kernel<TD><<<n, 256, 0, ctx->stream>>>(Q, ldq, n, ldk, offdiag, DB, E + rc);
   RCF_CHECK_LAUNCH(ctx);
   CUtensorMap mb;
-  RCF_TRY(encode_digits(ctx, &mb, DB, 2 * n, ldk, 2 * int64_t(n)));
+  RCF_TRY(encode_digits(ctx, &mb, DB, 2 * n, ldk, 2 * int64_t(n), TD));
   for (int64_t r0 = 0; r0 < nrows; r0 += rc) {
     const int64_t nr = std::min(rc, nrows - r0);
     CUtensorMap ma;
-    RCF_TRY(encode_digits(ctx, &ma, DA, nr, ldk, 2 * int64_t(n)));
+    RCF_TRY(encode_digits(ctx, &ma, DA, nr, ldk, 2 * int64_t(n), TD));
     row_exponent_kernel<<<unsigned((nr + 255) / 256), 256, 0, ctx->stream>>>(Y, ldy, n, r0, nr, E);
     RCF_CHECK_LAUNCH(ctx);
-    slice_rows_kernel<<<dim3(unsigned((nr + 31) / 32), unsigned((n + 31) / 32)), 256, 0, ctx->stream>>>(
+    slice_rows_kernel<TD><<<dim3(unsigned((nr + 31) / 32), unsigned((n + 31) / 32)), 256, 0, ctx->stream>>>(
         Y, ldy, n, r0, nr, E, ldk, DA);
     RCF_CHECK_LAUNCH(ctx);
     // one launch covers K = 2n <= LAUNCH_WINDOWS windows: the output is written, not added to
-    RCF_TRY(launch_gemm(ctx, ma, mb, int(nr), 2 * n, 0, 2 * n, 1, E, E + rc, X + 2 * r0, 0, 2, 2 * ldx, 0, true));
+    RCF_TRY(launch_gemm<TD>(ctx, ma, mb, int(nr), 2 * n, 0, 2 * n, 1, E, E + rc, X + 2 * r0, 0, 2, 2 * ldx, 0,
+                            true));
   }
   return RCF_OK;
+}
+
+}  // namespace
+}  // namespace tc
+
+// X (nrows x n complex, ldx) = Y Q for a device n x n complex Q (ldq).  mixed = false:
+// FP64-accurate, X may equal Y (ldx == ldy).  mixed = true (Section III-C-4): Y Q_offdiag at
+// FP32-level accuracy (3 digits) plus Y diag(Q) in FP64; X must not overlap Y.
+int tc_rotate(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Q, int64_t ldq, int64_t nrows,
+              double* X, int64_t ldx, bool mixed) {
+  using namespace tc;
+  if (!ctx->d_err) return fail(ctx, RCF_ENOTSUP, "tensor-core products need the device error word");
+  if (2 * n > LAUNCH_WINDOWS * WIN)
+    return fail(ctx, RCF_ENOTSUP, "tensor-core rotation supports up to %d vectors", LAUNCH_WINDOWS * WIN / 2);
+  const char* x0 = reinterpret_cast<const char*>(X);
+  const char* y0 = reinterpret_cast<const char*>(Y);
+  const bool overlap = x0 < y0 + size_t(ldy) * n * 16 && y0 < x0 + size_t(ldx) * n * 16;
+  if (mixed) {
+    if (overlap) return fail(ctx, RCF_EINVAL, "the mixed-precision rotation cannot write over its input");
+    RCF_TRY(rotate_chunks<T_LOW>(ctx, Y, ldy, n, Q, ldq, nrows, X, ldx, 1));
+    add_diag_kernel<<<dim3(unsigned((nrows + 255) / 256), n), 256, 0, ctx->stream>>>(Y, ldy, Q, ldq, nrows, X, ldx);
+    RCF_CHECK_LAUNCH(ctx);
+    return RCF_OK;
+  }
+  if (X != Y && overlap)
+    return fail(ctx, RCF_EINVAL, "rotation output overlaps its input (only X == Y is allowed)");
+  if (X == Y && ldx != ldy) return fail(ctx, RCF_EINVAL, "in-place rotation needs equal leading dimensions");
+  return rotate_chunks<T>(ctx, Y, ldy, n, Q, ldq, nrows, X, ldx, 0);
 }
 
 }  // namespace rcf

@@ -189,11 +189,12 @@ int launch_gemm_tn_df(rcf_ctx* ctx, const double* A, int64_t lda, const double* 
                       const double* w, int64_t K, int m, int n, int lower, double* C, int64_t ldc);
 // FP64-accurate products on the bf16 tensor cores (gemm_tc.cu):
 // C (n x nz complex, ldc) = Y^H diag(w) Z over nrows complex rows (w[r / 2], null: 1;
-// lower: only C(i, j), i >= j, when Z == Y), and X (nrows x n) = Y Q (X may equal Y)
+// lower: only C(i, j), i >= j, when Z == Y), and X (nrows x n) = Y Q (X may equal Y; mixed:
+// the off-diagonal part of Q at FP32-level accuracy plus the diagonal part in FP64)
 int tc_gemm_tn(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* w, const double* Z, int64_t ldz,
                int nz, int64_t nrows, double* C, int64_t ldc, int lower);
 int tc_rotate(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Q, int64_t ldq, int64_t nrows,
-              double* X, int64_t ldx);
+              double* X, int64_t ldx, bool mixed = false);
 // hi[i], lo[i] = double-float split of x[i] (integer operations only)
 int launch_split_f64(rcf_ctx* ctx, int64_t n, const double* x, float* hi, float* lo);
 

@@ -68,7 +68,7 @@ __global__ void weight_rows_kernel(const double* __restrict__ w, const double* _
 // i >= j, is needed (the Hermitian Gram matrix)
 int inner_product(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Z, int64_t ldz, int nz,
                   int64_t nrows, const double* w, double* C, int64_t ldc, int arith, int lower) {
-  if (arith == RCF_RR_TC) return tc_gemm_tn(ctx, Y, ldy, n, w, Z, ldz, nz, nrows, C, ldc, lower);
+  if (arith == RCF_RR_TC || arith == RCF_RR_MIXED) return tc_gemm_tn(ctx, Y, ldy, n, w, Z, ldz, nz, nrows, C, ldc, lower);
   if (arith == RCF_RR_DF) {
     if (ldc != n) return fail(ctx, RCF_ENOTSUP, "double-float products need ldc == n");
     return launch_gemm_tn_df(ctx, Y, ldy, Z, ldz, w, nrows, n, nz, lower && Z == Y && nz == n, C, ldc);
@@ -108,6 +108,7 @@ int inner_product(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const doubl
 int rotate(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, const double* Q, int64_t ldq, int64_t nrows,
            double* X, int64_t ldx, int arith) {
   if (arith == RCF_RR_TC) return tc_rotate(ctx, Y, ldy, n, Q, ldq, nrows, X, ldx);
+  if (arith == RCF_RR_MIXED) return tc_rotate(ctx, Y, ldy, n, Q, ldq, nrows, X, ldx, true);
   if (nrows > INT32_MAX || ldy > INT32_MAX || ldx > INT32_MAX)
     return fail(ctx, RCF_ENOTSUP, "dimensions above 2^31 are not supported by the BLAS path");
   const char* x0 = reinterpret_cast<const char*>(X);
@@ -177,7 +178,7 @@ int cholqr_pass(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int n, b
   for (int i = 0; i < n; ++i)
     if (!std::isfinite(diag[i].x) || !(diag[i].x > 0.0))
       return fail(ctx, RCF_ENOTSPD, "Cholesky-QR: Gram factor not finite and positive (column %d)", i + 1);
-  if (ctx->rr_arith == RCF_RR_TC) {
+  if (ctx->rr_arith == RCF_RR_TC || ctx->rr_arith == RCF_RR_MIXED) {
     // Y <- Y L^{-H}: invert the n x n factor (TRTRI), apply its adjoint as a rotation in place
     size_t dbytes = 0, hbytes = 0;
     RCF_SOLVER(ctx, cusolverDnXtrtri_bufferSize(ctx->solver, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, n,
@@ -263,7 +264,7 @@ int rr_orth(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nv
   RCF_SOLVER(ctx, cusolverDnZheevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, nvec, A,
                                    nvec, w, work, lwork, info));
   RCF_TRY(rotate(ctx, Y, ldy, nvec, reinterpret_cast<const double*>(A), nvec, N, X_out, ldx,
-                 ctx->rr_arith == RCF_RR_TC ? RCF_RR_TC : RCF_RR_FP64));
+                 ctx->rr_arith == RCF_RR_DF ? RCF_RR_FP64 : ctx->rr_arith));
   int hinfo = 0;
   RCF_CUDA(ctx, cudaMemcpyAsync(ritz_out, w, sizeof(double) * nvec, cudaMemcpyDeviceToHost, ctx->stream));
   RCF_CUDA(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -419,7 +420,7 @@ extern "C" int rcf_inner(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, cons
   if (ldy < nrows || ldz < nrows || (ldy & 1) || (ldz & 1) || ldc < n)
     return fail(ctx, RCF_EINVAL, "bad leading dimension");
   if (w && (nrows & 1)) return fail(ctx, RCF_EINVAL, "a node weight needs an even number of rows");
-  if (arith != RCF_RR_FP64 && arith != RCF_RR_DF && arith != RCF_RR_TC)
+  if (arith != RCF_RR_FP64 && arith != RCF_RR_DF && arith != RCF_RR_TC && arith != RCF_RR_MIXED)
     return fail(ctx, RCF_EINVAL, "unknown arithmetic %d", arith);
   if (((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(Z) | reinterpret_cast<uintptr_t>(C)) & 15) != 0)
     return fail(ctx, RCF_EINVAL, "buffers must be 16-byte aligned");
@@ -439,7 +440,8 @@ extern "C" int rcf_rotate(rcf_ctx* ctx, const double* Y, int64_t ldy, int n, con
   if (n <= 0 || nrows <= 0) return fail(ctx, RCF_EINVAL, "sizes must be >= 1");
   if (ldy < nrows || ldx < nrows || (ldy & 1) || (ldx & 1) || ldq < n)
     return fail(ctx, RCF_EINVAL, "bad leading dimension");
-  if (arith != RCF_RR_FP64 && arith != RCF_RR_TC) return fail(ctx, RCF_EINVAL, "unknown arithmetic %d", arith);
+  if (arith != RCF_RR_FP64 && arith != RCF_RR_TC && arith != RCF_RR_MIXED)
+    return fail(ctx, RCF_EINVAL, "unknown arithmetic %d", arith);
   if (((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(Q) | reinterpret_cast<uintptr_t>(X)) & 15) != 0)
     return fail(ctx, RCF_EINVAL, "buffers must be 16-byte aligned");
   const char* q0 = reinterpret_cast<const char*>(Q);

@@ -141,8 +141,9 @@ def main(argv=None):
     ap.add_argument("--nwanted", type=int, default=None,
                     help="wanted vectors (default: all but a buffer of max(4, nvec/10))")
     ap.add_argument("--runs", default="rchfsi_fp32_df,rchfsi_fp32,chfsi_fp64")
-    ap.add_argument("--rr", default="fp64", choices=["fp64", "df", "tc"],
-                    help="tall products of Cholesky-QR2 and Rayleigh-Ritz: cuBLAS FP64, double-float, or tensor cores")
+    ap.add_argument("--rr", default="tc", choices=["fp64", "df", "tc", "mixed"],
+                    help="tall products of Cholesky-QR2 and Rayleigh-Ritz: cuBLAS FP64, double-float, tensor "
+                         "cores, or tensor cores with the mixed-precision rotation")
     a = ap.parse_args(argv)
     over = {k: v for k, v in (("nvec", a.nvec), ("block", a.block), ("degree", a.degree)) if v}
     w = workloads.workload(a.workload, **over)
@@ -155,7 +156,8 @@ def main(argv=None):
     runs.sort(key=lambda r: RUNS[r][1] != R.RCF_FP64)
     t0 = time.time()
     out = run(w, runs, a.cycles, a.tol, nw,
-              rr_arith={"fp64": R.RCF_RR_FP64, "df": R.RCF_RR_DF, "tc": R.RCF_RR_TC}[a.rr])
+              rr_arith={"fp64": R.RCF_RR_FP64, "df": R.RCF_RR_DF, "tc": R.RCF_RR_TC,
+                        "mixed": R.RCF_RR_MIXED}[a.rr])
     out["rr_arith"] = a.rr
     out["wall_s"] = time.time() - t0
     print(json.dumps(out), flush=True)

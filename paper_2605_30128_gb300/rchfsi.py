@@ -21,7 +21,7 @@ RCF_FP64, RCF_FP32, RCF_FP32_DF, RCF_FP16, RCF_BF16 = 0, 1, 2, 3, 4
 RCF_CHFSI, RCF_RCHFSI = 0, 1
 RCF_FORM_H, RCF_FORM_DINV_H, RCF_FORM_H_DINV = 0, 1, 2
 RCF_STEP_CPASYNC, RCF_STEP_TMA = 0, 1
-RCF_RR_FP64, RCF_RR_DF, RCF_RR_TC = 0, 1, 2
+RCF_RR_FP64, RCF_RR_DF, RCF_RR_TC, RCF_RR_MIXED = 0, 1, 2, 3
 
 EXPORTS = [
     "rcf_create", "rcf_destroy", "rcf_status_string", "rcf_last_error", "rcf_sync",
@@ -423,7 +423,8 @@ def rcf_launch_count(ctx) -> int:
 
 
 def rcf_set_rr_arith(ctx, kind: int) -> None:
-    """Tall products of Cholesky-QR and Rayleigh-Ritz: RCF_RR_FP64 (cuBLAS), RCF_RR_DF or RCF_RR_TC."""
+    """Tall products of Cholesky-QR and Rayleigh-Ritz: RCF_RR_FP64 (cuBLAS), RCF_RR_DF, RCF_RR_TC or
+    RCF_RR_MIXED."""
     _check(ctx, lib().rcf_set_rr_arith(ctx, int(kind)))
 
 

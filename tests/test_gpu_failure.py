@@ -85,7 +85,8 @@ def _gram_launches(g, fn):
 
 
 def test_cholqr_shifted_pass_engages_on_exact_breakdown(prob):
-    """Columns y1 = s e_r and y2 = s e_r + tau e_t with M_r s^2 = 1 and M_t tau^2 = 1e-18: the
+    """Run with the FP64 tall products, whose Gram matrix is one kernel plus cuBLAS per pass
+    (the launch count is the observable).  Columns y1 = s e_r and y2 = s e_r + tau e_t with M_r s^2 = 1 and M_t tau^2 = 1e-18: the
     Gram matrix is v^2 [[1, 1], [1, 1]] exactly in FP64 (v^2 + 1e-18 rounds to v^2), so the first
     Cholesky factorisation meets a zero pivot.  The shifted pass makes the block well
     conditioned, the two plain passes finish: 4 Gram launches instead of 2."""
@@ -102,8 +103,12 @@ def test_cholqr_shifted_pass_engages_on_exact_breakdown(prob):
     Yd = to_dev(Y)
     # a well-conditioned block of the same size: two Gram launches
     Yok = to_dev(workloads.complex_normal(7, (g.N, 2)))
-    assert _gram_launches(g, lambda: R.rcf_cholqr2(g.ctx, g.op, Yok)) == 2
-    assert _gram_launches(g, lambda: R.rcf_cholqr2(g.ctx, g.op, Yd)) == 4
+    R.rcf_set_rr_arith(g.ctx, R.RCF_RR_FP64)
+    try:
+        assert _gram_launches(g, lambda: R.rcf_cholqr2(g.ctx, g.op, Yok)) == 2
+        assert _gram_launches(g, lambda: R.rcf_cholqr2(g.ctx, g.op, Yd)) == 4
+    finally:
+        R.rcf_set_rr_arith(g.ctx, R.RCF_RR_TC)
     Q = to_host(Yd)
     Md = np.repeat(mass, 2)
     G = Q.conj().T @ (Md[:, None] * Q)
@@ -124,8 +129,12 @@ def test_cholqr_rank_deficient_block_fails_after_the_shifted_pass(prob):
     Y = np.zeros((g.N, 2), dtype=np.complex128)
     Y[2 * r, :] = _exact_entry(mass[r])[0]           # two identical columns: rank 1
     Yd = to_dev(Y)
-    with pytest.raises(R.RcfError) as ei:
-        R.rcf_cholqr2(g.ctx, g.op, Yd)
+    R.rcf_set_rr_arith(g.ctx, R.RCF_RR_FP64)
+    try:
+        with pytest.raises(R.RcfError) as ei:
+            R.rcf_cholqr2(g.ctx, g.op, Yd)
+    finally:
+        R.rcf_set_rr_arith(g.ctx, R.RCF_RR_TC)
     assert ei.value.status == R.RCF_ENOTSPD
     # the context stays usable
     Yok = to_dev(workloads.complex_normal(8, (g.N, 3)))
@@ -149,6 +158,25 @@ def test_nan_inputs_are_refused(prob):
     R.rcf_potential_set(g.ctx, g.op, g.V, g.B)        # the operator keeps working
     Y = workloads.complex_normal(9, (g.N, 3))
     Y[100, 1] = np.nan
-    with pytest.raises(R.RcfError) as ei:
-        R.rcf_cholqr2(g.ctx, g.op, to_dev(Y))
-    assert ei.value.status == R.RCF_ENOTSPD
+    for arith in (R.RCF_RR_TC, R.RCF_RR_FP64, R.RCF_RR_DF):
+        R.rcf_set_rr_arith(g.ctx, arith)
+        try:
+            with pytest.raises(R.RcfError) as ei:
+                R.rcf_cholqr2(g.ctx, g.op, to_dev(Y))
+        finally:
+            R.rcf_set_rr_arith(g.ctx, R.RCF_RR_TC)
+        assert ei.value.status == R.RCF_ENOTSPD, arith
+    # a NaN or an infinity in an operand of the tensor-core products gives NaN outputs
+    import torch
+    Yd = to_dev(Y)
+    C = torch.zeros((3, 3), dtype=torch.complex128, device="cuda")
+    R.rcf_inner(g.ctx, Yd, Yd, C, None, R.RCF_RR_TC)
+    Cn = C.cpu().numpy()
+    assert np.isnan(Cn[1, :]).all() and np.isnan(Cn[:, 1]).all() and np.isfinite(Cn[0, 0])
+    Yi = workloads.complex_normal(10, (g.N, 3))
+    Yi[7, 2] = np.inf
+    Q = to_dev(np.eye(3, dtype=np.complex128))
+    X = torch.zeros_like(Yd)
+    R.rcf_rotate(g.ctx, to_dev(Yi), Q, X, R.RCF_RR_TC)
+    Xn = X.cpu().numpy()
+    assert np.isnan(Xn[:, 7]).all() and np.isfinite(np.delete(Xn, 7, axis=1)).all()

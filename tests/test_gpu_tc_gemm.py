@@ -8,6 +8,8 @@
   bound: 7 digits of 8 bits after scaling each row / column by a power of two) of the exact
   product (Python fractions on small cases; numpy FP64 plus its own bound on larger ones).
 - Cholesky-QR2 and Rayleigh-Ritz with RCF_RR_TC against the oracle and against the FP64 mode.
+- The mixed-precision rotation (RCF_RR_MIXED, Section III-C-4): error bounded by the
+  off-diagonal part at FP32 level, and Algorithm 1 with it reaching the oracle's eigenvalues.
 """
 import math
 from fractions import Fraction
@@ -188,3 +190,74 @@ def test_cholqr2_tc_orthonormal_at_full_size():
         assert (torch.linalg.norm(Rec - Y0) / torch.linalg.norm(Y0)).item() < 1e-12
     finally:
         g.close()
+
+
+def test_mixed_rotation_error_is_fp32_level_in_the_offdiagonal_part(ctx):
+    """Section III-C-4: X = Y Q_diag (FP64) + Y Q_offdiag (FP32-level).  For Q near the identity
+    (a Rayleigh-Ritz rotation close to convergence) the error is bounded by the off-diagonal
+    part alone: |X - Y Q| <= K 2^-21 max|y_r| max|Q_offdiag(:, j)| per entry (3 digits of 8
+    bits), so the rotation's relative error falls with ||Q_offdiag||."""
+    import torch
+    from paper_2605_30128_gb300 import rchfsi as R
+    rows, n = 20000, 96
+    Y = workloads.complex_normal(41, (rows, n))
+    E = workloads.complex_normal(42, (n, n))
+    errs = []
+    for eps in (1e-2, 1e-5):
+        Q = np.diag(np.exp(1j * np.linspace(0, 3, n))) + eps * E
+        Qo = Q - np.diag(np.diag(Q))
+        X = torch.zeros((n, rows), dtype=torch.complex128, device="cuda")
+        R.rcf_rotate(ctx, _dev(Y), _dev(Q), X, R.RCF_RR_MIXED)
+        Xm = X.cpu().numpy().T
+        ref = Y @ Q
+        mxr = np.maximum(np.abs(Y.real), np.abs(Y.imag)).max(axis=1)
+        mxq = np.maximum(np.abs(Qo.real), np.abs(Qo.imag)).max(axis=0)
+        bound = 2 * n * 2.0 ** -21 * mxr[:, None] * mxq[None, :] + 4 * 2.0 ** -53 * np.abs(Y) * np.abs(np.diag(Q))
+        assert np.all(np.abs(Xm.real - ref.real) <= bound) and np.all(np.abs(Xm.imag - ref.imag) <= bound)
+        errs.append(np.linalg.norm(Xm - ref) / np.linalg.norm(ref))
+        # the FP64-accurate rotation of the same Q is ~2^-50 of the result
+        R.rcf_rotate(ctx, _dev(Y), _dev(Q), X, R.RCF_RR_TC)
+        assert np.linalg.norm(X.cpu().numpy().T - ref) / np.linalg.norm(ref) < 1e-14
+    assert errs[0] > 1e-10 and errs[1] < errs[0] * 1e-2      # proportional to ||Q_offdiag||
+    with pytest.raises(R.RcfError):
+        Yd = _dev(Y)
+        R.rcf_rotate(ctx, Yd, _dev(np.eye(n, dtype=np.complex128)), Yd, R.RCF_RR_MIXED)   # in place refused
+
+
+def test_eigensolver_loop_with_mixed_rotation_reaches_oracle(cfg1):
+    """Algorithm 1 with the mixed FP32 R-ChFSI filter and the mixed-precision rotation
+    (RCF_RR_MIXED) converges to residuals below 1e-9 and to the oracle's eigenvalues within
+    1e-7 Ha, like the FP64 rotation: near convergence Q is nearly diagonal, so the FP32-level
+    error of Y Q_offdiag is small in absolute terms (Section III-C-4)."""
+    import torch
+    from oracle import rchfsi_eigensolver
+    from paper_2605_30128_gb300 import rchfsi as R
+    H, nw = cfg1.H, 28
+    X0 = workloads.complex_normal(cfg1.w.seed + 100, (H.N, cfg1.w.nvec))
+    from oracle import lanczos_bounds
+    _, hi, *_ = lanczos_bounds(H, workloads.complex_normal(cfg1.w.seed + 200, H.N), cfg1.w.lanczos)
+    _, ref, _ = rchfsi_eigensolver(H, X0, q=10, lmax=hi, tol=1e-10, max_cycles=120, nwanted=nw)
+    ctx, op = cfg1.g.ctx, cfg1.g.op
+    hists = {}
+    for arith in (R.RCF_RR_TC, R.RCF_RR_MIXED):
+        R.rcf_set_rr_arith(ctx, arith)
+        try:
+            Yd = to_dev(X0)
+            Xd = torch.zeros_like(Yd)
+            lam = R.rcf_rayleigh_ritz(ctx, op, Yd, Xd)
+            cn = torch.zeros(X0.shape[1], dtype=torch.float64, device="cuda")
+            hist = []
+            for c in range(150):
+                R.rcf_residual(ctx, op, Xd, lam, None, cn)
+                hist.append(cn.cpu().numpy()[:nw].max())
+                if hist[-1] < 1e-9:
+                    break
+                R.rcf_filter(ctx, op, Xd, lam, 10, (float(lam.min()), float(lam.max()), hi), R.RCF_RCHFSI,
+                             R.RCF_FP32, 0, Yd)
+                lam = R.rcf_rayleigh_ritz(ctx, op, Yd, Xd)
+        finally:
+            R.rcf_set_rr_arith(ctx, R.RCF_RR_TC)
+        assert hist[-1] < 1e-9, (arith, hist[-5:])
+        assert np.max(np.abs(lam[:nw] - ref[:nw])) < 1e-7, arith
+        hists[arith] = hist
+    assert abs(len(hists[R.RCF_RR_MIXED]) - len(hists[R.RCF_RR_TC])) <= 2
