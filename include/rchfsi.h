@@ -310,6 +310,28 @@ int rcf_cholqr2(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int nvec
 int rcf_rayleigh_ritz_orth(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nvec,
                            double* X_out, int64_t ldx, double* ritz_out);
 
+/* ---- electrostatics: Poisson solve (Section III-B-1; Algorithm pcg_fusion) ---- */
+
+/* y = K x for scalar nodal fields on the mesh (device FP64 [nnodes], node
+ * I = x + G_x (y + G_y z)), K_IJ = int grad N_I . grad N_J the periodic FE
+ * Laplacian, applied matrix-free (the paper's K x kernel; twice the kinetic
+ * term of Eq. hloc).  y must not overlap x.  Asynchronous on the context's
+ * stream. */
+int rcf_laplacian(rcf_ctx* ctx, const rcf_mesh* mesh, const double* x, double* y);
+
+/* Solve K x = f by preconditioned CG in the fused arrangement of Algorithm
+ * pcg_fusion, FP64 throughout, vectors and scalars on the device.  f and x:
+ * device [nnodes]; x holds the initial guess on entry and the solution on exit
+ * (K is singular on the periodic mesh: f must have zero sum, and the solution
+ * keeps the mean of the guess).  Preconditioner P^-1 = chi(A) diag(K)^-1 with
+ * A = diag(K)^-1 K and chi the degree cheb_degree polynomial of Chebyshev
+ * semi-iteration on the interval [a, b] of A's spectrum (0 < a < b; degree 0:
+ * plain Jacobi).  Stops when ||r||_2 < tol or after maxit iterations; writes
+ * the iteration count and the final ||r||_2 to the host.  Synchronises once
+ * per iteration for the convergence test. */
+int rcf_poisson_pcg(rcf_ctx* ctx, const rcf_mesh* mesh, const double* f, double* x, int cheb_degree,
+                    double a, double b, double tol, int maxit, int* iterations, double* residual);
+
 /* ---- derivatives (no counterpart in the paper) ------------------------- */
 
 /* Accumulate (+=) the derivatives of weight * Re tr(W^H H U) with respect to

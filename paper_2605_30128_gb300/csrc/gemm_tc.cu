@@ -13,18 +13,19 @@
 // (the omitted s + t > T + 1 terms are below the truncation r).  Each digit product
 // is at most 2^14 in magnitude, so a sum over WIN = 1024 consecutive k is an integer of
 // magnitude <= 2^24: the tensor core's FP32 accumulation of such a window is exact.
-// Each (window, s, t) accumulator is drained from tensor memory into a 64-bit
-// fixed-point sum per output entry (F = sum_w S_w 2^(FIX - BETA (w - 2)), w = s + t),
-// so the only rounding is the truncation of digit products below 2^-FIX of the
-// leading term and the final conversion to FP64.
+// Each (window, s, t) accumulator is drained from tensor memory into two 64-bit
+// fixed-point sums per output entry, one for the weights w = s + t <= 4 (kept in tensor
+// memory) and one for w >= 5 (kept in registers), each with every shift a left shift: the
+// digit products are summed exactly, and the only roundings are the digit truncation and
+// the final conversion to FP64.
 //
 // Kernel: one CTA per 128 x 128 output tile and K range, persistent over its
 // windows.  Warp 0 issues the TMA loads of the two operand tiles (128 rows x 64 k,
 // bf16, 128-byte swizzle) into a 6-stage shared-memory ring; warp 1 (one thread)
 // issues tcgen05.mma (M = N = 128, K = 16, FP32 accumulate) into one of two
-// 128-column accumulators in tensor memory; warps 2..9 drain the other accumulator
-// (tcgen05.ld) into the fixed-point sums they hold in registers (each warp: 32
-// rows x 64 columns).  Every wait is bounded; on time-out the CTA records an error
+// 128-column accumulators in tensor memory; warps 4..11 (two warpgroups, given most of
+// the registers by setmaxnreg) drain the other accumulator (tcgen05.ld) into the
+// fixed-point sums (each warp: 32 rows x 64 columns).  Every wait is bounded; on time-out the CTA records an error
 // word, waits (bounded) for its copies and MMAs in flight, frees its tensor memory
 // and returns.  All copies use this GPU's own memory; no cluster, no multicast.
 #include <cuda.h>
@@ -44,9 +45,16 @@ constexpr int WIN = 1024;        // k per exact FP32 window
 constexpr int BK = 64;           // k per staged tile (128 bytes of bf16: one swizzle row)
 constexpr int TM = 128, TN = 128;
 constexpr int NSTAGE = 6;
-constexpr int FIX = 34;          // fixed-point position of the weight-2 digit products
+constexpr int FIX_HI = 34;       // fixed point of the weights 2..4 (in units of weight-2 products)
+constexpr int FIX_LO = 32;       // fixed point of the weights 5..8 (in units of weight-5 products)
+constexpr int W_SPLIT = 2;       // w - 2 <= W_SPLIT: the tensor-memory sum
 constexpr int LAUNCH_WINDOWS = 8;   // windows per CTA per launch (bounds |F| < 2^63)
-constexpr int NTHREADS = 320;
+constexpr int NTHREADS = 384;    // three warpgroups: producer + MMA (+2 idle warps), two drain groups
+// register split (setmaxnreg): launched with 168 per thread (65536 / 384 rounded down to 8);
+// warpgroup 0 drops to 40 and the two drain warpgroups rise to 232:
+// 128 x 40 + 256 x 232 = 64512 = 384 x 168
+constexpr int REG_LAUNCH = 168, REG_LOW = 40, REG_HIGH = 232;
+static_assert(128 * REG_LOW + 256 * REG_HIGH <= NTHREADS * REG_LAUNCH, "register split above the launch total");
 constexpr int TILE_BYTES = TM * BK * 2;   // 16 KB per operand tile
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // every wait gives up after 2 s
 constexpr int E_NONFINITE = 1 << 14;   // exponent of a row or column holding an Inf or a NaN
@@ -162,7 +170,39 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-// 32 lanes x 32 columns of 32-bit words from tensor memory
+// 32 lanes x 32 columns of 32-bit words from / to tensor memory
+__device__ __forceinline__ void tmem_ld32u(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st32u(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+        "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+        "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8u(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st8u(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+               ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   uint32_t r[32];
   asm volatile(
@@ -233,9 +273,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {   // tensor memory: two 128-column accumulators (the rest unused)
+  if (warp == 1) {   // tensor memory: two 128-column accumulators, then the high-weight sums
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(256)
+                 "r"(512)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -251,6 +291,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     return int((b - a + BK - 1) / BK);
   };
 
+  if (warp < 4) {
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_LOW));
   if (warp == 0) {
     // ---- producer ----
     if (lane == 0) {
@@ -320,11 +362,26 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mma_commit(smem_u32(fin));
       mbar_wait_inflight(smem_u32(fin), 0);
     }
+  }
   } else {
-    // ---- drain: warps 2..9; lanes quarter (warp % 4), columns half (warp - 2) / 4 ----
-    const int q = warp & 3, half = (warp - 2) >> 2;
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_HIGH));
+    // ---- drain: warps 4..11; lanes quarter (warp % 4), columns half (warp - 4) / 4 ----
+    const int q = warp & 3, half = (warp - 4) >> 2;
     const int r = row0 + 32 * q + lane;
-    long long F[64];
+    // high-weight sums in tensor memory: low words at columns 256 + c, high words at 384 + c
+    const uint32_t lane_base = tmem + (uint32_t(32 * q) << 16);
+    const uint32_t fh_lo = lane_base + uint32_t(2 * TN + 64 * half), fh_hi = fh_lo + TN;
+    {
+      uint32_t z[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) z[c] = 0u;
+      for (int h = 0; h < 8; ++h) {
+        tmem_st8u(fh_lo + 8 * h, z);
+        tmem_st8u(fh_hi + 8 * h, z);
+      }
+      tmem_wait_st();
+    }
+    long long F[64];   // low-weight sum
 #pragma unroll
     for (int c = 0; c < 64; ++c) F[c] = 0;
     int acc = 0;
@@ -339,27 +396,46 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         tc_fence_after();
         const int wgt = int(kProd.s[p]) + int(kProd.t[p]);   // (s - 1) + (t - 1) = w - 2
-        const int sh = FIX - BETA * wgt;
-        const uint32_t ta = tmem + (uint32_t(32 * q) << 16) + uint32_t(b * TN + 64 * half);
+        const uint32_t ta = lane_base + uint32_t(b * TN + 64 * half);
+        if (wgt <= W_SPLIT) {
+          // exact integers |v| <= 2^24 shifted left into the tensor-memory sum
+          const int sh = FIX_HI - BETA * wgt;
+#pragma unroll 1
+          for (int h = 0; h < 8; ++h) {
+            uint32_t v[8], lo[8], hi[8];
+            tmem_ld8u(ta + 8 * h, v);
+            tmem_ld8u(fh_lo + 8 * h, lo);
+            tmem_ld8u(fh_hi + 8 * h, hi);
+            tmem_wait_ld();
+            if (h == 7) {   // the whole accumulator read: it may be reused
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
+            }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float v[32];
-          tmem_ld32(ta + 32 * h, v);
-          if (h == 1) {   // both halves read: the accumulator may be reused
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
+            for (int c = 0; c < 8; ++c) {
+              const long long f = static_cast<long long>((static_cast<unsigned long long>(hi[c]) << 32) | lo[c]) +
+                                  (static_cast<long long>(__float2int_rn(__uint_as_float(v[c]))) << sh);
+              lo[c] = static_cast<uint32_t>(f);
+              hi[c] = static_cast<uint32_t>(static_cast<unsigned long long>(f) >> 32);
+            }
+            tmem_st8u(fh_lo + 8 * h, lo);
+            tmem_st8u(fh_hi + 8 * h, hi);
+            tmem_wait_st();
           }
-          // exact integers |v| <= 2^24; shifted into the fixed-point sum (right shifts round
-          // to nearest the bits below 2^-FIX of the leading digit products: flooring them
-          // would add a bias growing with the number of windows)
-          if (sh >= 0) {
+        } else {
+          const int sh = FIX_LO - BETA * (wgt - W_SPLIT - 1);
 #pragma unroll
-            for (int c = 0; c < 32; ++c) F[32 * h + c] += (long long)__float2int_rn(v[c]) << sh;
-          } else {
-            const int half_ulp = 1 << (-sh - 1);
+          for (int h = 0; h < 2; ++h) {
+            float v[32];
+            tmem_ld32(ta + 32 * h, v);
+            if (h == 1) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(smem_u32(acc_empty + b));
+            }
 #pragma unroll
-            for (int c = 0; c < 32; ++c) F[32 * h + c] += (long long)((__float2int_rn(v[c]) + half_ulp) >> (-sh));
+            for (int c = 0; c < 32; ++c) F[32 * h + c] += static_cast<long long>(__float2int_rn(v[c])) << sh;
           }
         }
       }
@@ -367,25 +443,42 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (!ok) {
       if (lane == 0) atomicExch(g.err, 1);
       *abort_flag = 1;
-    } else if (r < g.m) {
-      const int e_r = g.ea[r];
+    } else {
+      const int e_r = r < g.m ? g.ea[r] : 0;
       double* o = g.out + int64_t(blockIdx.y) * g.ss + int64_t(r) * g.rs;
 #pragma unroll
-      for (int c = 0; c < 64; c += 2) {
-        const int col = col0 + 64 * half + c;
-        if (col >= g.n) break;
-        const int e0 = e_r + g.eb[col], e1 = col + 1 < g.n ? e_r + g.eb[col + 1] : 0;
-        const double v0 = e0 >= E_NONFINITE ? __longlong_as_double(0x7FF8000000000000ll)
-                                            : ldexp(double(F[c]), e0 - FIX - 2 * BETA);
-        const double v1 = e1 >= E_NONFINITE ? __longlong_as_double(0x7FF8000000000000ll)
-                                            : (col + 1 < g.n ? ldexp(double(F[c + 1]), e1 - FIX - 2 * BETA) : 0.0);
-        double* dst = o + int64_t(col >> 1) * g.cs2;
-        if (g.accumulate) {
-          dst[0] += v0;
-          if (col + 1 < g.n) dst[1] += v1;
-        } else {
-          dst[0] = v0;
-          if (col + 1 < g.n) dst[1] = v1;
+      for (int h = 0; h < 8; ++h) {
+        uint32_t lo[8], hi[8];
+        tmem_ld8u(fh_lo + 8 * h, lo);   // warp-wide loads, before any lane leaves
+        tmem_ld8u(fh_hi + 8 * h, hi);
+        tmem_wait_ld();
+        if (r >= g.m) continue;
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+          const int col = col0 + 64 * half + 8 * h + c;
+          if (col >= g.n) break;
+          double v[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int cc = col + u;
+            if (cc >= g.n) {
+              v[u] = 0.0;
+              continue;
+            }
+            const int e = e_r + g.eb[cc];
+            const long long fh = static_cast<long long>((static_cast<unsigned long long>(hi[c + u]) << 32) | lo[c + u]);
+            v[u] = e >= E_NONFINITE ? __longlong_as_double(0x7FF8000000000000ll)
+                                    : ldexp(double(fh), e - FIX_HI - 2 * BETA) +
+                                          ldexp(double(F[8 * h + c + u]), e - FIX_LO - 3 * BETA - 2 * BETA);
+          }
+          double* dst = o + int64_t(col >> 1) * g.cs2;
+          if (g.accumulate) {
+            dst[0] += v[0];
+            if (col + 1 < g.n) dst[1] += v[1];
+          } else {
+            dst[0] = v[0];
+            if (col + 1 < g.n) dst[1] = v[1];
+          }
         }
       }
     }
@@ -394,7 +487,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
   }
 }
 

@@ -33,7 +33,7 @@ EXPORTS = [
     "rcf_apply_noalloc", "rcf_set_step_kernel", "rcf_residual_df", "rcf_cholqr2",
     "rcf_rayleigh_ritz_orth", "rcf_filter_host", "rcf_set_rr_arith",
     "rcf_bfp_stream_bytes", "rcf_bfp_encode", "rcf_bfp_decode", "rcf_ritz_cotangent",
-    "rcf_set_wait_limit", "rcf_inner", "rcf_rotate",
+    "rcf_set_wait_limit", "rcf_inner", "rcf_rotate", "rcf_laplacian", "rcf_poisson_pcg",
 ]
 
 _lib = None
@@ -93,6 +93,8 @@ def lib() -> ctypes.CDLL:
         "rcf_bfp_encode": (i32, [vp, vp, i64, i32, vp]),
         "rcf_bfp_decode": (i32, [vp, vp, i64, i32, vp]),
         "rcf_set_wait_limit": (i32, [vp, i64]),
+        "rcf_laplacian": (i32, [vp, vp, vp, vp]),
+        "rcf_poisson_pcg": (i32, [vp, vp, vp, vp, i32, dbl, dbl, dbl, i32, vp, vp]),
         "rcf_inner": (i32, [vp, vp, i64, i32, vp, i64, i32, i64, vp, vp, i64, i32]),
         "rcf_rotate": (i32, [vp, vp, i64, i32, vp, i64, i64, vp, i64, i32]),
         "rcf_ritz_cotangent": (i32, [vp, vp, vp, i64, vp, i64, i32, vp, vp, vp, i64, vp, vp, vp]),
@@ -455,6 +457,27 @@ def rcf_rotate(ctx, Y, Q, X, arith: int = 2, nrows=None):
     px, ldx = _dev(X, torch.complex128, "X")
     rows = Y.shape[1] if nrows is None else int(nrows)
     _check(ctx, lib().rcf_rotate(ctx, py, ldy, Y.shape[0], pq, ldq, rows, px, ldx, int(arith)))
+
+
+def _field(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def rcf_laplacian(ctx, mesh, x, y):
+    """y = K x (scalar nodal fields, float64 CUDA tensors of nnodes entries)."""
+    _check(ctx, lib().rcf_laplacian(ctx, mesh, _field(x, "x"), _field(y, "y")))
+
+
+def rcf_poisson_pcg(ctx, mesh, f, x, cheb_degree: int, a: float, b: float, tol: float, maxit: int):
+    """Solve K x = f (x: initial guess in, solution out); returns (iterations, final ||r||)."""
+    it = ctypes.c_int(0)
+    res = ctypes.c_double(0.0)
+    _check(ctx, lib().rcf_poisson_pcg(ctx, mesh, _field(f, "f"), _field(x, "x"), int(cheb_degree), float(a),
+                                      float(b), float(tol), int(maxit), ctypes.byref(it), ctypes.byref(res)))
+    return it.value, res.value
 
 
 def rcf_set_wait_limit(ctx, polls: int) -> None:
