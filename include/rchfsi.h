@@ -166,13 +166,22 @@ int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec, const void
  * inside the library's device image, present on every GPU that loads the
  * library until the process exits.  Limit: natoms * nvec <= 16384 per call;
  * larger calls return RCF_EINVAL with a message (split the vectors).  The
- * first call on a device looks up the array's device address (once per
- * device).  All calls share the one array: calls that may run at the same
+ * first call on a context looks up the array's device address with the
+ * context's device current; with lazy module loading that first lookup may
+ * load the library's device code, a driver-side allocation, so make the first
+ * call at set-up, before any stream capture.  A context created after a
+ * cudaDeviceReset looks the address up again.  All calls share the one
+ * array: calls that may run at the same
  * time on the GPU (different streams or contexts) race and must be
  * serialised by the caller.  Nothing in the array needs clearing between
  * calls: each call overwrites the coefficients it reads. */
 int rcf_apply_noalloc(rcf_ctx* ctx, const rcf_op* op, int form, const void* X, int64_t ldx,
                       int nvec, void* Y, int64_t ldy, int prec);
+
+/* Bytes of device scratch memory this context holds (its grow-only slots,
+ * allocated on first use by the calls that need them and freed by
+ * rcf_destroy); library-specific, for memory accounting. */
+int64_t rcf_workspace_bytes(const rcf_ctx* ctx);
 
 /* Number of kernels this context has launched so far (its own kernels; the
  * dense library routines of Rayleigh-Ritz are not counted). */

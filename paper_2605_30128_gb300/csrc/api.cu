@@ -231,6 +231,14 @@ extern "C" int rcf_set_rr_arith(rcf_ctx* ctx, int kind) {
   return RCF_OK;
 }
 
+extern "C" int64_t rcf_workspace_bytes(const rcf_ctx* ctx) {
+  if (!ctx) return -1;
+  int64_t b = 0;
+  for (size_t i = 0; i < ctx->ws_ptr.size(); ++i)
+    if (ctx->ws_ptr[i]) b += int64_t(ctx->ws_size[i]);
+  return b;
+}
+
 extern "C" int rcf_set_wait_limit(rcf_ctx* ctx, int64_t polls) {
   if (!ctx) return RCF_EINVAL;
   if (polls < 0) return fail(ctx, RCF_EINVAL, "wait limit must be >= 0 polls");

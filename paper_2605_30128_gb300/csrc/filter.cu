@@ -656,7 +656,7 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
                       ctx->copy_in));
     return cuda_check(ctx, cudaEventRecord(ev_in[b], ctx->copy_in));
   };
-  st = copy_in(0);
+  if (st == RCF_OK) st = copy_in(0);
   for (int b = 0; b < nblk && st == RCF_OK; ++b) {
     const int n = count(b);
     st = cuda_check(ctx, cudaStreamWaitEvent(ctx->stream, ev_in[b], 0));

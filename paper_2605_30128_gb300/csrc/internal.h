@@ -41,6 +41,7 @@ struct rcf_ctx {
   int step_kernel = RCF_STEP_CPASYNC;   // FP32 step kernel (rcf_set_step_kernel)
   int rr_arith = RCF_RR_TC;             // tall products of Cholesky-QR and Rayleigh-Ritz (rcf_set_rr_arith)
   int64_t wait_limit = int64_t(1) << 24;   // polls of a bounded device-side wait (rcf_set_wait_limit)
+  void* noalloc_scratch = nullptr;          // device address of rcf_apply_noalloc's fixed array
   cudaStream_t copy_in = nullptr;       // host-to-device and device-to-host streams of
   cudaStream_t copy_out = nullptr;      // rcf_filter_host (created on first use)
   // grow-only scratch buffers, one per slot

@@ -9,8 +9,6 @@
 // For them this variant keeps that scratch in a fixed array in device memory
 // that is part of the loaded library (every GPU that loads the library holds
 // it until the process exits) and allocates nothing.
-#include <mutex>
-
 #include "internal.h"
 
 namespace rcf {
@@ -23,26 +21,22 @@ constexpr int64_t kNoallocDoubles = 2 * kNoallocAtomVectors * 24;
 
 static __device__ __align__(256) double g_projector_scratch[kNoallocDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_projector_scratch on `device`, looked up once per device with that
-// device current (host code must not use the symbol itself as a device pointer).
-int scratch_address(rcf_ctx* ctx, int device, void** out) {
-  if (device < 0 || device >= kMaxDevices) return fail(ctx, RCF_EINVAL, "device %d out of range", device);
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[device]) {
+// Device address of g_projector_scratch for the context's device, looked up on the first call
+// on that context with its device current (host code must not use the symbol itself as a
+// device pointer).  Kept per context, so a context created after a cudaDeviceReset looks it up
+// again instead of keeping an address from before the reset.
+int scratch_address(rcf_ctx* ctx, void** out) {
+  if (!ctx->noalloc_scratch) {
     int cur = -1;
     RCF_CUDA(ctx, cudaGetDevice(&cur));
-    if (cur != device) RCF_CUDA(ctx, cudaSetDevice(device));
+    if (cur != ctx->device) RCF_CUDA(ctx, cudaSetDevice(ctx->device));
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_projector_scratch);
-    if (cur != device) cudaSetDevice(cur);
+    if (cur != ctx->device) cudaSetDevice(cur);
     if (e != cudaSuccess || !p) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_projector_scratch)", __FILE__, __LINE__);
-    g_scratch_addr[device] = p;
+    ctx->noalloc_scratch = p;
   }
-  *out = g_scratch_addr[device];
+  *out = ctx->noalloc_scratch;
   return RCF_OK;
 }
 
@@ -107,7 +101,7 @@ extern "C" int rcf_apply_noalloc(rcf_ctx* ctx, const rcf_op* op, int form, const
                 "(apply fewer vectors per call, or use rcf_apply)",
                 (long long)atom_vectors, (long long)kNoallocAtomVectors);
   void* base = nullptr;
-  RCF_TRY(scratch_address(ctx, ctx->device, &base));
+  RCF_TRY(scratch_address(ctx, &base));
   const size_t half = size_t(kNoallocAtomVectors) * 24;   // doubles per array
   if (prec == RCF_FP64) {
     double* C = static_cast<double*>(base);

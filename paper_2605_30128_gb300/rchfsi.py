@@ -33,7 +33,7 @@ EXPORTS = [
     "rcf_apply_noalloc", "rcf_set_step_kernel", "rcf_residual_df", "rcf_cholqr2",
     "rcf_rayleigh_ritz_orth", "rcf_filter_host", "rcf_set_rr_arith",
     "rcf_bfp_stream_bytes", "rcf_bfp_encode", "rcf_bfp_decode", "rcf_ritz_cotangent",
-    "rcf_set_wait_limit", "rcf_inner", "rcf_rotate", "rcf_laplacian", "rcf_poisson_pcg",
+    "rcf_set_wait_limit", "rcf_inner", "rcf_rotate", "rcf_laplacian", "rcf_poisson_pcg", "rcf_workspace_bytes",
 ]
 
 _lib = None
@@ -94,6 +94,7 @@ def lib() -> ctypes.CDLL:
         "rcf_bfp_decode": (i32, [vp, vp, i64, i32, vp]),
         "rcf_set_wait_limit": (i32, [vp, i64]),
         "rcf_laplacian": (i32, [vp, vp, vp, vp]),
+        "rcf_workspace_bytes": (i64, [vp]),
         "rcf_poisson_pcg": (i32, [vp, vp, vp, vp, i32, dbl, dbl, dbl, i32, vp, vp]),
         "rcf_inner": (i32, [vp, vp, i64, i32, vp, i64, i32, i64, vp, vp, i64, i32]),
         "rcf_rotate": (i32, [vp, vp, i64, i32, vp, i64, i64, vp, i64, i32]),
@@ -464,6 +465,11 @@ def _field(t, name):
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
         raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def rcf_workspace_bytes(ctx) -> int:
+    """Bytes of device scratch memory the context holds."""
+    return int(lib().rcf_workspace_bytes(ctx))
 
 
 def rcf_laplacian(ctx, mesh, x, y):

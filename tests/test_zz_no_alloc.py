@@ -46,3 +46,28 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(pair):
         R.rcf_apply_noalloc(pair.g.ctx, pair.g.op, 2, Xd, Yd, R.RCF_FP32)
     assert e.value.status == R.RCF_EINVAL
     assert "capacity" in str(e.value)
+
+
+def test_noalloc_allocates_nothing_on_a_fresh_context(pair):
+    """The promise itself: on a context and operator that have never run rcf_apply, the
+    allocation-free product leaves the context's scratch memory at zero bytes, and still
+    agrees with rcf_apply (which then allocates its scratch)."""
+    import torch
+    from paper_2605_30128_gb300 import rchfsi as R
+    from paper_2605_30128_gb300.problem import GPUProblem
+    g = GPUProblem(pair.w, params=pair.params)
+    try:
+        g.set_potential(pair.V, pair.B)
+        assert R.rcf_workspace_bytes(g.ctx) == 0
+        X = to_dev(workloads.complex_normal(77, (pair.N, 5)))
+        Y1 = torch.zeros_like(X)
+        for _ in range(2):
+            R.rcf_apply_noalloc(g.ctx, g.op, 0, X, Y1, R.RCF_FP64)
+        torch.cuda.synchronize()
+        assert R.rcf_workspace_bytes(g.ctx) == 0
+        Y2 = torch.zeros_like(X)
+        R.rcf_apply(g.ctx, g.op, 0, X, Y2, R.RCF_FP64)
+        assert R.rcf_workspace_bytes(g.ctx) > 0          # rcf_apply keeps its coefficients in scratch
+        assert rel(to_host(Y1), to_host(Y2)) < 1e-12
+    finally:
+        g.close()
