@@ -326,7 +326,7 @@ def assemble_line(w, ws: int, steps: int, warmup: int, m: dict) -> dict:
                        "ms_per_step": e["ms"], "sample": e["sample"], "link": e["link"],
                        "call": "rcf_filter_host, RCF_FP32 (pinned host X and Y; wall clock around the "
                                "synchronising call)"}
-    for key in ("adjoint", "bfp_codec"):
+    for key in ("adjoint", "bfp_codec", "poisson"):
         if key in m:
             line[key] = m[key]
     if "cpu_baseline" in m:
@@ -389,6 +389,39 @@ def codec_leg(R, ctx, op, Xb, ritz_b, peak, stream):
                     note="algorithmic bytes = 4 per value + the stream; frac of the measured copy bandwidth")
     except Exception as exc:
         return {"error": repr(exc)[:300]}
+
+def poisson_leg(R, ctx, mesh, w, dev, gen, timed):
+    """K x on the scalar nodal field of the mesh (10 launches timed) and one PCG solve with a
+    degree-5 Chebyshev-Jacobi preconditioner (interval from the Gershgorin bound) of a seeded
+    zero-sum right-hand side to an absolute residual of 1e-10 (the paper's setting, p = 7 there).
+    Any failure is reported in the returned object."""
+    import torch
+    try:
+        n = w.nnodes
+        x = torch.randn((n,), dtype=torch.float64, device=dev, generator=gen)
+        y = torch.empty_like(x)
+        R.rcf_laplacian(ctx, mesh, x, y)
+        kx_ms = timed(lambda: R.rcf_laplacian(ctx, mesh, x, y), 10)
+        f = torch.randn((n,), dtype=torch.float64, device=dev, generator=gen)
+        f -= f.mean()
+        xs = torch.zeros_like(f)
+        t0 = time.perf_counter()
+        it, res = R.rcf_poisson_pcg(ctx, mesh, f, xs, 5, 0.0, 0.0, 1e-10, 5000)
+        torch.cuda.synchronize()
+        pcg_ms = (time.perf_counter() - t0) * 1e3
+        p = w.p
+        taps = 3.0 * (2 * p + 1 + (p - 1) * (p + 1)) / p        # stencil taps per node, 3 directions
+        flops = 2.0 * taps + 9.0                                   # FMA per tap; weights and sums
+        return {"nodes": n, "kx_ms": kx_ms, "kx_dofs_per_s": n / (kx_ms * 1e-3),
+                "kx_fp64_tflops": n * flops / (kx_ms * 1e-3) / 1e12, "flop_per_dof": flops,
+                "fp64_peak_tflops_nominal": 1.25, "kx_frac_of_nominal_fp64": n * flops / (kx_ms * 1e-3) / 1.25e15,
+                "pcg_iterations": it, "pcg_residual": res, "pcg_ms": pcg_ms,
+                "pcg_ms_per_iteration": pcg_ms / max(it, 1), "chebyshev_degree": 5,
+                "note": "scalar periodic FE Laplacian on the bench mesh, FP64; PCG wall clock includes one "
+                        "host read of the residual norm per iteration"}
+    except Exception as exc:
+        return {"error": repr(exc)[:300]}
+
 
 def run_ours(args):
     import numpy as np
@@ -583,6 +616,10 @@ def run_ours(args):
                             "points, checkpoints every %d steps" % wa.ckpt)
         pa_.close()
         del Xa, Ya, Ybar, dV, dB
+
+        # ---- the periodic Poisson solve on the same mesh (Section III-B-1; Algorithm
+        #      pcg_fusion): the matrix-free K x kernel and the fused PCG ----
+        m["poisson"] = poisson_leg(R, ctx, prob.mesh, w, dev, gen, timed)
 
         # ---- block floating-point codec (Section III-C-3) on one residual block ----
         m["bfp_codec"] = codec_leg(R, ctx, op, X[:blk], ritz[:blk], peak[0], stream)

@@ -334,8 +334,9 @@ int rcf_laplacian(rcf_ctx* ctx, const rcf_mesh* mesh, const double* x, double* y
  * (K is singular on the periodic mesh: f must have zero sum, and the solution
  * keeps the mean of the guess).  Preconditioner P^-1 = chi(A) diag(K)^-1 with
  * A = diag(K)^-1 K and chi the degree cheb_degree polynomial of Chebyshev
- * semi-iteration on the interval [a, b] of A's spectrum (0 < a < b; degree 0:
- * plain Jacobi).  Stops when ||r||_2 < tol or after maxit iterations; writes
+ * semi-iteration on the interval [a, b] of A's spectrum (0 < a < b; b <= 0:
+ * b = the Gershgorin bound of A's spectrum and a = b / 20; degree 0: plain
+ * Jacobi).  Stops when ||r||_2 < tol or after maxit iterations; writes
  * the iteration count and the final ||r||_2 to the host.  Synchronises once
  * per iteration for the convergence test. */
 int rcf_poisson_pcg(rcf_ctx* ctx, const rcf_mesh* mesh, const double* f, double* x, int cheb_degree,

@@ -16,6 +16,7 @@
 // P^-1 = chi(A) diag(K)^-1, A = diag(K)^-1 K, chi the degree-m polynomial of Chebyshev
 // semi-iteration on [a, b] (textbook three-term recurrence); each of its steps is one
 // fused K x pass that also updates the iterate, its residual and the next direction.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -266,6 +267,25 @@ __global__ void kdiag_kernel(const LapTables t, int P, double* __restrict__ kd, 
           t.c[2][ak][P] * t.wg[ai] * t.wg[aj];
 }
 
+// Gershgorin bound of the spectrum of diag(K)^-1 K: max over the local positions of
+// sum_J |K_IJ| / K_II (every node of a uniform mesh is one of p^3 local positions)
+double gershgorin_top(const LapTables& t, int p) {
+  double best = 0.0;
+  for (int ai = 0; ai < p; ++ai)
+    for (int aj = 0; aj < p; ++aj)
+      for (int ak = 0; ak < p; ++ak) {
+        const int a[3] = {ai, aj, ak};
+        double row = 0.0, diag = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          const double wp = t.wg[a[(d + 1) % 3]] * t.wg[a[(d + 2) % 3]];
+          for (int o = 0; o <= 2 * p; ++o) row += std::fabs(t.c[d][a[d]][o]) * wp;
+          diag += t.c[d][a[d]][p] * wp;
+        }
+        best = std::max(best, row / diag);
+      }
+  return best;
+}
+
 int check_field(rcf_ctx* ctx, const void* p, const char* name) {
   if (!p) return fail(ctx, RCF_EINVAL, "%s is NULL", name);
   if (reinterpret_cast<uintptr_t>(p) & 7) return fail(ctx, RCF_EINVAL, "%s is not 8-byte aligned", name);
@@ -298,7 +318,8 @@ extern "C" int rcf_poisson_pcg(rcf_ctx* ctx, const rcf_mesh* mesh, const double*
   RCF_TRY(check_field(ctx, x, "x"));
   if (!iterations || !residual) return fail(ctx, RCF_EINVAL, "iterations and residual must be host pointers");
   if (cheb_degree < 0 || maxit < 0 || !(tol >= 0.0)) return fail(ctx, RCF_EINVAL, "bad degree, tolerance or limit");
-  if (cheb_degree > 0 && !(0.0 < a && a < b)) return fail(ctx, RCF_EINVAL, "the Chebyshev interval needs 0 < a < b");
+  if (cheb_degree > 0 && b > 0.0 && !(0.0 < a && a < b))
+    return fail(ctx, RCF_EINVAL, "the Chebyshev interval needs 0 < a < b");
   const int64_t n = mesh->nnodes;
   {
     const char* pf = reinterpret_cast<const char*>(f);
@@ -309,6 +330,10 @@ extern "C" int rcf_poisson_pcg(rcf_ctx* ctx, const rcf_mesh* mesh, const double*
   LapTables t;
   std::vector<double> kd1;
   build_lap_tables(mesh, &t, &kd1);
+  if (cheb_degree > 0 && !(b > 0.0)) {   // interval from the Gershgorin bound
+    b = gershgorin_top(t, mesh->p);
+    a = b / 20.0;
+  }
   // r, z, p, w, res, d0, d1, kdiag; reduction partials; device scalars
   double* ws = nullptr;
   const size_t vec = size_t(n);

@@ -145,3 +145,21 @@ def test_invalid_arguments():
             R.rcf_laplacian(ctx, gm, f, f)                                     # y overlaps x
     finally:
         _close(ctx, gm)
+
+
+def test_default_interval_from_the_gershgorin_bound():
+    """b <= 0: the library takes the Chebyshev interval from the Gershgorin bound of
+    diag(K)^-1 K; the solve converges to the oracle's solution."""
+    import torch
+    from paper_2605_30128_gb300 import rchfsi as R
+    ctx, gm, _ = _mesh_pair(3, 6.0, 5)
+    try:
+        mesh, K, Kd, f, b = _problem(3, 6.0, 5, seed=3)
+        xo, _, _ = pcg(K, f, lambda r: chebyshev_jacobi(K, Kd, r, 5, b / 20.0, b), 1e-11, 2000)
+        fd = torch.from_numpy(f).cuda()
+        x = torch.zeros_like(fd)
+        it, res = R.rcf_poisson_pcg(ctx, gm, fd, x, 5, 0.0, 0.0, 1e-11, 2000)
+        assert res < 1e-11 and it > 0
+        np.testing.assert_allclose(x.cpu().numpy(), xo, atol=1e-9 * np.abs(xo).max())
+    finally:
+        _close(ctx, gm)
