@@ -319,6 +319,36 @@ int rcf_cholqr2(rcf_ctx* ctx, const rcf_op* op, double* Y, int64_t ldy, int nvec
 int rcf_rayleigh_ritz_orth(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int nvec,
                            double* X_out, int64_t ldx, double* ritz_out);
 
+/* ---- full consistent mass (Section III-A; Section III-B-2) ---------------- */
+
+/* Switch the operator to the full consistent mass with nq Gauss-Legendre points
+ * per direction (p + 1 <= nq <= 12; exact for the mass and kinetic integrals):
+ * M_{2I+a,2J+b} = delta_ab int N_I N_J, the kinetic and potential integrals by
+ * the same rule, V and B given at the Gauss points, the spin-orbit projector
+ * columns int N_I beta.  D, the GLL-integrated (lumped) mass, stays the
+ * filter's diagonal in place of M^-1, as in the paper.  Call before
+ * rcf_potential_set / rcf_projectors_set, which then take V [ncells][nq^3] and
+ * B [3][ncells][nq^3] at the points of rcf_op_gauss_points (point
+ * q = qx + nq (qy + nq qz)).  With the full mass: rcf_apply (FP64, FP32),
+ * rcf_cheb_step, rcf_residual (R = HX - M X Lambda with the full M),
+ * rcf_filter (FP64; FP32 recurrence with the FP64 residual), the Lanczos
+ * bound, Cholesky-QR and Rayleigh-Ritz (Y^H M Y with the full M) and
+ * rcf_mass_apply; the double-float residual, 16-bit storage, the adjoint, the
+ * gradients, the Ritz cotangent and rcf_apply_noalloc return RCF_ENOTSUP.
+ * Synchronises. */
+int rcf_op_set_gauss(rcf_op* op, int nq);
+
+/* Coordinates of the Gauss points of a full-mass operator (host
+ * [ncells][nq^3][3]).  RCF_EINVAL for a lumped operator. */
+int rcf_op_gauss_points(const rcf_op* op, double* out);
+
+/* Y = M X: the full consistent mass (three 1D passes) for an operator made
+ * with rcf_op_set_gauss (prec RCF_FP64 or RCF_FP32), else the lumped diagonal
+ * (RCF_FP64).  Layouts as rcf_apply; Y must not overlap X.  Asynchronous on
+ * the context's stream. */
+int rcf_mass_apply(rcf_ctx* ctx, const rcf_op* op, const void* X, int64_t ldx, int nvec, void* Y,
+                   int64_t ldy, int prec);
+
 /* ---- electrostatics: Poisson solve (Section III-B-1; Algorithm pcg_fusion) ---- */
 
 /* y = K x for scalar nodal fields on the mesh (device FP64 [nnodes], node

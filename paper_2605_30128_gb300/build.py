@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librchfsi.so")
 SOURCES = ["api.cu", "stencil.cu", "stencil_tma.cu", "residual_df.cu", "gemm_df.cu", "nonlocal.cu", "vectors.cu", "filter.cu", "rr.cu",
-           "noalloc.cu", "bfp.cu", "gemm_tc.cu", "poisson.cu"]
+           "noalloc.cu", "bfp.cu", "gemm_tc.cu", "poisson.cu", "fullmass.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

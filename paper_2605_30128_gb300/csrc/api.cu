@@ -405,6 +405,7 @@ extern "C" int rcf_op_destroy(rcf_op* op) {
   cudaFree(op->d_pot32);
   cudaFree(op->d_potdf);
   free_proj(&op->proj);
+  free_fm(op->fm);
   delete op;
   return RCF_OK;
 }
@@ -413,7 +414,7 @@ extern "C" int rcf_potential_set(rcf_op* op, const double* V, const double* B, i
   if (!op) return RCF_EINVAL;
   rcf_ctx* ctx = op->ctx;
   const rcf_mesh* m = op->mesh;
-  const size_t nq = size_t(m->ncells) * m->nloc;
+  const size_t nq = size_t(m->ncells) * (op->fm ? op->fm->nq * op->fm->nq * op->fm->nq : m->nloc);
   std::vector<double> hv, hb;
   if (V && on_device) {
     hv.resize(nq);
@@ -425,6 +426,7 @@ extern "C" int rcf_potential_set(rcf_op* op, const double* V, const double* B, i
     RCF_CUDA(ctx, cudaMemcpy(hb.data(), B, sizeof(double) * 3 * nq, cudaMemcpyDeviceToHost));
     B = hb.data();
   }
+  if (op->fm) return fm_set_potential(ctx, op, V, B);
   std::vector<double> pot(4 * size_t(m->nnodes), 0.0);
   if (V || B) {
     for (int64_t e = 0; e < m->ncells; ++e)
@@ -474,7 +476,9 @@ extern "C" int rcf_projectors_set(rcf_op* op, int natoms, const double* pos, con
   pa.offsets.assign(natoms + 1, 0);
   pa.hcoup.assign(h, h + 2 * natoms);
   const double pi = 3.14159265358979323846;
-  for (int a = 0; a < natoms; ++a) {
+  if (op->fm) RCF_TRY(fm_projector_entries(ctx, op, natoms, pos, width, rcut_factor, &pa.node, &pa.atom, &pa.beta,
+                                           &pa.offsets));
+  for (int a = 0; a < natoms && !op->fm; ++a) {
     for (int j = 0; j < 2; ++j)
       if (!(width[2 * a + j] > 0.0)) return fail(ctx, RCF_EINVAL, "projector width must be > 0");
     const double rc = rcut_factor * std::max(width[2 * a], width[2 * a + 1]);

@@ -168,6 +168,12 @@ double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, i
 //   form H:      out = M (A (D^{-1} H_loc) in + B in + C prev + g rv) + A H_nloc in
 template <typename Real, typename St>
 int apply_full(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real, St>& a0) {
+  if (op->fm) {   // full consistent mass: form H's M is the full mass (fullmass.cu)
+    if constexpr (std::is_same<Real, St>::value)
+      return apply_full_fm<Real>(ctx, op, form, a0);
+    else
+      return fail(ctx, RCF_ENOTSUP, "16-bit storage is not available with the full mass");
+  }
   StepArgs<Real, St> a = a0;
   a.pot = pot_of<Real>(op);
   a.mass = op->mesh->d_mass;
@@ -747,6 +753,7 @@ extern "C" int rcf_lanczos_bounds(rcf_ctx* ctx, const rcf_op* op, int nsteps, co
 extern "C" int rcf_grad_bilinear(rcf_ctx* ctx, const rcf_op* op, const double* W, int64_t ldw,
                                  const double* U, int64_t ldu, int nvec, double weight, double* dV,
                                  double* dB, double* dh) {
+  if (op && op->fm) return fail(ctx, RCF_ENOTSUP, "gradients are not available with the full consistent mass");
   if (!ctx || !op) return RCF_EINVAL;
   RCF_TRY(check_block(ctx, op, W, ldw, nvec, 8, "W"));
   RCF_TRY(check_block(ctx, op, U, ldu, nvec, 8, "U"));
@@ -953,6 +960,7 @@ extern "C" int rcf_adjoint_filter(rcf_ctx* ctx, const rcf_op* op, const double* 
                                   int nvec, const double* ritz, int degree, const double bounds[3],
                                   int mode, int prec, const double* Ybar, int64_t ldyb,
                                   int ckpt_every, double* dV, double* dB, double* dh) {
+  if (op && op->fm) return fail(ctx, RCF_ENOTSUP, "the adjoint filter is not available with the full consistent mass");
   if (!ctx || !op) return RCF_EINVAL;
   RCF_TRY(check_block(ctx, op, X, ldx, nvec, 8, "X"));
   RCF_TRY(check_block(ctx, op, Ybar, ldyb, nvec, 8, "Ybar"));

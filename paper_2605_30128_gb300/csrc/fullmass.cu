@@ -1,0 +1,630 @@
+// The Hamiltonian and mass with the full consistent mass and Gauss-Legendre quadrature
+// (Section III-A; Section III-B-2): the paper's noncollinear setting, where the filter uses a
+// diagonal D (the GLL-integrated mass) in place of M^-1 and R-ChFSI still converges to the
+// eigenpairs of H x = eps M x.
+//
+// With nq >= p + 1 Gauss points per direction the cell integrals of the kinetic term and of
+// the mass are exact, and on a uniform mesh the assembled matrices are tensor products of
+// assembled 1D matrices: M = Mz (x) My (x) Mx and the kinetic term
+// 1/2 (Kz My Mx + Mz Ky Mx + Mz My Kx), with K the 1D stiffness (2/h) K1 and M the 1D
+// consistent mass (h/2) M1, both banded (the nodes of an element, two elements at a vertex).
+// They are applied by sum factorisation in three node passes, one per direction:
+//   x: t1 = Mx u, t2 = Kx u;  y: s1 = My t1, s2 = Ky t1 + My t2;  z: K u = Kz s1 + Mz s2
+// (the 1/2 folded into the K tables), and M u = Mz My Mx u the same way.
+// The potential V I + B . sigma is given at the Gauss points and couples all nodes of a cell:
+// per cell and vector, the nodal spinor values are interpolated to the nq^3 points (three
+// 1D contractions with the Lagrange table B1 [nq][np]), multiplied by w_q |J| (V I + B . sigma),
+// projected back (the transposed contractions) and written to a per-cell buffer; a node pass
+// then sums the contributions of the (up to 8) cells of each node, with no atomics.
+// The spin-orbit projector columns int N_I beta are computed with the same Gauss rule at
+// set-up and applied by the nonlocal kernels of the lumped operator.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+#include "stencil_common.cuh"
+
+namespace rcf {
+namespace {
+
+__device__ __forceinline__ int wrapi(int i, int G) { return i < 0 ? i + G : (i >= G ? i - G : i); }
+
+// 4 reals of node I of vector v (complex spinor: re up, im up, re down, im down)
+template <typename Real>
+__device__ __forceinline__ R4<Real> ld_node(const Real* base, int64_t ld, int v, int64_t I) {
+  return ldg4(reinterpret_cast<const R4<Real>*>(base + 2 * int64_t(v) * ld) + I);
+}
+template <typename Real>
+__device__ __forceinline__ void st_node(Real* base, int64_t ld, int v, int64_t I, const R4<Real>& x) {
+  st4(reinterpret_cast<R4<Real>*>(base + 2 * int64_t(v) * ld) + I, x);
+}
+
+// One 1D pass along direction d: out1 = c1 * in1 + c2 * in2, out2 = c3 * in1 + c4 * in2
+// (tables [p][2p + 1] by local position and offset; null tables, inputs and outputs skipped)
+template <typename Real>
+__global__ void fm_pass_kernel(int d, int p, int Gx, int Gy, int Gz, const Real* __restrict__ c1,
+                               const Real* __restrict__ c2, const Real* __restrict__ c3,
+                               const Real* __restrict__ c4, const Real* __restrict__ in1,
+                               const Real* __restrict__ in2, int64_t ldin, Real* __restrict__ out1,
+                               Real* __restrict__ out2, int64_t ldout) {
+  const int64_t I = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (I >= int64_t(Gx) * Gy * Gz) return;
+  const int idx[3] = {int(I % Gx), int((I / Gx) % Gy), int(I / (int64_t(Gx) * Gy))};
+  const int G[3] = {Gx, Gy, Gz};
+  const int64_t stride = d == 0 ? 1 : (d == 1 ? int64_t(Gx) : int64_t(Gx) * Gy);
+  const int i = idx[d], a = i % p;
+  const int lo = a == 0 ? -p : -a, hi = a == 0 ? p : p - a;
+  const int64_t base = I - int64_t(i) * stride;
+  R4<Real> o1 = zero4<Real>(), o2 = zero4<Real>();
+  const int row = a * (2 * p + 1) + p;
+  for (int o = lo; o <= hi; ++o) {
+    const int64_t J = base + int64_t(wrapi(i + o, G[d])) * stride;
+    const R4<Real> x1 = ld_node(in1, ldin, v, J);
+    if (c1) fma4(o1, c1[row + o], x1);
+    if (c3) fma4(o2, c3[row + o], x1);
+    if (in2) {
+      const R4<Real> x2 = ld_node(in2, ldin, v, J);
+      if (c2) fma4(o1, c2[row + o], x2);
+      if (c4) fma4(o2, c4[row + o], x2);
+    }
+  }
+  if (out1) st_node(out1, ldout, v, I, o1);
+  if (out2) st_node(out2, ldout, v, I, o2);
+}
+
+// Per cell e and vector v: E[v][e][l] = sum_q N_l(x_q) w_q |J| (V_q I + B_q . sigma) u(x_q),
+// u(x_q) = sum_l' N_l'(x_q) u_{node(e, l')}.  Shared memory: two buffers of S4 spinors.
+template <typename Real>
+__global__ void fm_cell_kernel(int p, int nq, int nx, int ny, int nz, const Real* __restrict__ B1,
+                               const Real* __restrict__ vq, const Real* __restrict__ in, int64_t ldin,
+                               Real* __restrict__ E, int S4) {
+  extern __shared__ __align__(16) unsigned char fm_smem[];
+  R4<Real>* bufA = reinterpret_cast<R4<Real>*>(fm_smem);
+  R4<Real>* bufB = bufA + S4;
+  const int np = p + 1;
+  const int64_t e = blockIdx.x;
+  const int v = blockIdx.y;
+  const int ex = int(e % nx), ey = int((e / nx) % ny), ez = int(e / (int64_t(nx) * ny));
+  const int Gx = nx * p, Gy = ny * p, Gz = nz * p;
+  const int nl = np * np * np, nq3 = nq * nq * nq;
+  // gather the cell's nodal values: l = a + np (b + np c)
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    const int a = l % np, b = (l / np) % np, c = l / (np * np);
+    const int64_t I = (ex * p + a) % Gx + int64_t(Gx) * ((ey * p + b) % Gy + int64_t(Gy) * ((ez * p + c) % Gz));
+    bufA[l] = ld_node(in, ldin, v, I);
+  }
+  __syncthreads();
+  // interpolate along x: A1[qx + nq (b + np c)] = sum_a B1[qx][a] U[a + np (b + np c)]
+  for (int t = threadIdx.x; t < nq * np * np; t += blockDim.x) {
+    const int qx = t % nq, bc = t / nq;
+    R4<Real> s = zero4<Real>();
+    for (int a = 0; a < np; ++a) fma4(s, B1[qx * np + a], bufA[a + np * bc]);
+    bufB[t] = s;
+  }
+  __syncthreads();
+  // along y: A2[qx + nq (qy + nq c)] = sum_b B1[qy][b] A1[qx + nq (b + np c)]
+  for (int t = threadIdx.x; t < nq * nq * np; t += blockDim.x) {
+    const int qx = t % nq, qy = (t / nq) % nq, c = t / (nq * nq);
+    R4<Real> s = zero4<Real>();
+    for (int b = 0; b < np; ++b) fma4(s, B1[qy * np + b], bufB[qx + nq * (b + np * c)]);
+    bufA[t] = s;
+  }
+  __syncthreads();
+  // along z, then the spinor potential at the point
+  const Real* vc = vq + 4 * e * int64_t(nq3);
+  for (int t = threadIdx.x; t < nq3; t += blockDim.x) {
+    const int qxy = t % (nq * nq), qz = t / (nq * nq);
+    R4<Real> u = zero4<Real>();
+    for (int c = 0; c < np; ++c) fma4(u, B1[qz * np + c], bufA[qxy + nq * nq * c]);
+    const Real V = vc[4 * t], Bx = vc[4 * t + 1], By = vc[4 * t + 2], Bz = vc[4 * t + 3];
+    // up = (V + Bz) u_up + (Bx - i By) u_dn ; dn = (Bx + i By) u_up + (V - Bz) u_dn
+    R4<Real> o;
+    o.v[0] = (V + Bz) * u.v[0] + Bx * u.v[2] + By * u.v[3];
+    o.v[1] = (V + Bz) * u.v[1] + Bx * u.v[3] - By * u.v[2];
+    o.v[2] = Bx * u.v[0] - By * u.v[1] + (V - Bz) * u.v[2];
+    o.v[3] = Bx * u.v[1] + By * u.v[0] + (V - Bz) * u.v[3];
+    bufB[t] = o;
+  }
+  __syncthreads();
+  // project along z: P2[qx + nq (qy + nq c)] = sum_qz B1[qz][c] W[qx + nq (qy + nq qz)]
+  for (int t = threadIdx.x; t < nq * nq * np; t += blockDim.x) {
+    const int qxy = t % (nq * nq), c = t / (nq * nq);
+    R4<Real> s = zero4<Real>();
+    for (int qz = 0; qz < nq; ++qz) fma4(s, B1[qz * np + c], bufB[qxy + nq * nq * qz]);
+    bufA[t] = s;
+  }
+  __syncthreads();
+  // along y: P1[qx + nq (b + np c)] = sum_qy B1[qy][b] P2[qx + nq (qy + nq c)]
+  for (int t = threadIdx.x; t < nq * np * np; t += blockDim.x) {
+    const int qx = t % nq, b = (t / nq) % np, c = t / (nq * np);
+    R4<Real> s = zero4<Real>();
+    for (int qy = 0; qy < nq; ++qy) fma4(s, B1[qy * np + b], bufA[qx + nq * (qy + nq * c)]);
+    bufB[t] = s;
+  }
+  __syncthreads();
+  // along x: E[a + np (b + np c)] = sum_qx B1[qx][a] P1[qx + nq (b + np c)]
+  R4<Real>* out = reinterpret_cast<R4<Real>*>(E) + (int64_t(v) * gridDim.x + e) * nl;
+  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
+    const int a = t % np, bc = t / np;
+    R4<Real> s = zero4<Real>();
+    for (int qx = 0; qx < nq; ++qx) fma4(s, B1[qx * np + a], bufB[qx + nq * bc]);
+    out[t] = s;
+  }
+}
+
+// T[I] += sum over the cells e containing node I of E[v][e][local index of I in e]
+template <typename Real>
+__global__ void fm_gather_kernel(int p, int nx, int ny, int nz, int64_t ncells, const Real* __restrict__ E,
+                                 Real* __restrict__ T, int64_t ldt) {
+  const int Gx = nx * p, Gy = ny * p, Gz = nz * p;
+  const int64_t I = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (I >= int64_t(Gx) * Gy * Gz) return;
+  const int i = int(I % Gx), j = int((I / Gx) % Gy), k = int(I / (int64_t(Gx) * Gy));
+  const int np = p + 1;
+  // per direction: (cell, local) pairs; a vertex belongs to the element on each side
+  int ce[3][2], cl[3][2], cn[3];
+  const int idx[3] = {i, j, k}, nc[3] = {nx, ny, nz};
+  for (int d = 0; d < 3; ++d) {
+    const int a = idx[d] % p, el = idx[d] / p;
+    ce[d][0] = el;
+    cl[d][0] = a;
+    cn[d] = 1;
+    if (a == 0) {
+      ce[d][1] = (el + nc[d] - 1) % nc[d];
+      cl[d][1] = p;
+      cn[d] = 2;
+    }
+  }
+  const R4<Real>* Ev = reinterpret_cast<const R4<Real>*>(E) + int64_t(v) * ncells * (np * np * np);
+  R4<Real> s = ld4(reinterpret_cast<const R4<Real>*>(T + 2 * int64_t(v) * ldt) + I);
+  for (int z = 0; z < cn[2]; ++z)
+    for (int y = 0; y < cn[1]; ++y)
+      for (int x = 0; x < cn[0]; ++x) {
+        const int64_t e = ce[0][x] + int64_t(nx) * (ce[1][y] + int64_t(ny) * ce[2][z]);
+        const int l = cl[0][x] + np * (cl[1][y] + np * cl[2][z]);
+        const R4<Real> w = Ev[e * (np * np * np) + l];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) s.v[c] += w.v[c];
+      }
+  st_node(T, ldt, v, I, s);
+}
+
+// elementwise combinations on node tuples (complex rows r < rows, vector v):
+//   mode 0: out = B in + C prev + g[v] rv                 (the argument of M in form H)
+//   mode 1: out = A T + W                                  (form H, W = M (B in + ...))
+//   mode 2: out = A dinv T + B in + C prev + g[v] rv       (form D^-1 H)
+//   mode 3: out = A T + B in + C prev + g[v] rv            (form H D^-1)
+//   mode 4: out = dinv in                                  (the scaled input of H D^-1)
+template <typename Real>
+__global__ void fm_combine_kernel(int mode, int64_t nodes, Real A, const Real* __restrict__ T, int64_t ldt,
+                                  const Real* __restrict__ W, int64_t ldw, Real B, const Real* in, int64_t ldin,
+                                  Real C, const Real* prev, int64_t ldprev, const double* __restrict__ g,
+                                  const Real* rv, int64_t ldrv, const double* __restrict__ dinv, Real* out,
+                                  int64_t ldout) {
+  const int64_t I = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (I >= nodes) return;
+  auto at = [&](const Real* b, int64_t ld) {
+    return ld4(reinterpret_cast<const R4<Real>*>(b + 2 * int64_t(v) * ld) + I);
+  };
+  R4<Real> o = zero4<Real>();
+  if (mode == 4) {
+    fma4(o, Real(dinv[I]), at(in, ldin));
+  } else {
+    if (mode == 1 || mode == 2 || mode == 3) fma4(o, mode == 2 ? Real(A * dinv[I]) : A, at(T, ldt));
+    if (mode == 1) {
+      const R4<Real> w = at(W, ldw);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) o.v[c] += w.v[c];
+    } else {
+      if (in && B != Real(0)) fma4(o, B, at(in, ldin));
+      if (prev) fma4(o, C, at(prev, ldprev));
+      if (rv && g) fma4(o, Real(g[v]), at(rv, ldrv));
+    }
+  }
+  st4(reinterpret_cast<R4<Real>*>(out + 2 * int64_t(v) * ldout) + I, o);
+}
+
+}  // namespace
+}  // namespace rcf
+
+namespace rcf {
+namespace {
+
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on the Legendre polynomial from the
+// Chebyshev guess; the standard construction, e.g. Numerical Recipes' gauleg)
+void gauss_legendre(int n, std::vector<double>* x, std::vector<double>* w) {
+  x->assign(n, 0.0);
+  w->assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), pp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        const double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      const double z1 = z;
+      z = z1 - p1 / pp;
+      if (std::fabs(z - z1) < 1e-16) break;
+    }
+    (*x)[i] = -z;
+    (*x)[n - 1 - i] = z;
+    (*w)[i] = (*w)[n - 1 - i] = 2.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
+// Lagrange basis l_a on the nodes xi at the point t (product formula)
+double lagrange(const std::vector<double>& xi, int a, double t) {
+  double v = 1.0;
+  for (size_t b = 0; b < xi.size(); ++b)
+    if (int(b) != a) v *= (t - xi[b]) / (xi[a] - xi[b]);
+  return v;
+}
+
+template <typename T>
+int upload_vec(rcf_ctx* ctx, T** dst, const std::vector<T>& v) {
+  if (*dst) cudaFree(*dst);
+  *dst = nullptr;
+  if (v.empty()) return RCF_OK;
+  RCF_CUDA(ctx, cudaMalloc(dst, sizeof(T) * v.size()));
+  RCF_CUDA(ctx, cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return RCF_OK;
+}
+
+template <typename Real>
+const Real* fm_tab(const FullMass* fm);
+template <>
+const double* fm_tab<double>(const FullMass* fm) { return fm->d_tab64; }
+template <>
+const float* fm_tab<float>(const FullMass* fm) { return fm->d_tab32; }
+template <typename Real>
+const Real* fm_b1(const FullMass* fm);
+template <>
+const double* fm_b1<double>(const FullMass* fm) { return fm->d_B1_64; }
+template <>
+const float* fm_b1<float>(const FullMass* fm) { return fm->d_B1_32; }
+template <typename Real>
+const Real* fm_vq(const FullMass* fm);
+template <>
+const double* fm_vq<double>(const FullMass* fm) { return fm->d_vq64; }
+template <>
+const float* fm_vq<float>(const FullMass* fm) { return fm->d_vq32; }
+
+// table of kind (0 = K, 1 = M) and direction d: [p][2p + 1]
+template <typename Real>
+const Real* table(const rcf_op* op, int kind, int d) {
+  const int p = op->mesh->p;
+  return fm_tab<Real>(op->fm) + (size_t(kind) * 3 + d) * size_t(p) * (2 * p + 1);
+}
+
+template <typename Real>
+int pass(rcf_ctx* ctx, const rcf_op* op, int d, const Real* c1, const Real* c2, const Real* c3, const Real* c4,
+         const Real* in1, const Real* in2, int64_t ldin, Real* out1, Real* out2, int64_t ldout, int nvec) {
+  const rcf_mesh* m = op->mesh;
+  fm_pass_kernel<Real><<<dim3(unsigned((m->nnodes + 255) / 256), nvec), 256, 0, ctx->stream>>>(
+      d, m->p, m->G[0], m->G[1], m->G[2], c1, c2, c3, c4, in1, in2, ldin, out1, out2, ldout);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+
+template <typename Real>
+int combine(rcf_ctx* ctx, const rcf_op* op, int mode, int nvec, Real A, const Real* T, int64_t ldt,
+            const Real* W, int64_t ldw, Real B, const Real* in, int64_t ldin, Real C, const Real* prev,
+            int64_t ldprev, const double* g, const Real* rv, int64_t ldrv, Real* out, int64_t ldout) {
+  const rcf_mesh* m = op->mesh;
+  fm_combine_kernel<Real><<<dim3(unsigned((m->nnodes + 255) / 256), nvec), 256, 0, ctx->stream>>>(
+      mode, m->nnodes, A, T, ldt, W, ldw, B, in, ldin, C, prev, ldprev, g, rv, ldrv, m->d_inv_mass64, out, ldout);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+
+template <typename Real>
+int ws_block(rcf_ctx* ctx, int slot, const rcf_op* op, int nvec, Real** p) {
+  return workspace(ctx, slot, sizeof(Real) * 4 * size_t(op->mesh->nnodes) * nvec, reinterpret_cast<void**>(p));
+}
+
+// T = H u (kinetic with the consistent 1D masses, Gauss-point potential, projectors); u, T
+// node-tuple blocks with ld = 2M
+template <typename Real>
+int hamiltonian_fm(rcf_ctx* ctx, const rcf_op* op, const Real* u, int64_t ldu, int nvec, Real* T) {
+  const rcf_mesh* m = op->mesh;
+  const FullMass* fm = op->fm;
+  const int64_t ld = 2 * m->nnodes;
+  Real *t1, *t2, *s1, *s2;
+  RCF_TRY(ws_block<Real>(ctx, WS_FM_T1, op, nvec, &t1));
+  RCF_TRY(ws_block<Real>(ctx, WS_FM_T2, op, nvec, &t2));
+  RCF_TRY(ws_block<Real>(ctx, WS_FM_S1, op, nvec, &s1));
+  RCF_TRY(ws_block<Real>(ctx, WS_FM_S2, op, nvec, &s2));
+  const Real *Kx = table<Real>(op, 0, 0), *Ky = table<Real>(op, 0, 1), *Kz = table<Real>(op, 0, 2);
+  const Real *Mx = table<Real>(op, 1, 0), *My = table<Real>(op, 1, 1), *Mz = table<Real>(op, 1, 2);
+  RCF_TRY(pass<Real>(ctx, op, 0, Mx, nullptr, Kx, nullptr, u, nullptr, ldu, t1, t2, ld, nvec));
+  RCF_TRY(pass<Real>(ctx, op, 1, My, nullptr, Ky, My, t1, t2, ld, s1, s2, ld, nvec));
+  RCF_TRY(pass<Real>(ctx, op, 2, Kz, Mz, nullptr, nullptr, s1, s2, ld, T, nullptr, ld, nvec));
+  // Gauss-point potential: per-cell contributions, then summed at the nodes
+  if (fm_vq<Real>(fm)) {
+    const int np = m->p + 1, nq = fm->nq;
+    Real* E;
+    RCF_TRY(workspace(ctx, WS_FM_CELL, sizeof(Real) * 4 * size_t(m->ncells) * np * np * np * nvec,
+                      reinterpret_cast<void**>(&E)));
+    const int S4 = std::max(nq * nq * nq, np * np * np);
+    const size_t smem = 2 * size_t(S4) * sizeof(R4<Real>);
+    if (smem > 48 * 1024)
+      RCF_CUDA(ctx, cudaFuncSetAttribute(fm_cell_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    fm_cell_kernel<Real><<<dim3(unsigned(m->ncells), nvec), 128, smem, ctx->stream>>>(
+        m->p, nq, m->n[0], m->n[1], m->n[2], fm_b1<Real>(fm), fm_vq<Real>(fm), u, ldu, E, S4);
+    RCF_CHECK_LAUNCH(ctx);
+    fm_gather_kernel<Real><<<dim3(unsigned((m->nnodes + 255) / 256), nvec), 256, 0, ctx->stream>>>(
+        m->p, m->n[0], m->n[1], m->n[2], m->ncells, E, T, ld);
+    RCF_CHECK_LAUNCH(ctx);
+  }
+  // spin-orbit projectors: the columns int N_I beta are stored as beta' = column / D_I, so the
+  // lumped operator's kernels with the D weights apply them
+  if (op->proj.natoms > 0) {
+    const size_t bytes = sizeof(Real) * 24 * size_t(op->proj.natoms) * nvec;
+    Real *Cc, *C2;
+    RCF_TRY(workspace(ctx, WS_NLC, bytes, reinterpret_cast<void**>(&Cc)));
+    RCF_TRY(workspace(ctx, WS_NLC2, bytes, reinterpret_cast<void**>(&C2)));
+    RCF_TRY((launch_nl_project<Real, Real>(ctx, op, u, ldu, nvec, 1, Cc)));
+    RCF_TRY(launch_nl_delta<Real>(ctx, op, Cc, nvec, Real(1), C2));
+    RCF_TRY((launch_nl_addback<Real, Real>(ctx, op, C2, nvec, 1, T, ld)));
+  }
+  return RCF_OK;
+}
+
+}  // namespace
+
+template <typename Real>
+int mass_apply_fm(rcf_ctx* ctx, const rcf_op* op, const Real* X, int64_t ldx, int nvec, Real* Y, int64_t ldy) {
+  const int64_t ld = 2 * op->mesh->nnodes;
+  Real *t1, *s1;
+  RCF_TRY(ws_block<Real>(ctx, WS_FM_T1, op, nvec, &t1));
+  RCF_TRY(ws_block<Real>(ctx, WS_FM_S1, op, nvec, &s1));
+  RCF_TRY(pass<Real>(ctx, op, 0, table<Real>(op, 1, 0), nullptr, nullptr, nullptr, X, nullptr, ldx, t1, nullptr,
+                     ld, nvec));
+  RCF_TRY(pass<Real>(ctx, op, 1, table<Real>(op, 1, 1), nullptr, nullptr, nullptr, t1, nullptr, ld, s1, nullptr,
+                     ld, nvec));
+  RCF_TRY(pass<Real>(ctx, op, 2, table<Real>(op, 1, 2), nullptr, nullptr, nullptr, s1, nullptr, ld, Y, nullptr,
+                     ldy, nvec));
+  return RCF_OK;
+}
+
+template <typename Real>
+int apply_full_fm(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real, Real>& a) {
+  const int nvec = a.nvec;
+  if (nvec == 0) return RCF_OK;
+  const int64_t ld = 2 * op->mesh->nnodes;
+  const Real* u = a.in;
+  int64_t ldu = a.ld_in;
+  if (form == RCF_FORM_H_DINV) {   // u = D^-1 in
+    Real* U;
+    RCF_TRY(ws_block<Real>(ctx, WS_FM_U, op, nvec, &U));
+    RCF_TRY(combine<Real>(ctx, op, 4, nvec, Real(0), nullptr, 0, nullptr, 0, Real(0), a.in, a.ld_in, Real(0),
+                          nullptr, 0, nullptr, nullptr, 0, U, ld));
+    u = U;
+    ldu = ld;
+  }
+  Real* T;
+  RCF_TRY(ws_block<Real>(ctx, WS_FM_T, op, nvec, &T));
+  RCF_TRY(hamiltonian_fm<Real>(ctx, op, u, ldu, nvec, T));
+  if (form == RCF_FORM_H) {
+    // out = A T + M (B in + C prev + g rv)
+    Real *W, *MW;
+    RCF_TRY(ws_block<Real>(ctx, WS_FM_W, op, nvec, &W));
+    RCF_TRY(ws_block<Real>(ctx, WS_FM_U, op, nvec, &MW));
+    RCF_TRY(combine<Real>(ctx, op, 0, nvec, Real(0), nullptr, 0, nullptr, 0, a.B, a.in, a.ld_in, a.C, a.prev,
+                          a.ld_prev, a.g, a.rv, a.ld_rv, W, ld));
+    RCF_TRY(mass_apply_fm<Real>(ctx, op, W, ld, nvec, MW, ld));
+    return combine<Real>(ctx, op, 1, nvec, a.A, T, ld, MW, ld, Real(0), nullptr, 0, Real(0), nullptr, 0, nullptr,
+                         nullptr, 0, a.out, a.ld_out);
+  }
+  return combine<Real>(ctx, op, form == RCF_FORM_DINV_H ? 2 : 3, nvec, a.A, T, ld, nullptr, 0, a.B, a.in, a.ld_in,
+                       a.C, a.prev, a.ld_prev, a.g, a.rv, a.ld_rv, a.out, a.ld_out);
+}
+
+template int apply_full_fm<double>(rcf_ctx*, const rcf_op*, int, const StepArgs<double, double>&);
+template int apply_full_fm<float>(rcf_ctx*, const rcf_op*, int, const StepArgs<float, float>&);
+template int mass_apply_fm<double>(rcf_ctx*, const rcf_op*, const double*, int64_t, int, double*, int64_t);
+template int mass_apply_fm<float>(rcf_ctx*, const rcf_op*, const float*, int64_t, int, float*, int64_t);
+
+void free_fm(FullMass* fm) {
+  if (!fm) return;
+  for (void* p : {static_cast<void*>(fm->d_tab64), static_cast<void*>(fm->d_tab32), static_cast<void*>(fm->d_B1_64),
+                  static_cast<void*>(fm->d_B1_32), static_cast<void*>(fm->d_vq64), static_cast<void*>(fm->d_vq32)})
+    if (p) cudaFree(p);
+  delete fm;
+}
+
+}  // namespace rcf
+
+namespace rcf {
+
+// V, B at the Gauss points ([ncells][nq^3], [3][ncells][nq^3], host) -> w_q |J| (V, Bx, By, Bz)
+int fm_set_potential(rcf_ctx* ctx, rcf_op* op, const double* V, const double* B) {
+  FullMass* fm = op->fm;
+  const rcf_mesh* m = op->mesh;
+  const int nq = fm->nq, nq3 = nq * nq * nq;
+  const size_t npt = size_t(m->ncells) * nq3;
+  std::vector<double> vq(4 * npt, 0.0);
+  for (int64_t e = 0; e < m->ncells; ++e)
+    for (int q = 0; q < nq3; ++q) {
+      const double wq = fm->gw[q % nq] * fm->gw[(q / nq) % nq] * fm->gw[q / (nq * nq)] * m->detJ;
+      const size_t i = size_t(e) * nq3 + q;
+      vq[4 * i] = V ? wq * V[i] : 0.0;
+      for (int d = 0; d < 3; ++d) vq[4 * i + 1 + d] = B ? wq * B[d * npt + i] : 0.0;
+    }
+  for (double x : vq)
+    if (!std::isfinite(x)) return fail(ctx, RCF_EINVAL, "potential contains a non-finite value");
+  std::vector<float> v32(vq.begin(), vq.end());
+  RCF_TRY(upload_vec(ctx, &fm->d_vq64, vq));
+  RCF_TRY(upload_vec(ctx, &fm->d_vq32, v32));
+  return RCF_OK;
+}
+
+// Projector columns int N_I beta_{j,i} by the Gauss rule, as (node, atom, beta' = column / D_I)
+// entries, nodes ascending per atom (the nodes whose column is not zero)
+int fm_projector_entries(rcf_ctx* ctx, const rcf_op* op, int natoms, const double* pos, const double* width,
+                         double rcut_factor, std::vector<int>* node, std::vector<int>* atom,
+                         std::vector<double>* beta, std::vector<int>* offsets) {
+  const FullMass* fm = op->fm;
+  const rcf_mesh* m = op->mesh;
+  const int p = m->p, np = p + 1, nq = fm->nq, nq3 = nq * nq * nq, nl = np * np * np;
+  const double pi = 3.14159265358979323846;
+  offsets->assign(natoms + 1, 0);
+  std::vector<double> col;
+  for (int a = 0; a < natoms; ++a) {
+    double Nj[2], s2[2], rj2[2];
+    for (int j = 0; j < 2; ++j) {
+      const double s = width[2 * a + j];
+      if (!(s > 0.0)) return fail(ctx, RCF_EINVAL, "projector width must be > 0");
+      Nj[j] = std::sqrt(2.0 / (std::pow(pi, 1.5) * std::pow(s, 5)));
+      s2[j] = s * s;
+      rj2[j] = (rcut_factor * s) * (rcut_factor * s);
+    }
+    col.assign(size_t(m->nnodes) * 6, 0.0);
+    std::vector<char> touched(m->nnodes, 0);
+    for (int64_t e = 0; e < m->ncells; ++e) {
+      const int ex = int(e % m->n[0]), ey = int((e / m->n[0]) % m->n[1]), ez = int(e / (int64_t(m->n[0]) * m->n[1]));
+      const int ec[3] = {ex, ey, ez};
+      for (int q = 0; q < nq3; ++q) {
+        const int ql[3] = {q % nq, (q / nq) % nq, q / (nq * nq)};
+        double d[3], r2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          const double xk = ec[k] * m->h[k] + (fm->gx[ql[k]] + 1.0) * m->h[k] / 2.0;
+          double dd = xk - pos[3 * a + k];
+          dd -= m->L[k] * std::nearbyint(dd / m->L[k]);
+          d[k] = dd;
+          r2 += dd * dd;
+        }
+        double g[2];
+        bool any = false;
+        for (int j = 0; j < 2; ++j) {
+          g[j] = r2 < rj2[j] ? Nj[j] * std::exp(-r2 / (2.0 * s2[j])) : 0.0;
+          any = any || g[j] != 0.0;
+        }
+        if (!any) continue;
+        const double wq = fm->gw[ql[0]] * fm->gw[ql[1]] * fm->gw[ql[2]] * m->detJ;
+        for (int l = 0; l < nl; ++l) {
+          const int la = l % np, lb = (l / np) % np, lc = l / (np * np);
+          const double N = fm->B1[ql[0] * np + la] * fm->B1[ql[1] * np + lb] * fm->B1[ql[2] * np + lc];
+          const int64_t I = (ex * p + la) % m->G[0] +
+                            int64_t(m->G[0]) * ((ey * p + lb) % m->G[1] + int64_t(m->G[1]) * ((ez * p + lc) % m->G[2]));
+          touched[I] = 1;
+          for (int j = 0; j < 2; ++j)
+            for (int i = 0; i < 3; ++i) col[size_t(I) * 6 + 3 * j + i] += wq * N * g[j] * d[i];
+        }
+      }
+    }
+    for (int64_t I = 0; I < m->nnodes; ++I) {
+      if (!touched[I]) continue;
+      bool nz = false;
+      for (int c = 0; c < 6; ++c) nz = nz || col[size_t(I) * 6 + c] != 0.0;
+      if (!nz) continue;
+      node->push_back(int(I));
+      atom->push_back(a);
+      for (int c = 0; c < 6; ++c) beta->push_back(col[size_t(I) * 6 + c] / m->mass[I]);
+    }
+    (*offsets)[a + 1] = int(node->size());
+  }
+  return RCF_OK;
+}
+
+}  // namespace rcf
+
+using namespace rcf;
+
+extern "C" int rcf_op_set_gauss(rcf_op* op, int nq) {
+  if (!op) return RCF_EINVAL;
+  rcf_ctx* ctx = op->ctx;
+  const rcf_mesh* m = op->mesh;
+  const int p = m->p, np = p + 1;
+  if (nq < p + 1 || nq > 12) return fail(ctx, RCF_EINVAL, "nq must be in [p + 1, 12] (got %d for p = %d)", nq, p);
+  RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  FullMass* fm = new FullMass();
+  fm->nq = nq;
+  gauss_legendre(nq, &fm->gx, &fm->gw);
+  fm->B1.resize(size_t(nq) * np);
+  for (int q = 0; q < nq; ++q)
+    for (int a = 0; a < np; ++a) fm->B1[size_t(q) * np + a] = lagrange(m->xi, a, fm->gx[q]);
+  // element matrices on [-1, 1]: stiffness (exact with the GLL rule), mass (Gauss rule)
+  std::vector<double> M1(size_t(np) * np, 0.0);
+  for (int a = 0; a < np; ++a)
+    for (int b = 0; b < np; ++b)
+      for (int q = 0; q < nq; ++q) M1[size_t(a) * np + b] += fm->gw[q] * fm->B1[size_t(q) * np + a] * fm->B1[size_t(q) * np + b];
+  const int W = 2 * p + 1;
+  fm->tab.assign(size_t(2) * 3 * p * W, 0.0);
+  for (int kind = 0; kind < 2; ++kind)
+    for (int d = 0; d < 3; ++d) {
+      const double sc = kind == 0 ? 0.5 * 2.0 / m->h[d] : m->h[d] / 2.0;
+      const double* E = kind == 0 ? m->K1.data() : M1.data();
+      double* T = fm->tab.data() + (size_t(kind) * 3 + d) * p * W;
+      for (int a = 0; a < p; ++a)
+        for (int q = 0; q <= p; ++q) {
+          if (a == 0) {
+            T[q] += sc * E[size_t(p) * np + q];            // element on the left: local p, offset q - p
+            T[p + q] += sc * E[q];                         // element on the right: local 0, offset q
+          } else {
+            T[size_t(a) * W + q - a + p] += sc * E[size_t(a) * np + q];
+          }
+        }
+    }
+  std::vector<float> t32(fm->tab.begin(), fm->tab.end()), b32(fm->B1.begin(), fm->B1.end());
+  int st = upload_vec(ctx, &fm->d_tab64, fm->tab);
+  if (st == RCF_OK) st = upload_vec(ctx, &fm->d_tab32, t32);
+  if (st == RCF_OK) st = upload_vec(ctx, &fm->d_B1_64, fm->B1);
+  if (st == RCF_OK) st = upload_vec(ctx, &fm->d_B1_32, b32);
+  if (st != RCF_OK) {
+    free_fm(fm);
+    return st;
+  }
+  free_fm(op->fm);
+  op->fm = fm;
+  return RCF_OK;
+}
+
+extern "C" int rcf_op_gauss_points(const rcf_op* op, double* out) {
+  if (!op || !out) return RCF_EINVAL;
+  if (!op->fm) return fail(op->ctx, RCF_EINVAL, "the operator has no Gauss quadrature (rcf_op_set_gauss)");
+  const rcf_mesh* m = op->mesh;
+  const int nq = op->fm->nq, nq3 = nq * nq * nq;
+  for (int64_t e = 0; e < m->ncells; ++e) {
+    const int ec[3] = {int(e % m->n[0]), int((e / m->n[0]) % m->n[1]), int(e / (int64_t(m->n[0]) * m->n[1]))};
+    for (int q = 0; q < nq3; ++q) {
+      const int ql[3] = {q % nq, (q / nq) % nq, q / (nq * nq)};
+      for (int d = 0; d < 3; ++d)
+        out[(size_t(e) * nq3 + q) * 3 + d] = ec[d] * m->h[d] + (op->fm->gx[ql[d]] + 1.0) * m->h[d] / 2.0;
+    }
+  }
+  return RCF_OK;
+}
+
+extern "C" int rcf_mass_apply(rcf_ctx* ctx, const rcf_op* op, const void* X, int64_t ldx, int nvec, void* Y,
+                              int64_t ldy, int prec) {
+  if (!ctx || !op) return RCF_EINVAL;
+  if (prec != RCF_FP64 && prec != RCF_FP32) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  const int64_t rows = 2 * op->mesh->nnodes;
+  const size_t real = prec == RCF_FP64 ? 8 : 4;
+  if (nvec < 0) return fail(ctx, RCF_EINVAL, "nvec < 0");
+  if (nvec == 0) return RCF_OK;
+  if (!X || !Y || ldx < rows || ldy < rows || (ldx & 1) || (ldy & 1) ||
+      (reinterpret_cast<uintptr_t>(X) % (4 * real)) || (reinterpret_cast<uintptr_t>(Y) % (4 * real)))
+    return fail(ctx, RCF_EINVAL, "X or Y: NULL, misaligned, or leading dimension below 2M / odd");
+  const char* x0 = static_cast<const char*>(X);
+  const char* y0 = static_cast<const char*>(Y);
+  if (x0 < y0 + size_t(ldy) * nvec * 2 * real && y0 < x0 + size_t(ldx) * nvec * 2 * real)
+    return fail(ctx, RCF_EINVAL, "Y overlaps X");
+  if (op->fm) {
+    if (prec == RCF_FP64)
+      return mass_apply_fm<double>(ctx, op, static_cast<const double*>(X), ldx, nvec, static_cast<double*>(Y), ldy);
+    return mass_apply_fm<float>(ctx, op, static_cast<const float*>(X), ldx, nvec, static_cast<float*>(Y), ldy);
+  }
+  if (prec == RCF_FP64)   // the diagonal mass of the lumped operator
+    return launch_scale_mass(ctx, op->mesh, static_cast<const double*>(X), ldx, nvec, 1.0, static_cast<double*>(Y), ldy);
+  return fail(ctx, RCF_ENOTSUP, "the diagonal mass is applied in FP64 only");
+}

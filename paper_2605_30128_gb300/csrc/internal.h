@@ -94,9 +94,29 @@ struct ProjAtoms {
   float* d_betadf = nullptr;     // [nent][6][2] beta (hi, lo)
 };
 
+// Full consistent mass with Gauss-Legendre quadrature (Section III-A; Section III-B-2): the
+// operator's integrals use nq Gauss points per direction; D (the lumped GLL mass) stays the
+// filter's diagonal in place of M^-1.
+struct FullMass {
+  int nq = 0;
+  std::vector<double> gx, gw;     // Gauss nodes and weights on [-1, 1]
+  std::vector<double> B1;         // [nq][np] Lagrange basis l_a at the Gauss nodes
+  // 1D assembled rows per direction d and local position a (0 = element vertex), offsets
+  // -p .. p: K = 1/2 (2 / h_d) K1 (stiffness), M = (h_d / 2) M1 (consistent mass);
+  // layout [2 (K, M)][3][p][2p + 1]
+  std::vector<double> tab;
+  double* d_tab64 = nullptr;
+  float* d_tab32 = nullptr;
+  double* d_B1_64 = nullptr;      // [nq][np]
+  float* d_B1_32 = nullptr;
+  double* d_vq64 = nullptr;       // [ncells][nq^3][4]: w_q |J| (V, Bx, By, Bz)
+  float* d_vq32 = nullptr;
+};
+
 struct rcf_op {
   rcf_ctx* ctx = nullptr;
   const rcf_mesh* mesh = nullptr;
+  FullMass* fm = nullptr;      // non-null: full consistent mass, Gauss quadrature
   double* d_pot64 = nullptr;   // [nnodes][4] (pv, pbx, pby, pbz) / M_I
   float* d_pot32 = nullptr;
   float* d_potdf = nullptr;    // [nnodes][8] (pv+bz, pv-bz, bx, by) / M_I: hi[4], lo[4]
@@ -134,7 +154,8 @@ int workspace(rcf_ctx* ctx, int slot, size_t bytes, void** out);
 enum WsSlot {
   WS_R64 = 0, WS_R32, WS_ZA, WS_ZB, WS_COEF, WS_NLC, WS_NLC2, WS_LANCZOS, WS_RR_W, WS_RR_S,
   WS_RR_T, WS_RR_INFO, WS_RR_WORK, WS_GRAD, WS_CKPT, WS_ADJ_A, WS_ADJ_B, WS_ADJ_C, WS_ADJ_U,
-  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HY0, WS_R16, WS_SCALE, WS_GEMM_PART, WS_TC_A, WS_TC_B, WS_TC_E, WS_TC_C, WS_TC_Q, WS_PCG, WS_COUNT
+  WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HY0, WS_R16, WS_SCALE, WS_GEMM_PART, WS_TC_A, WS_TC_B, WS_TC_E, WS_TC_C, WS_TC_Q, WS_PCG, WS_FM_U, WS_FM_T, WS_FM_T1, WS_FM_T2,
+  WS_FM_S1, WS_FM_S2, WS_FM_CELL, WS_FM_W, WS_COUNT
 };
 
 // ---------------------------------------------------------------------------
@@ -269,6 +290,21 @@ void channel_projector_table(double* h /* [2][6][6] complex */);
 // dV[e][l] += |J| w_l gnode[0][I(e,l)], dB[d][e][l] += |J| w_l gnode[1+d][I(e,l)]
 int launch_grad_to_quadrature(rcf_ctx* ctx, const rcf_mesh* m, const double* gnode, double* dV,
                               double* dB);
+
+// full consistent mass (fullmass.cu): the same contract as apply_full for an operator with
+// op->fm (form H: out = A H in + M (B in + C prev + g rv), M the full mass; the other
+// forms as apply_full), and Y = M X
+template <typename Real>
+int apply_full_fm(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real, Real>& a);
+template <typename Real>
+int mass_apply_fm(rcf_ctx* ctx, const rcf_op* op, const Real* X, int64_t ldx, int nvec, Real* Y, int64_t ldy);
+void free_fm(FullMass* fm);
+// set-up of the full-mass operator (fullmass.cu): the Gauss-point potential, and the projector
+// entries (node, atom, column / D_I) with the per-atom offsets
+int fm_set_potential(rcf_ctx* ctx, rcf_op* op, const double* V, const double* B);
+int fm_projector_entries(rcf_ctx* ctx, const rcf_op* op, int natoms, const double* pos, const double* width,
+                         double rcut_factor, std::vector<int>* node, std::vector<int>* atom,
+                         std::vector<double>* beta, std::vector<int>* offsets);
 
 // the Hamiltonian-multivector product with the nonlocal part (filter.cu)
 template <typename Real, typename St = Real>

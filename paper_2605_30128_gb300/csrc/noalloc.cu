@@ -81,6 +81,7 @@ using namespace rcf;
 extern "C" int rcf_apply_noalloc(rcf_ctx* ctx, const rcf_op* op, int form, const void* X,
                                  int64_t ldx, int nvec, void* Y, int64_t ldy, int prec) {
   if (!ctx || !op) return RCF_EINVAL;
+  if (op->fm) return fail(ctx, RCF_ENOTSUP, "rcf_apply_noalloc is not available with the full consistent mass");
   if (form < 0 || form > 2) return fail(ctx, RCF_EINVAL, "unknown form %d", form);
   if (prec != RCF_FP64 && prec != RCF_FP32) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
   if (nvec < 0) return fail(ctx, RCF_EINVAL, "nvec < 0");

@@ -541,6 +541,7 @@ int launch_residual_df(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t 
                        const double* neglam_d, float* Rh, float* Rl, int64_t ldr) {
   if (nvec <= 0) return RCF_OK;
   const rcf_mesh* m = op->mesh;
+  if (op->fm) return fail(ctx, RCF_ENOTSUP, "the double-float residual is not available with the full consistent mass");
   if (!op->d_potdf) return fail(ctx, RCF_EINVAL, "potential not set");
   ResidualDFArgs args{};
   args.X = X; args.ldx = ldx;

@@ -138,6 +138,18 @@ __global__ void inverse_adjoint_kernel(const double* __restrict__ Li, int n, dou
 // S = Y^H M Y  (lower triangle), S: n x n
 int gram(rcf_ctx* ctx, const rcf_op* op, const double* Y, int64_t ldy, int n, cuDoubleComplex* S) {
   const int64_t N = 2 * op->mesh->nnodes;
+  if (op->fm) {   // the full consistent mass: S = Y^H (M Y), column chunks of M Y
+    const int cb = std::min(n, 256);
+    double* T = nullptr;
+    RCF_TRY(workspace(ctx, WS_RR_T, sizeof(double) * 2 * size_t(N) * cb, reinterpret_cast<void**>(&T)));
+    for (int c0 = 0; c0 < n; c0 += cb) {
+      const int nc = std::min(cb, n - c0);
+      RCF_TRY(mass_apply_fm<double>(ctx, op, Y + 2 * int64_t(c0) * ldy, ldy, nc, T, N));
+      RCF_TRY(inner_product(ctx, Y, ldy, n, T, N, nc, N, nullptr, reinterpret_cast<double*>(S + size_t(c0) * n), n,
+                            ctx->rr_arith, 0));
+    }
+    return RCF_OK;
+  }
   return inner_product(ctx, Y, ldy, n, Y, ldy, n, N, op->mesh->d_mass, reinterpret_cast<double*>(S), n,
                        ctx->rr_arith, 1);
 }
@@ -337,6 +349,7 @@ extern "C" int rcf_ritz_cotangent(rcf_ctx* ctx, const rcf_op* op, const double* 
                                   const double* thetabar, double* Ybar, int64_t ldb, double* dV,
                                   double* dB, double* dh) {
   if (!ctx || !op) return RCF_EINVAL;
+  if (op->fm) return fail(ctx, RCF_ENOTSUP, "the Ritz cotangent is not available with the full consistent mass");
   RCF_TRY(check_y(ctx, op, Y, ldy, nvec));
   RCF_TRY(check_y(ctx, op, X, ldx, nvec));
   RCF_TRY(check_y(ctx, op, Ybar, ldb, nvec));

@@ -34,6 +34,7 @@ EXPORTS = [
     "rcf_rayleigh_ritz_orth", "rcf_filter_host", "rcf_set_rr_arith",
     "rcf_bfp_stream_bytes", "rcf_bfp_encode", "rcf_bfp_decode", "rcf_ritz_cotangent",
     "rcf_set_wait_limit", "rcf_inner", "rcf_rotate", "rcf_laplacian", "rcf_poisson_pcg", "rcf_workspace_bytes",
+    "rcf_op_set_gauss", "rcf_op_gauss_points", "rcf_mass_apply",
 ]
 
 _lib = None
@@ -95,6 +96,9 @@ def lib() -> ctypes.CDLL:
         "rcf_set_wait_limit": (i32, [vp, i64]),
         "rcf_laplacian": (i32, [vp, vp, vp, vp]),
         "rcf_workspace_bytes": (i64, [vp]),
+        "rcf_op_set_gauss": (i32, [vp, i32]),
+        "rcf_op_gauss_points": (i32, [vp, vp]),
+        "rcf_mass_apply": (i32, [vp, vp, vp, i64, i32, vp, i64, i32]),
         "rcf_poisson_pcg": (i32, [vp, vp, vp, vp, i32, dbl, dbl, dbl, i32, vp, vp]),
         "rcf_inner": (i32, [vp, vp, i64, i32, vp, i64, i32, i64, vp, vp, i64, i32]),
         "rcf_rotate": (i32, [vp, vp, i64, i32, vp, i64, i64, vp, i64, i32]),
@@ -465,6 +469,24 @@ def _field(t, name):
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
         raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def rcf_op_set_gauss(ctx, op, nq: int) -> None:
+    """Switch op to the full consistent mass with nq Gauss points per direction."""
+    _check(ctx, lib().rcf_op_set_gauss(op, int(nq)))
+
+
+def rcf_op_gauss_points(ctx, op, ncells: int, nq: int) -> np.ndarray:
+    out = np.empty((ncells, nq ** 3, 3), dtype=np.float64)
+    _check(ctx, lib().rcf_op_gauss_points(op, _np_ptr(out)))
+    return out
+
+
+def rcf_mass_apply(ctx, op, X, Y, prec: int = RCF_FP64):
+    """Y = M X (complex tensors of shape (nvec, 2M))."""
+    px, ldx = _dev_mv(X, prec, "X")
+    py, ldy = _dev_mv(Y, prec, "Y")
+    _check(ctx, lib().rcf_mass_apply(ctx, op, px, ldx, X.shape[0], py, ldy, int(prec)))
 
 
 def rcf_workspace_bytes(ctx) -> int:
