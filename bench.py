@@ -41,6 +41,7 @@ sys.path.insert(0, ROOT)
 METRIC = "filtered DoF·vec·deg/s: mixed-prec R-ChFSI vs FP64 ChFSI at ≤1e-7 Ha eig err"
 UNIT = "DoF·vec·deg/s"
 BYTES_PER_UNIT = 32.0   # read Z_k, Z_{k-1}, R (complex64) + write Z_{k+1}
+BYTES_PER_UNIT_BFP12 = 27.0   # as above with R read from its 12-bit BFP stream (3 B per DoF)
 KERNEL_SRC = os.path.join(ROOT, "paper_2605_30128_gb300", "csrc", "stencil.cu")
 
 
@@ -294,6 +295,11 @@ def assemble_line(w, ws: int, steps: int, warmup: int, m: dict) -> dict:
         "bf16_storage": {"value": rate(vm["bf16_storage"]), "unit": UNIT, "ms_per_step": vm["bf16_storage"],
                          "precision": "as fp16_storage with bfloat16 (RCF_BF16)"},
     }
+    if "bfp12_residual" in vm:
+        line["variants"]["bfp12_residual"] = {
+            "value": rate(vm["bfp12_residual"]), "unit": UNIT, "ms_per_step": vm["bfp12_residual"],
+            "precision": "as the headline with R (FP64, rounded to FP32) kept as a 12-bit block floating-point "
+                         "stream read by every step (RCF_FP32_BFP12)"}
     k = m["kernel"]
     blk = k["blk"]
     alg = BYTES_PER_UNIT * N * blk
@@ -309,6 +315,13 @@ def assemble_line(w, ws: int, steps: int, warmup: int, m: dict) -> dict:
                                   "frac": a16 / peak, "kernel_ms": k["k16_ms"], "algorithmic_bytes": 16.0 * N * blk,
                                   "kernel": "step_kernel<float,__half,%d> (recurrence step, vectors stored as "
                                             "binary16)" % w.p}
+    if "kbfp_ms" in k:
+        ab = BYTES_PER_UNIT_BFP12 * N * blk
+        abfp = ab / (k["kbfp_ms"] * 1e-3) / 1e9
+        line["roofline_bfp12_step"] = {"bound": "hbm", "achieved": abfp, "peak": peak, "unit": "GB/s",
+                                       "frac": abfp / peak, "kernel_ms": k["kbfp_ms"], "algorithmic_bytes": ab,
+                                       "kernel": "step_kernel<float,%d> reading R from a 12-bit BFP stream "
+                                                 "(27 B per unit)" % w.p}
     r = m["residual"]
     line["residual"] = {"fp64_ms": r["fp64_ms"], "double_float_ms": r["df_ms"], "vectors": blk,
                         "note": "R = H X - M X Lambda of one block, spin-orbit terms included"}
@@ -504,7 +517,8 @@ def run_ours(args):
 
     m["variants_ms"] = {"df_residual": time_variant(R.RCF_FP32_DF),
                         "fp16_storage": time_variant(R.RCF_FP16),
-                        "bf16_storage": time_variant(R.RCF_BF16)}
+                        "bf16_storage": time_variant(R.RCF_BF16),
+                        "bfp12_residual": time_variant(R.RCF_FP32_BFP12)}
 
     # ---- dominant kernel: one FP32 recurrence step on a block, timed alone ----
     blk = min(w.block, nvec)
@@ -526,8 +540,16 @@ def run_ours(args):
                                    0.1, -0.5, -1.0, g, zm16)
     timed(st16, 3)
     kern["k16_ms"] = timed(st16, 10)
-    m["kernel"] = kern
     del zk16, zm16, rr16
+    # the FP32 step reading R from its 12-bit BFP stream (27 B per unit)
+    rs = torch.empty((R.rcf_bfp_stream_bytes(4 * (N // 2) * blk, 12),), dtype=torch.uint8, device=dev)
+    R.rcf_bfp_encode(ctx, torch.view_as_real(Rr).reshape(-1), 12, rs)
+    stb = lambda: R.rcf_cheb_step(ctx, op1, R.RCF_FORM_H_DINV, R.RCF_FP32_BFP12, Zk, Zm, rs,
+                                  0.1, -0.5, -1.0, g, Zm)
+    timed(stb, 3)
+    kern["kbfp_ms"] = timed(stb, 10)
+    del rs
+    m["kernel"] = kern
     R.rcf_op_destroy(op1)
     del Zk, Zm, Rr
     # the residual of one block: native FP64 (the headline path) and double-float

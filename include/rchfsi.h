@@ -57,7 +57,9 @@ typedef enum {
  * sums: about 2^-46 relative accuracy, against 2^-52 for FP64) instead of FP64,
  * because this GPU runs FP64 at a small fraction of its FP32 rate.  The paper
  * keeps R in FP64 (Section III-C); this variant is the library's. */
-typedef enum { RCF_FP64 = 0, RCF_FP32 = 1, RCF_FP32_DF = 2, RCF_FP16 = 3, RCF_BF16 = 4 } rcf_precision;
+typedef enum {
+  RCF_FP64 = 0, RCF_FP32 = 1, RCF_FP32_DF = 2, RCF_FP16 = 3, RCF_BF16 = 4, RCF_FP32_BFP12 = 5
+} rcf_precision;
 /* RCF_FP16 / RCF_BF16 (R-ChFSI only; in rcf_apply and rcf_cheb_step the
  * multivectors are 16-bit complex pairs): the recurrence vectors Z_k, Z_{k-1}
  * and R are STORED as IEEE binary16 / bfloat16 pairs and the products are
@@ -70,6 +72,20 @@ typedef enum { RCF_FP64 = 0, RCF_FP32 = 1, RCF_FP32_DF = 2, RCF_FP16 = 3, RCF_BF
  * 16-bit rounding of the stored vectors as well, since that error too scales
  * with ||R||.  The paper applies 16-bit and block-floating-point formats to
  * communicated data (Section III-C-3); this variant is the library's. */
+/* RCF_FP32_BFP12 (R-ChFSI only; rcf_filter, rcf_filter_host, rcf_cheb_step):
+ * the FP32 recurrence of RCF_FP32 with the FP64 residual R, rounded to FP32,
+ * kept as a 12-bit block floating-point stream (Section III-C-3's format with
+ * n_bits = 12: one 6-byte block per node 4-tuple (re_up, im_up, re_dn, im_dn)
+ * and vector, as rcf_bfp_encode writes it).  Every use of R sees the decoded
+ * values, and the steps read their g[v] R term from the stream: 6 bytes per
+ * node and vector instead of 16, 27 instead of 32 bytes per DoF, vector and
+ * degree.  The recurrence is linear in R, so the storage rounding (2^-9 of the
+ * block's largest entry) is an error proportional to ||R||, the property of
+ * Section III-B-2 that allows the low-precision recurrence.  In rcf_cheb_step,
+ * Zk, Zkm1 and out are complex64 and R is such a stream: block v * nnodes + I
+ * holds node I of column v, 4-byte aligned, 6 nnodes nvec bytes.  The paper
+ * uses the format for communicated data; this storage use is the library's.
+ * Not available with the full mass (RCF_ENOTSUP); rejected by rcf_apply. */
 
 /* Filter form: plain ChFSI (Eq. ChFSIrecurrence) or R-ChFSI (Eq. rChFSIrecurrence). */
 typedef enum { RCF_CHFSI = 0, RCF_RCHFSI = 1 } rcf_mode;
@@ -151,7 +167,7 @@ int rcf_apply(rcf_ctx* ctx, const rcf_op* op, int form, const void* X, int64_t l
  *   out = alpha op(Zk) + beta Zk + gamma Zkm1 + g[v] R_v     (v = column)
  * Zk, Zkm1, R, out share the leading dimension ld; Zkm1, R and g (device
  * double [nvec]) may be NULL.  out may alias Zkm1 (updated in place) but not
- * Zk or R.  prec as in rcf_apply. */
+ * Zk or R.  prec as in rcf_apply, or RCF_FP32_BFP12 with R a 12-bit BFP stream. */
 int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec, const void* Zk,
                   const void* Zkm1, const void* R, int64_t ld, int nvec, double alpha, double beta,
                   double gamma, const double* g, void* out);

@@ -16,105 +16,14 @@
 // All scaling is by powers of two, split into two factors that are normal FP32
 // numbers, so every product is exact (or, when it underflows, far below 1/2, where
 // the rounded coefficient is 0 either way): the only rounding is the rint of the
-// quantisation, and decoding is exact.  The helpers are __host__ __device__ so that
-// their arithmetic can be checked on a CPU as well.
+// quantisation, and decoding is exact.  The block helpers (bfp_common.cuh) are
+// __host__ __device__ so that their arithmetic can be checked on a CPU as well.
 #include <cstring>
 
-#include "internal.h"
+#include "bfp_common.cuh"
 
 namespace rcf {
 namespace {
-
-__host__ __device__ __forceinline__ uint32_t bits_of(float x) {
-  uint32_t u;
-  memcpy(&u, &x, sizeof(u));
-  return u;
-}
-__host__ __device__ __forceinline__ float float_of(uint32_t u) {
-  float x;
-  memcpy(&x, &u, sizeof(x));
-  return x;
-}
-// 2^k for -126 <= k <= 127
-__host__ __device__ __forceinline__ float pow2i(int k) { return float_of(uint32_t(k + 127) << 23); }
-// x 2^k for |k| <= 252, as two power-of-two products (each factor a normal number)
-__host__ __device__ __forceinline__ float scale_pow2(float x, int k) {
-  const int h = k / 2;
-  return (x * pow2i(h)) * pow2i(k - h);
-}
-
-template <int V>
-__host__ __device__ __forceinline__ uint64_t bfp_encode4(const float x[4]) {
-  constexpr int QMAX = (1 << (V - 1)) - 1;
-  const float m = fmaxf(fmaxf(fabsf(x[0]), fabsf(x[1])), fmaxf(fabsf(x[2]), fabsf(x[3])));
-  if (!(m > 0.0f)) return 0;                                // all zero
-  const int f = int((bits_of(m) >> 23) & 0xFFu);            // biased FP32 exponent of the max
-  int emax = f == 0 ? -126 : f - 126;                       // 2^(emax-1) <= m < 2^emax
-  if (emax > 128) emax = 128;                               // non-finite input: unspecified code
-  const float lo = emax == 128 ? -float(QMAX) : -float(QMAX + 1);
-  uint64_t w = uint64_t(emax + 127);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    float s = rintf(scale_pow2(x[i], V - 1 - emax));        // round half to even
-    s = fminf(fmaxf(s, lo), float(QMAX));
-    const int q = int(s);
-    w |= uint64_t(uint32_t(q) & ((1u << V) - 1u)) << (8 + i * V);
-  }
-  return w;
-}
-
-template <int V>
-__host__ __device__ __forceinline__ void bfp_decode4(uint64_t w, float y[4]) {
-  const int e = int(w & 0xFFu);
-  const int k = e - 127 - V + 1;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int fld = int((w >> (8 + i * V)) & ((1u << V) - 1u));
-    const int q = fld >= (1 << (V - 1)) ? fld - (1 << V) : fld;   // restore the sign bits
-    y[i] = e == 0 ? 0.0f : scale_pow2(float(q), k);
-  }
-}
-
-// one block's bytes in the stream: 8 bytes as one word, 6 as three 2-byte words, 5 as bytes
-template <int NB>
-struct BlockIO;
-template <>
-struct BlockIO<16> {
-  static __device__ __forceinline__ void store(unsigned char* s, int64_t b, uint64_t w) {
-    reinterpret_cast<uint64_t*>(s)[b] = w;
-  }
-  static __device__ __forceinline__ uint64_t load(const unsigned char* s, int64_t b) {
-    return __ldg(reinterpret_cast<const unsigned long long*>(s) + b);
-  }
-};
-template <>
-struct BlockIO<12> {
-  static __device__ __forceinline__ void store(unsigned char* s, int64_t b, uint64_t w) {
-    uint16_t* p = reinterpret_cast<uint16_t*>(s) + 3 * b;
-    p[0] = uint16_t(w);
-    p[1] = uint16_t(w >> 16);
-    p[2] = uint16_t(w >> 32);
-  }
-  static __device__ __forceinline__ uint64_t load(const unsigned char* s, int64_t b) {
-    const unsigned short* p = reinterpret_cast<const unsigned short*>(s) + 3 * b;
-    return uint64_t(__ldg(p)) | (uint64_t(__ldg(p + 1)) << 16) | (uint64_t(__ldg(p + 2)) << 32);
-  }
-};
-template <>
-struct BlockIO<10> {
-  static __device__ __forceinline__ void store(unsigned char* s, int64_t b, uint64_t w) {
-    unsigned char* p = s + 5 * b;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) p[j] = static_cast<unsigned char>(w >> (8 * j));
-  }
-  static __device__ __forceinline__ uint64_t load(const unsigned char* s, int64_t b) {
-    const unsigned char* p = s + 5 * b;
-    uint64_t w = 0;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) w |= uint64_t(__ldg(p + j)) << (8 * j);
-    return w;
-  }
-};
 
 constexpr int kBfpThreads = 256;
 constexpr int kBfpUnroll = 4;   // blocks per thread per pass (independent loads in flight)
@@ -181,6 +90,23 @@ __global__ void __launch_bounds__(kBfpThreads) bfp_decode_kernel(const unsigned 
   }
 }
 
+// 12-bit storage of a residual block (the FP32 recurrence with R kept as a BFP stream):
+// every block of x is encoded into s and x is overwritten by the decoded values, so
+// that the uses of R that read x and those that read s see the same numbers.  x is
+// 16-byte aligned and n a multiple of 4 (whole node 4-tuples).
+__global__ void __launch_bounds__(kBfpThreads) bfp12_round_trip_kernel(float* __restrict__ x, int64_t nblk,
+                                                                         unsigned char* __restrict__ s) {
+  const int64_t S = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; b < nblk; b += S) {
+    const float4 t = reinterpret_cast<const float4*>(x)[b];
+    float v[4] = {t.x, t.y, t.z, t.w};
+    const uint64_t w = bfp_encode4<10>(v);
+    BlockIO<12>::store(s, b, w);
+    bfp_decode4<10>(w, v);
+    reinterpret_cast<float4*>(x)[b] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
 int bfp_bytes_per_block(int nbits) {
   switch (nbits) {
     case 16: return 8;
@@ -219,6 +145,16 @@ int check_bfp_args(rcf_ctx* ctx, const void* vals, int64_t n, int nbits, const v
 }
 
 }  // namespace
+}  // namespace rcf
+
+namespace rcf {
+int launch_bfp12_round_trip(rcf_ctx* ctx, float* x, int64_t n, unsigned char* s) {
+  if (n <= 0) return RCF_OK;
+  const int64_t nblk = n / 4;
+  bfp12_round_trip_kernel<<<bfp_grid(nblk), kBfpThreads, 0, ctx->stream>>>(x, nblk, s);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
 }  // namespace rcf
 
 using namespace rcf;

@@ -224,22 +224,30 @@ int residual_impl(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, 
 
 // One R-ChFSI step (Eq. rChFSIrecurrence) for k >= 1:
 //   out = a_k H D^{-1} (zs Zk) - a_k c (zs Zk) + cp * Zkm1 + g[v] R
+// Rbfp (FP32): the g[v] R term reads R from its 12-bit BFP stream instead of R.
 template <typename Real, typename St = Real>
 int rchfsi_step(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int k, const St* Zk, double zs,
                 const St* Zkm1, double cp, const St* R, const double* g, St* out, int64_t ld,
-                int nvec) {
+                int nvec, const unsigned char* Rbfp = nullptr) {
   const double ak = 2.0 * ch.sigma[k + 1] / ch.e;
   StepArgs<Real, St> a = step_args<Real, St>(Zk, ld, out, ld, nvec, Real(ak * zs), Real(-ak * ch.c * zs));
   if (Zkm1) { a.prev = Zkm1; a.ld_prev = ld; a.C = Real(cp); }
-  a.rv = R; a.ld_rv = ld; a.g = g;
+  if (Rbfp) a.rv_bfp = Rbfp;
+  else { a.rv = R; a.ld_rv = ld; }
+  a.g = g;
   return apply_full<Real, St>(ctx, op, RCF_FORM_H_DINV, a);
 }
 
 // df: the residual in double-float arithmetic, written straight to its FP32 rounding
 // (FP32 recurrence, q >= 2); otherwise in FP64 and rounded by a separate pass.
+// bfp (FP32, q >= 2): R stored as a 12-bit BFP stream (Section III-C-3's block format, one
+// block per node 4-tuple): its FP32 rounding is encoded once and replaced by the decoded
+// values, and every step reads its g[v] R term from the stream (6 bytes per node and vector
+// instead of 16).  The recurrence is linear in R, so the storage rounding of R enters the
+// result as R-ChFSI applied to that rounding: an error proportional to ||R||.
 template <typename Real>
 int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
-                 int nvec, const double* lam_h, double* Y, int64_t ldy, bool df = false) {
+                 int nvec, const double* lam_h, double* Y, int64_t ldy, bool df = false, bool bfp = false) {
   const rcf_mesh* m = op->mesh;
   const int64_t rows = 2 * m->nnodes;
   const int64_t ld = rows;   // internal buffers: ld = 2M
@@ -269,6 +277,7 @@ int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const do
     RCF_TRY(launch_recover<double>(ctx, m, R64, ld, s, X, ldx, lamq_d, nvec, Y, ldy));
   } else {
     const Real* R = nullptr;
+    unsigned char* Rbfp = nullptr;
     if (sizeof(Real) == sizeof(double)) {
       R = reinterpret_cast<const Real*>(R64);
     } else {
@@ -276,13 +285,18 @@ int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const do
       RCF_TRY(workspace(ctx, WS_R32, sizeof(float) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R32)));
       if (df) RCF_TRY(launch_residual_df(ctx, op, X, ldx, nvec, tab_d, R32, nullptr, ld));
       else RCF_TRY(launch_to_c64(ctx, rows, R64, ld, nvec, R32, ld));
+      if (bfp) {
+        const int64_t nvals = 2 * ld * int64_t(nvec);
+        RCF_TRY(workspace(ctx, WS_RBFP, size_t((nvals / 4) * 6 + 16), reinterpret_cast<void**>(&Rbfp)));
+        RCF_TRY(launch_bfp12_round_trip(ctx, R32, nvals, Rbfp));
+      }
       R = reinterpret_cast<const Real*>(R32);
     }
     Real *ZA = nullptr, *ZB = nullptr;
     RCF_TRY(workspace(ctx, WS_ZA, sizeof(Real) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&ZA)));
     RCF_TRY(workspace(ctx, WS_ZB, sizeof(Real) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&ZB)));
     // k = 1: Z_2 = a_1 H D^-1 (s R) - a_1 c s R + a_1 Lambda_1 R   (Z_0 = 0)
-    RCF_TRY((rchfsi_step<Real, Real>(ctx, op, ch, 1, R, s, nullptr, 0.0, R, tab_d + nvec, ZA, ld, nvec)));
+    RCF_TRY((rchfsi_step<Real, Real>(ctx, op, ch, 1, R, s, nullptr, 0.0, R, tab_d + nvec, ZA, ld, nvec, Rbfp)));
     // Z_1 = s R is never materialised: it is R with the scale folded into the coefficients.
     const Real* Zkm1 = R;
     double zps = s;
@@ -291,7 +305,7 @@ int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const do
       const double bk = ch.sigma[k] * ch.sigma[k + 1];
       Real* out = (Zkm1 == R) ? ZB : const_cast<Real*>(Zkm1);   // in place over Z_{k-1}
       RCF_TRY((rchfsi_step<Real, Real>(ctx, op, ch, k, Zk, 1.0, Zkm1, -bk * zps, R,
-                                       tab_d + size_t(k) * nvec, out, ld, nvec)));
+                                       tab_d + size_t(k) * nvec, out, ld, nvec, Rbfp)));
       Zkm1 = Zk;
       zps = 1.0;
       Zk = out;
@@ -443,6 +457,9 @@ int filter_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, int mode
       case RCF_FP32_DF: return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, true);
       case RCF_FP16: return rchfsi_block16<__half>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy);
       case RCF_BF16: return rchfsi_block16<__nv_bfloat16>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy);
+      case RCF_FP32_BFP12:
+        if (op->fm) return fail(ctx, RCF_ENOTSUP, "BFP storage of R is not available with the full mass");
+        return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, false, true);
       default: return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
     }
   }
@@ -453,7 +470,7 @@ int filter_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, int mode
 // precision and mode of rcf_filter / rcf_filter_host
 int check_filter_mode(rcf_ctx* ctx, int mode, int prec) {
   if (mode != RCF_CHFSI && mode != RCF_RCHFSI) return fail(ctx, RCF_EINVAL, "unknown mode %d", mode);
-  if (prec < RCF_FP64 || prec > RCF_BF16) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
+  if (prec < RCF_FP64 || prec > RCF_FP32_BFP12) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
   if (prec >= RCF_FP32_DF && mode != RCF_RCHFSI)
     return fail(ctx, RCF_EINVAL, "precision %d applies to R-ChFSI only (it reshapes the residual)", prec);
   return RCF_OK;
@@ -476,6 +493,7 @@ extern "C" int rcf_apply(rcf_ctx* ctx, const rcf_op* op, int form, const void* X
                          int nvec, void* Y, int64_t ldy, int prec) {
   if (!ctx || !op) return RCF_EINVAL;
   if (form < 0 || form > 2) return fail(ctx, RCF_EINVAL, "unknown form %d", form);
+  if (prec == RCF_FP32_BFP12) return fail(ctx, RCF_EINVAL, "RCF_FP32_BFP12 applies to rcf_filter and rcf_cheb_step");
   const size_t real = real_bytes(prec);
   if (real == 0) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
   RCF_TRY(check_block(ctx, op, X, ldx, nvec, real, "X"));
@@ -502,14 +520,21 @@ extern "C" int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec,
                              double beta, double gamma, const double* g, void* out) {
   if (!ctx || !op) return RCF_EINVAL;
   if (form < 0 || form > 2) return fail(ctx, RCF_EINVAL, "unknown form %d", form);
-  const size_t real = real_bytes(prec);
+  const bool bfp = prec == RCF_FP32_BFP12;   // Zk, Zkm1, out complex64; R a 12-bit BFP stream
+  const size_t real = bfp ? 4 : real_bytes(prec);
   if (real == 0) return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
   RCF_TRY(check_block(ctx, op, Zk, ld, nvec, real, "Zk"));
   RCF_TRY(check_block(ctx, op, out, ld, nvec, real, "out"));
   if (Zkm1) RCF_TRY(check_block(ctx, op, Zkm1, ld, nvec, real, "Zkm1"));
-  if (R) RCF_TRY(check_block(ctx, op, R, ld, nvec, real, "R"));
-  if (overlaps(Zk, ld, out, ld, nvec, 2 * real) || overlaps(R, ld, out, ld, nvec, 2 * real))
-    return fail(ctx, RCF_EINVAL, "out overlaps Zk or R");
+  const int64_t nn = op->mesh->nnodes;
+  if (R && bfp) {
+    if (!aligned(R, 4)) return fail(ctx, RCF_EINVAL, "R: the BFP stream must be 4-byte aligned");
+    if (op->fm) return fail(ctx, RCF_ENOTSUP, "BFP storage of R is not available with the full mass");
+  } else if (R) {
+    RCF_TRY(check_block(ctx, op, R, ld, nvec, real, "R"));
+  }
+  const bool r_over = bfp ? overlaps(R, nn, 6, out, ld, 2 * real, nvec) : overlaps(R, ld, out, ld, nvec, 2 * real);
+  if (overlaps(Zk, ld, out, ld, nvec, 2 * real) || r_over) return fail(ctx, RCF_EINVAL, "out overlaps Zk or R");
   if (Zkm1 && Zkm1 != out && overlaps(Zkm1, ld, out, ld, nvec, 2 * real))
     return fail(ctx, RCF_EINVAL, "out partly overlaps Zkm1");
   if (R && !g) return fail(ctx, RCF_EINVAL, "R given without g");
@@ -520,12 +545,13 @@ extern "C" int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec,
     StepArgs<Real, St> a = step_args<Real, St>(static_cast<const St*>(Zk), ld, static_cast<St*>(out), ld, nvec,
                                                Real(alpha), Real(beta));
     if (Zkm1) { a.prev = static_cast<const St*>(Zkm1); a.ld_prev = ld; a.C = Real(gamma); }
-    if (R) { a.rv = static_cast<const St*>(R); a.ld_rv = ld; a.g = g; }
+    if (R && bfp) { a.rv_bfp = static_cast<const unsigned char*>(R); a.g = g; }
+    else if (R) { a.rv = static_cast<const St*>(R); a.ld_rv = ld; a.g = g; }
     return apply_full<Real, St>(ctx, op, form, a);
   };
   switch (prec) {
     case RCF_FP64: return run(double{});
-    case RCF_FP32: return run(float{});
+    case RCF_FP32: case RCF_FP32_BFP12: return run(float{});
     case RCF_FP16: return run(__half{});
     default: return run(__nv_bfloat16{});
   }

@@ -399,6 +399,7 @@ template <typename Real>
 int apply_full_fm(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real, Real>& a) {
   const int nvec = a.nvec;
   if (nvec == 0) return RCF_OK;
+  if (a.rv_bfp) return fail(ctx, RCF_ENOTSUP, "BFP storage of R is not available with the full mass");
   const int64_t ld = 2 * op->mesh->nnodes;
   const Real* u = a.in;
   int64_t ldu = a.ld_in;

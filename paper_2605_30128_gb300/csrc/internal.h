@@ -155,7 +155,7 @@ enum WsSlot {
   WS_R64 = 0, WS_R32, WS_ZA, WS_ZB, WS_COEF, WS_NLC, WS_NLC2, WS_LANCZOS, WS_RR_W, WS_RR_S,
   WS_RR_T, WS_RR_INFO, WS_RR_WORK, WS_GRAD, WS_CKPT, WS_ADJ_A, WS_ADJ_B, WS_ADJ_C, WS_ADJ_U,
   WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HY0, WS_R16, WS_SCALE, WS_GEMM_PART, WS_TC_A, WS_TC_B, WS_TC_E, WS_TC_C, WS_TC_Q, WS_PCG, WS_FM_U, WS_FM_T, WS_FM_T1, WS_FM_T2,
-  WS_FM_S1, WS_FM_S2, WS_FM_CELL, WS_FM_W, WS_COUNT
+  WS_FM_S1, WS_FM_S2, WS_FM_CELL, WS_FM_W, WS_RBFP, WS_COUNT
 };
 
 // ---------------------------------------------------------------------------
@@ -173,6 +173,8 @@ struct StepArgs {
   const St* prev;    int64_t ld_prev;   // may be null
   const St* rv;      int64_t ld_rv;     // may be null
   const double* g;                      // [nvec] coefficients of rv (device), may be null
+  const unsigned char* rv_bfp;          // instead of rv (FP32 only): R as a 12-bit BFP stream,
+                                        // block v * nnodes + node (4-byte aligned), may be null
   St* out;           int64_t ld_out;
   Real A, B, C;
   const Real* pot;                      // [nnodes][4]
@@ -255,6 +257,9 @@ int launch_colnorm2(rcf_ctx* ctx, int64_t rows, const double* x, int64_t ldx, in
 // 16-bit storage of the recurrence: per-column largest modulus of a complex64 block (as
 // float bits; cmax pre-zeroed), the power-of-two scale above it and its reciprocal, the
 // scaled copy in the storage type, and the recovery Y = D^{-1} Z zscale[v] + X lam[v]
+// 12-bit BFP storage of n floats (n a multiple of 4, x 16-byte aligned): the stream s
+// (6 bytes per 4 values) receives their encoding and x the decoded values (bfp.cu)
+int launch_bfp12_round_trip(rcf_ctx* ctx, float* x, int64_t n, unsigned char* s);
 int launch_colmax_f32(rcf_ctx* ctx, int64_t rows, const float* x, int64_t ldx, int nvec, unsigned* cmax);
 int launch_pow2_scale(rcf_ctx* ctx, const unsigned* cmax, int n, double* scale, float* inv);
 template <typename St>

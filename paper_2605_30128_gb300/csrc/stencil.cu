@@ -24,6 +24,9 @@
 // the element's P planes are written when its closing vertex plane arrives.
 // Every input element is read from L2/HBM once per plane visit; outputs are
 // written once.
+#include <type_traits>
+
+#include "bfp_common.cuh"
 #include "internal.h"
 #include "stencil_common.cuh"
 
@@ -40,7 +43,9 @@ __host__ __device__ constexpr int stage_elems(bool own) {
 // halo (NST-1 planes ahead) instead of register prefetch one plane ahead.
 // ZB: planes consumed per block barrier (1 or 2); NST - ZB planes are in flight.
 // St: storage type of the multivectors (arithmetic in Real; a 16-bit St halves the traffic)
-template <typename Real, typename St, int P, int TX, int TY, int NST, bool OWN, int ZB>
+// RBF (FP32): the residual term reads R from a 12-bit BFP stream (a.rv_bfp, one block per
+// node 4-tuple, 6 bytes instead of 16), decoded in registers
+template <typename Real, typename St, int P, int TX, int TY, int NST, bool OWN, int ZB, bool RBF>
 __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
     step_kernel(const StepArgs<Real, St> a, const KTab<Real, P> tab, const int Gx, const int Gy,
                 const int Gz) {
@@ -55,6 +60,8 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
   using V4 = R4<Real>;
   using S4 = R4<St>;
   using CV = Cvt<Real, St>;
+  static_assert(!RBF || (std::is_same<Real, float>::value && std::is_same<St, float>::value && !OWN),
+                "BFP residual: FP32 storage, own planes through registers");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   S4* S = reinterpret_cast<S4*>(smem_raw);                        // [NST][STAGE]
   Real* ST = reinterpret_cast<Real*>(S + NST * STAGE);           // [2][P+1][P+1] x and y tables
@@ -115,13 +122,19 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
   // this thread's potential, previous iterate and residual of one plane, one plane ahead.
   // prev may alias out: each element is read here before this thread writes it.
   V4 npot = zero4<Real>(), nprev = zero4<Real>(), nrv = zero4<Real>();
+  uint32_t nrw = 0, nrh = 0;   // RBF: the raw words of R's block, decoded when consumed
+  const int64_t rblk0 = int64_t(v) * plane * Gz + col;   // RBF: block of node (col, z = 0)
   auto fetch_own = [&](int z) {
     if (!active) return;
     const int64_t I = col + int64_t(z) * plane;
     npot = ldg4(pot + I);
     if (!OWN) {
       if (prev) nprev = CV::in(ldgs(prev + I));
-      if (rv) nrv = CV::in(ldgs(rv + I));
+      if constexpr (RBF) {
+        bfp12_fetch(a.rv_bfp, rblk0 + int64_t(z) * plane, nrw, nrh);
+      } else if (rv) {
+        nrv = CV::in(ldgs(rv + I));
+      }
     }
   };
 
@@ -192,7 +205,8 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
       const V4 u = CV::in(Pl[(ly + P) * W + lx + P]);
       const V4 cpot = npot;
       const V4 cprev = OWN ? (prev ? CV::in(Pl[HALO + tid]) : zero4<Real>()) : nprev;
-      const V4 crv = OWN ? (rv ? CV::in(Pl[HALO + NT + tid]) : zero4<Real>()) : nrv;
+      V4 crv = OWN ? (rv ? CV::in(Pl[HALO + NT + tid]) : zero4<Real>()) : nrv;
+      const uint32_t crw = nrw, crh = nrh;
       if (z + 1 < Gz) fetch_own(z + 1);
       // x and y terms (tables carry the factor A)
       V4 self = zero4<Real>();
@@ -220,7 +234,13 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
         fma4(self, A, hp);
         fma4(self, B, u);
         if (prev) fma4(self, C, cprev);
-        if (rv) fma4(self, gv, crv);
+        if constexpr (RBF) {
+          float r[4];
+          bfp_decode4<10>(bfp12_join(int((rblk0 + int64_t(z) * plane) & 1), crw, crh), r);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) crv.v[i] = r[i];
+        }
+        if (RBF || rv) fma4(self, gv, crv);
       }
       if (c == 0) {
         // the vertex plane closes element ez-1 (its local node P) and opens element ez
@@ -270,12 +290,18 @@ int launch_p(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Re
   const int ntx = (m->G[0] + TX - 1) / TX, nty = (m->G[1] + TY - 1) / TY;
   const size_t stage = size_t(stage_elems<P, TX, TY>(OWN));
   const size_t smem = size_t(NST) * stage * sizeof(R4<St>) + 2 * (P + 1) * (P + 1) * sizeof(Real);
-  auto kern = step_kernel<Real, St, P, TX, TY, NST, OWN, ZB>;
-  if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-  dim3 grid(ntx * nty, a.nvec);
-  kern<<<grid, TX * TY, smem, ctx->stream>>>(a, kt, m->G[0], m->G[1], m->G[2]);
-  RCF_CHECK_LAUNCH(ctx);
-  return RCF_OK;
+  auto launch = [&](auto kern) -> int {
+    if (smem > 48 * 1024)
+      RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    dim3 grid(ntx * nty, a.nvec);
+    kern<<<grid, TX * TY, smem, ctx->stream>>>(a, kt, m->G[0], m->G[1], m->G[2]);
+    RCF_CHECK_LAUNCH(ctx);
+    return RCF_OK;
+  };
+  if constexpr (std::is_same<Real, float>::value && std::is_same<St, float>::value) {
+    if (a.rv_bfp) return launch(step_kernel<Real, St, P, TX, TY, NST, OWN, ZB, true>);
+  }
+  return launch(step_kernel<Real, St, P, TX, TY, NST, OWN, ZB, false>);
 }
 
 }  // namespace
@@ -301,8 +327,10 @@ void build_tables(const rcf_mesh* m, int kind, Tables* t) {
 template <typename Real, typename St>
 int launch_step(rcf_ctx* ctx, const rcf_mesh* m, const Tables& t, const StepArgs<Real, St>& a) {
   if (a.nvec <= 0) return RCF_OK;
+  if (a.rv_bfp && !(std::is_same<Real, float>::value && std::is_same<St, float>::value))
+    return fail(ctx, RCF_ENOTSUP, "a BFP residual stream needs FP32 storage");
   if constexpr (sizeof(Real) == 4 && sizeof(St) == 4) {
-    if (ctx->step_kernel == RCF_STEP_TMA) {
+    if (ctx->step_kernel == RCF_STEP_TMA && !a.rv_bfp) {
       bool used = false;
       RCF_TRY(launch_step_tma(ctx, m, t, a, &used));
       if (used) return RCF_OK;

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librchfsi.so")
 
 RCF_OK, RCF_EINVAL, RCF_ENOMEM, RCF_ECUDA, RCF_ENOTSPD, RCF_ETIMEOUT, RCF_ENOTSUP = range(7)
-RCF_FP64, RCF_FP32, RCF_FP32_DF, RCF_FP16, RCF_BF16 = 0, 1, 2, 3, 4
+RCF_FP64, RCF_FP32, RCF_FP32_DF, RCF_FP16, RCF_BF16, RCF_FP32_BFP12 = 0, 1, 2, 3, 4, 5
 RCF_CHFSI, RCF_RCHFSI = 0, 1
 RCF_FORM_H, RCF_FORM_DINV_H, RCF_FORM_H_DINV = 0, 1, 2
 RCF_STEP_CPASYNC, RCF_STEP_TMA = 0, 1
@@ -263,7 +263,7 @@ def _dev_mv(t, prec: int, name: str):
     import torch
     if prec == RCF_FP64:
         return _dev(t, torch.complex128, name)
-    if prec == RCF_FP32:
+    if prec in (RCF_FP32, RCF_FP32_BFP12):
         return _dev(t, torch.complex64, name)
     if prec == RCF_FP16 and t.dtype == torch.complex32:
         return _dev(t, torch.complex32, name)
@@ -413,13 +413,22 @@ def rcf_adjoint_filter(ctx, op, X, ritz, degree: int, bounds, mode: int, prec: i
 
 def rcf_cheb_step(ctx, op, form: int, prec: int, Zk, Zkm1, R, alpha: float, beta: float, gamma: float,
                   g, out):
-    """out = alpha op(Zk) + beta Zk + gamma Zkm1 + g[v] R (tensors of shape (nvec, rows))."""
+    """out = alpha op(Zk) + beta Zk + gamma Zkm1 + g[v] R (tensors of shape (nvec, rows)).
+    prec RCF_FP32_BFP12: Zk, Zkm1, out complex64 and R a uint8 CUDA tensor holding the 12-bit
+    BFP stream of the nvec columns (6 bytes per node and column, column after column)."""
+    import torch
     pz, ld = _dev_mv(Zk, prec, "Zk")
     po, ldo = _dev_mv(out, prec, "out")
     if ldo != ld:
         raise ValueError("Zk and out must share the leading dimension")
     pm = None if Zkm1 is None else _dev_mv(Zkm1, prec, "Zkm1")[0]
-    pr = None if R is None else _dev_mv(R, prec, "R")[0]
+    if R is not None and prec == RCF_FP32_BFP12:
+        need = 6 * (Zk.shape[-1] // 2) * Zk.shape[0]
+        if not (R.is_cuda and R.dtype == torch.uint8 and R.is_contiguous() and R.numel() >= need):
+            raise ValueError(f"R: a contiguous uint8 CUDA stream of at least {need} bytes is required")
+        pr = ctypes.c_void_p(R.data_ptr())
+    else:
+        pr = None if R is None else _dev_mv(R, prec, "R")[0]
     pg = None if g is None else ctypes.c_void_p(g.data_ptr())
     _check(ctx, lib().rcf_cheb_step(ctx, op, int(form), int(prec), pz, pm, pr, ld, Zk.shape[0],
                                     float(alpha), float(beta), float(gamma), pg, po))

@@ -89,6 +89,22 @@ def rchfsi_filter_bfp(Hop, X, lam, lmin, lT, lmax, q, nbits):
     return Dinv * Z + X * Lk[q][None, :]
 
 
+def rchfsi_filter_bfp_residual(Hop, X, lam, lmin, lT, lmax, q, nbits=12):
+    """R-ChFSI with R alone stored in BFP (its FP32 rounding through the format; every use of R
+    sees the decoded values) and Z_k exact (FP64 arithmetic): the reference of the library's
+    RCF_FP32_BFP12, whose remaining difference from it is the FP32 recurrence."""
+    from oracle.filters import residual
+    c, e, sigma = filter_scalars(lmin, lT, lmax, q)
+    Dinv = 1.0 / Hop.Mdiag[:, None]
+    Rt = bfp_round(residual(Hop, X, lam), nbits)
+    Lk = ritz_filter_values(np.asarray(lam, dtype=np.float64), lmin, lT, lmax, q)
+    Zp, Z = np.zeros_like(Rt), (sigma[1] / e) * Rt
+    for k in range(1, q):
+        a = 2.0 * sigma[k + 1] / e
+        Zp, Z = Z, a * Hop.apply(Dinv * Z) - a * c * Z - sigma[k] * sigma[k + 1] * Zp + a * Rt * Lk[k][None, :]
+    return Dinv * Z + X * Lk[q][None, :]
+
+
 def rayleigh_ritz_mixed_rotation(Hop, Y):
     """Rayleigh-Ritz whose subspace rotation X = Y Q is split as in Section III-C-4:
     Y Q_diag in FP64 plus Y Q_offdiag in FP32 (complex64 operands and products, rounded

@@ -24,8 +24,9 @@ def fake_measurements(extras=True):
                                                       "reasons": [], "samples": 5},
          "N": w.ndof, "nvec": w.nvec, "degree": w.degree, "l2_gb": 32.8, "peak": (6802.0, "measured"),
          "traffic": {"bytes_per_launch_full_block": 1.7e10},
-         "variants_ms": {"df_residual": 720.0, "fp16_storage": 870.0, "bf16_storage": 900.0},
-         "kernel": {"blk": 256, "k_ms": 3.5, "step_ms": 4.0, "k16_ms": 4.4},
+         "variants_ms": {"df_residual": 720.0, "fp16_storage": 870.0, "bf16_storage": 900.0,
+                         "bfp12_residual": 950.0},
+         "kernel": {"blk": 256, "k_ms": 3.5, "step_ms": 4.0, "k16_ms": 4.4, "kbfp_ms": 3.3},
          "residual": {"fp64_ms": 88.0, "df_ms": 17.8}}
     if extras:
         m.update({"fp64_chfsi": {"blk": 256, "f64_ms": 3500.0, "mix_ms": 250.0},
@@ -63,7 +64,10 @@ def test_assembled_line_has_every_key():
     assert e["h2d_bytes_per_step"] == w.nvec * w.ndof * 16 and e["d2h_bytes_per_step"] > 0
     assert abs(e["value"] - units / 1.2) < 1e-6 * e["value"]
     assert line["fp64_chfsi"]["speedup_mixed_over_fp64"] == 14.0
-    assert set(line["variants"]) == {"df_residual", "fp16_storage", "bf16_storage"}
+    assert set(line["variants"]) == {"df_residual", "fp16_storage", "bf16_storage", "bfp12_residual"}
+    rb = line["roofline_bfp12_step"]
+    assert abs(rb["achieved"] - 27.0 * w.ndof * 256 / 3.3e-3 / 1e9) < 1e-6 * rb["achieved"]
+    assert abs(rb["frac"] - rb["achieved"] / 6802.0) < 1e-12
 
 
 def test_assembled_line_scales_with_ranks_and_nulls_stale_traffic():

@@ -131,6 +131,8 @@ def test_unsupported_paths_are_refused(fm):
     Y = torch.zeros_like(X)
     for fn in (lambda: R.rcf_filter(fm.ctx, fm.op, X, np.zeros(2), 4, (-1.0, 0.0, 50.0), R.RCF_RCHFSI,
                                     R.RCF_FP32_DF, 0, Y),
+               lambda: R.rcf_filter(fm.ctx, fm.op, X, np.zeros(2), 4, (-1.0, 0.0, 50.0), R.RCF_RCHFSI,
+                                    R.RCF_FP32_BFP12, 0, Y),
                lambda: R.rcf_apply_noalloc(fm.ctx, fm.op, 0, X, Y, R.RCF_FP64)):
         with pytest.raises(R.RcfError) as ei:
             fn()

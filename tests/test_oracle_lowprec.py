@@ -96,6 +96,24 @@ def test_bfp_storage_error_is_residual_proportional(near_converged, nbits, lo, h
     assert 0.5e-3 < errs[1] / errs[0] < 2e-3
 
 
+@pytest.mark.parametrize("nbits,lo,hi", [(16, 1.2e-7, 6e-7), (12, 2e-6, 9e-6)])
+def test_bfp_residual_storage_error_is_residual_proportional(near_converged, nbits, lo, hi):
+    """R alone stored in BFP (the library's RCF_FP32_BFP12 at 12 bits): measured 2.7e-7 / 4.4e-6
+    at a 1e-3 perturbation (16 / 12 bits), falling 1000x with it; most of the error of storing
+    Z_k, Z_{k-1} and R comes from R, the term every step adds."""
+    from lowprec_emulation import rchfsi_filter_bfp, rchfsi_filter_bfp_residual
+    H, Xc, lam, b, noise = near_converged
+    errs, full = [], []
+    for delta in (1e-3, 1e-6):
+        X = Xc + delta * noise / np.linalg.norm(noise) * np.linalg.norm(Xc)
+        ref = rchfsi_filter(H, X, lam, *b, 10)
+        errs.append(_rel(rchfsi_filter_bfp_residual(H, X, lam, *b, 10, nbits)[:, :28], ref[:, :28]))
+        full.append(_rel(rchfsi_filter_bfp(H, X, lam, *b, 10, nbits)[:, :28], ref[:, :28]))
+    assert lo < errs[0] < hi
+    assert 0.5e-3 < errs[1] / errs[0] < 2e-3
+    assert 0.5 * full[0] < errs[0] < full[0]
+
+
 def test_bfp_storage_eigensolver_follows_the_fp64_loop(near_converged):
     """Algorithm 1 from a perturbed block: with 12-bit BFP storage the residual history and the
     Ritz values follow the FP64 filter's, cycle by cycle."""
