@@ -9,6 +9,7 @@
 #include <type_traits>
 
 #include "internal.h"
+#include "stencil_common.cuh"
 
 namespace rcf {
 namespace {
@@ -49,19 +50,32 @@ __global__ void __launch_bounds__(kProjThreads)
   Real acc[24];
 #pragma unroll
   for (int i = 0; i < 24; ++i) acc[i] = Real(0);
-  for (int e = e0 + threadIdx.x; e < e1; e += kProjThreads) {
-    const int I = node[e];
-    const Real w = proj_mass ? Real(mass[I]) : Real(1);
-    const Real ur = to_real<Real>(x[4 * int64_t(I) + 0]), ui = to_real<Real>(x[4 * int64_t(I) + 1]);
-    const Real dr = to_real<Real>(x[4 * int64_t(I) + 2]), di = to_real<Real>(x[4 * int64_t(I) + 3]);
+  // two support entries per pass, their node tuples loaded whole, so that two independent
+  // index -> value load chains are in flight per thread
+  const R4<St>* xt = reinterpret_cast<const R4<St>*>(x);
+  for (int e = e0 + threadIdx.x; e < e1; e += 2 * kProjThreads) {
+    const int e2 = e + kProjThreads;
+    const bool two = e2 < e1;
+    const int I = node[e], I2 = two ? node[e2] : I;
+    const R4<St> t1 = ldgs(xt + I), t2 = ldgs(xt + I2);
+    const Real w1 = proj_mass ? Real(mass[I]) : Real(1);
+    const Real w2 = two ? (proj_mass ? Real(mass[I2]) : Real(1)) : Real(0);
 #pragma unroll
-    for (int f6 = 0; f6 < 6; ++f6) {          // f6 = 3 j + i
-      const Real b = w * beta[6 * int64_t(e) + f6];
-      const int f = 2 * f6;                   // 6 j + 2 i + sigma = 2 (3 j + i) + sigma
-      acc[2 * f + 0] += b * ur;
-      acc[2 * f + 1] += b * ui;
-      acc[2 * (f + 1) + 0] += b * dr;
-      acc[2 * (f + 1) + 1] += b * di;
+    for (int h = 0; h < 2; ++h) {
+      const R4<St>& t = h ? t2 : t1;
+      const Real w = h ? w2 : w1;
+      const int64_t eb = 6 * int64_t(h ? (two ? e2 : e) : e);
+      const Real ur = to_real<Real>(t.v[0]), ui = to_real<Real>(t.v[1]);
+      const Real dr = to_real<Real>(t.v[2]), di = to_real<Real>(t.v[3]);
+#pragma unroll
+      for (int f6 = 0; f6 < 6; ++f6) {          // f6 = 3 j + i
+        const Real b = w * beta[eb + f6];
+        const int f = 2 * f6;                   // 6 j + 2 i + sigma = 2 (3 j + i) + sigma
+        acc[2 * f + 0] += b * ur;
+        acc[2 * f + 1] += b * ui;
+        acc[2 * (f + 1) + 0] += b * dr;
+        acc[2 * (f + 1) + 1] += b * di;
+      }
     }
   }
   __shared__ Real red[kProjThreads / 32][24];
@@ -126,6 +140,11 @@ __global__ void nl_addback_kernel(const int* __restrict__ unode, const int* __re
   if (u >= nunion) return;
   const int I = unode[u];
   const int nv = min(NV, nvec - v0);
+  // the node's outputs of the NV vectors, loaded as whole tuples before any update
+  R4<St> y[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j)
+    if (j < nv) y[j] = ld4(reinterpret_cast<const R4<St>*>(out + 2 * int64_t(v0 + j) * ld) + I);
   Real s[NV][4];
 #pragma unroll
   for (int j = 0; j < NV; ++j)
@@ -153,9 +172,9 @@ __global__ void nl_addback_kernel(const int* __restrict__ unode, const int* __re
 #pragma unroll
   for (int j = 0; j < NV; ++j)
     if (j < nv) {
-      St* y = out + 2 * int64_t(v0 + j) * ld + 4 * int64_t(I);
 #pragma unroll
-      for (int i = 0; i < 4; ++i) y[i] = from_real<St>(to_real<Real>(y[i]) + w * s[j][i]);
+      for (int i = 0; i < 4; ++i) y[j].v[i] = from_real<St>(to_real<Real>(y[j].v[i]) + w * s[j][i]);
+      st4(reinterpret_cast<R4<St>*>(out + 2 * int64_t(v0 + j) * ld) + I, y[j]);
     }
 }
 

@@ -249,8 +249,6 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
 #pragma unroll
           for (int cc = 0; cc < P; ++cc) fma4(acc[cc], tab.c[2][cc][P], u);
           emit(ez - 1);
-        } else {
-          u0 = u;
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[0].v[i] = accn.v[i] + self.v[i];
@@ -269,7 +267,9 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
       }
     }
   }
-  // the last element closes on plane Gz = 0 (periodic)
+  // the last element closes on plane Gz = 0 (periodic), read again here rather than kept in
+  // registers through the march
+  if (active) u0 = CV::in(ldgs(in + col));
 #pragma unroll
   for (int cc = 0; cc < P; ++cc) fma4(acc[cc], tab.c[2][cc][P], u0);
   emit(nz - 1);
