@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
         if (prev) fma4(self, C, cprev);
         if constexpr (RBF) {
           float r[4];
-          bfp_decode4<10>(bfp12_join(int((rblk0 + int64_t(z) * plane) & 1), crw, crh), r);
+          bfp12_decode(bfp12_join(int((rblk0 + int64_t(z) * plane) & 1), crw, crh), r);
 #pragma unroll
           for (int i = 0; i < 4; ++i) crv.v[i] = r[i];
         }
