@@ -75,83 +75,391 @@ __global__ void fm_pass_kernel(int d, int p, int Gx, int Gy, int Gz, const Real*
 }
 
 // Per cell e and vector v: E[v][e][l] = sum_q N_l(x_q) w_q |J| (V_q I + B_q . sigma) u(x_q),
-// u(x_q) = sum_l' N_l'(x_q) u_{node(e, l')}.  Shared memory: two buffers of S4 spinors.
-template <typename Real>
-__global__ void fm_cell_kernel(int p, int nq, int nx, int ny, int nz, const Real* __restrict__ B1,
-                               const Real* __restrict__ vq, const Real* __restrict__ in, int64_t ldin,
-                               Real* __restrict__ E, int S4) {
-  extern __shared__ __align__(16) unsigned char fm_smem[];
-  R4<Real>* bufA = reinterpret_cast<R4<Real>*>(fm_smem);
-  R4<Real>* bufB = bufA + S4;
-  const int np = p + 1;
+// u(x_q) = sum_l' N_l'(x_q) u_{node(e, l')} (u = dinv in if dinv is given), by sum
+// factorisation: each 1D contraction is done by one thread per line of the cell, with the
+// line's values in registers, so that shared memory holds only the intermediate blocks:
+//   1. gather + x:  line (b, c): u[a] from HBM -> A[qx + nq (b + NP c)]
+//   2. y:           line (qx, c): A[. b .] -> Bf[qx + nq (qy + nq c)]
+//   3. z, potential, z back: line (qx, qy): Bf[. c] -> u at the nq points of the line ->
+//                   times w_q |J| (V + B . sigma) -> projected back onto c -> A[qx + nq (qy + nq c)]
+//   4. y back:      line (qx, c): A[. qy .] -> Bf[qx + nq (b + NP c)]
+//   5. x back:      line (b, c): Bf[qx . .] -> E[a + NP (b + NP c)] in HBM
+// A block takes one cell and NVB vectors (the cell's potential read once for them); SB
+// tuples per vector and buffer.  B1 [nq][NP]: the Lagrange basis at the Gauss nodes.
+template <typename Real, int P>
+__global__ void __launch_bounds__(256) fm_cell_kernel(int nq, int nx, int ny, int nz, const Real* __restrict__ B1,
+                                                      const Real* __restrict__ vq, const Real* __restrict__ in,
+                                                      int64_t ldin, const double* __restrict__ dinv,
+                                                      Real* __restrict__ E, int nvec, int NVB, int SB) {
+  using V4 = R4<Real>;
+  constexpr int NP = P + 1, NL = NP * NP * NP;
+  extern __shared__ __align__(16) unsigned char fm_cell_smem[];
+  V4* A = reinterpret_cast<V4*>(fm_cell_smem);   // [NVB][SB]
+  V4* Bf = A + size_t(NVB) * SB;                  // [NVB][SB]
+  Real* B = reinterpret_cast<Real*>(Bf + size_t(NVB) * SB);   // [nq][NP]
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int64_t e = blockIdx.x;
-  const int v = blockIdx.y;
+  const int v0 = blockIdx.y * NVB, nvb = min(NVB, nvec - v0);
   const int ex = int(e % nx), ey = int((e / nx) % ny), ez = int(e / (int64_t(nx) * ny));
-  const int Gx = nx * p, Gy = ny * p, Gz = nz * p;
-  const int nl = np * np * np, nq3 = nq * nq * nq;
-  // gather the cell's nodal values: l = a + np (b + np c)
-  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
-    const int a = l % np, b = (l / np) % np, c = l / (np * np);
-    const int64_t I = (ex * p + a) % Gx + int64_t(Gx) * ((ey * p + b) % Gy + int64_t(Gy) * ((ez * p + c) % Gz));
-    bufA[l] = ld_node(in, ldin, v, I);
+  const int Gx = nx * P, Gy = ny * P, Gz = nz * P;
+  const int nq2 = nq * nq, nq3 = nq2 * nq;
+  for (int i = tid; i < nq * NP; i += nt) B[i] = B1[i];
+  __syncthreads();
+  // 1. gather and interpolate along x
+  for (int t = tid; t < nvb * NP * NP; t += nt) {
+    const int j = t / (NP * NP), line = t - j * NP * NP;
+    const int b = line % NP, c = line / NP;
+    int yy = ey * P + b, zz = ez * P + c;
+    if (yy >= Gy) yy -= Gy;
+    if (zz >= Gz) zz -= Gz;
+    const int64_t rowI = int64_t(Gx) * (yy + int64_t(Gy) * zz);
+    const V4* x = reinterpret_cast<const V4*>(in + 2 * int64_t(v0 + j) * ldin);
+    V4 u[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      int xx = ex * P + a;
+      if (xx >= Gx) xx -= Gx;
+      u[a] = ldg4(x + rowI + xx);
+      if (dinv) {
+        const Real d = Real(dinv[rowI + xx]);
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) u[a].v[c4] *= d;
+      }
+    }
+    V4* out = A + size_t(j) * SB + nq * line;
+    for (int qx = 0; qx < nq; ++qx) {
+      V4 s = zero4<Real>();
+#pragma unroll
+      for (int a = 0; a < NP; ++a) fma4(s, B[qx * NP + a], u[a]);
+      out[qx] = s;
+    }
   }
   __syncthreads();
-  // interpolate along x: A1[qx + nq (b + np c)] = sum_a B1[qx][a] U[a + np (b + np c)]
-  for (int t = threadIdx.x; t < nq * np * np; t += blockDim.x) {
-    const int qx = t % nq, bc = t / nq;
-    R4<Real> s = zero4<Real>();
-    for (int a = 0; a < np; ++a) fma4(s, B1[qx * np + a], bufA[a + np * bc]);
-    bufB[t] = s;
+  // 2. along y
+  for (int t = tid; t < nvb * nq * NP; t += nt) {
+    const int j = t / (nq * NP), line = t - j * nq * NP;
+    const int qx = line % nq, c = line / nq;
+    const V4* src = A + size_t(j) * SB;
+    V4 u[NP];
+#pragma unroll
+    for (int b = 0; b < NP; ++b) u[b] = src[qx + nq * (b + NP * c)];
+    V4* out = Bf + size_t(j) * SB;
+    for (int qy = 0; qy < nq; ++qy) {
+      V4 s = zero4<Real>();
+#pragma unroll
+      for (int b = 0; b < NP; ++b) fma4(s, B[qy * NP + b], u[b]);
+      out[qx + nq * (qy + nq * c)] = s;
+    }
   }
   __syncthreads();
-  // along y: A2[qx + nq (qy + nq c)] = sum_b B1[qy][b] A1[qx + nq (b + np c)]
-  for (int t = threadIdx.x; t < nq * nq * np; t += blockDim.x) {
-    const int qx = t % nq, qy = (t / nq) % nq, c = t / (nq * nq);
-    R4<Real> s = zero4<Real>();
-    for (int b = 0; b < np; ++b) fma4(s, B1[qy * np + b], bufB[qx + nq * (b + np * c)]);
-    bufA[t] = s;
-  }
-  __syncthreads();
-  // along z, then the spinor potential at the point
+  // 3. along z to the points, the spinor potential, and back along z
   const Real* vc = vq + 4 * e * int64_t(nq3);
-  for (int t = threadIdx.x; t < nq3; t += blockDim.x) {
-    const int qxy = t % (nq * nq), qz = t / (nq * nq);
-    R4<Real> u = zero4<Real>();
-    for (int c = 0; c < np; ++c) fma4(u, B1[qz * np + c], bufA[qxy + nq * nq * c]);
-    const Real V = vc[4 * t], Bx = vc[4 * t + 1], By = vc[4 * t + 2], Bz = vc[4 * t + 3];
-    // up = (V + Bz) u_up + (Bx - i By) u_dn ; dn = (Bx + i By) u_up + (V - Bz) u_dn
-    R4<Real> o;
-    o.v[0] = (V + Bz) * u.v[0] + Bx * u.v[2] + By * u.v[3];
-    o.v[1] = (V + Bz) * u.v[1] + Bx * u.v[3] - By * u.v[2];
-    o.v[2] = Bx * u.v[0] - By * u.v[1] + (V - Bz) * u.v[2];
-    o.v[3] = Bx * u.v[1] + By * u.v[0] + (V - Bz) * u.v[3];
-    bufB[t] = o;
+  for (int t = tid; t < nvb * nq2; t += nt) {
+    const int j = t / nq2, qxy = t - j * nq2;
+    const V4* src = Bf + size_t(j) * SB;
+    V4 u[NP], o[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) {
+      u[c] = src[qxy + nq2 * c];
+      o[c] = zero4<Real>();
+    }
+    for (int qz = 0; qz < nq; ++qz) {
+      V4 w = zero4<Real>();
+#pragma unroll
+      for (int c = 0; c < NP; ++c) fma4(w, B[qz * NP + c], u[c]);
+      const int q = qxy + nq2 * qz;
+      const Real V = vc[4 * q], Bx = vc[4 * q + 1], By = vc[4 * q + 2], Bz = vc[4 * q + 3];
+      // up = (V + Bz) u_up + (Bx - i By) u_dn ; dn = (Bx + i By) u_up + (V - Bz) u_dn
+      V4 h;
+      h.v[0] = (V + Bz) * w.v[0] + Bx * w.v[2] + By * w.v[3];
+      h.v[1] = (V + Bz) * w.v[1] + Bx * w.v[3] - By * w.v[2];
+      h.v[2] = Bx * w.v[0] - By * w.v[1] + (V - Bz) * w.v[2];
+      h.v[3] = Bx * w.v[1] + By * w.v[0] + (V - Bz) * w.v[3];
+#pragma unroll
+      for (int c = 0; c < NP; ++c) fma4(o[c], B[qz * NP + c], h);
+    }
+    V4* out = A + size_t(j) * SB;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) out[qxy + nq2 * c] = o[c];
   }
   __syncthreads();
-  // project along z: P2[qx + nq (qy + nq c)] = sum_qz B1[qz][c] W[qx + nq (qy + nq qz)]
-  for (int t = threadIdx.x; t < nq * nq * np; t += blockDim.x) {
-    const int qxy = t % (nq * nq), c = t / (nq * nq);
-    R4<Real> s = zero4<Real>();
-    for (int qz = 0; qz < nq; ++qz) fma4(s, B1[qz * np + c], bufB[qxy + nq * nq * qz]);
-    bufA[t] = s;
+  // 4. back along y
+  for (int t = tid; t < nvb * nq * NP; t += nt) {
+    const int j = t / (nq * NP), line = t - j * nq * NP;
+    const int qx = line % nq, c = line / nq;
+    const V4* src = A + size_t(j) * SB;
+    V4 o[NP];
+#pragma unroll
+    for (int b = 0; b < NP; ++b) o[b] = zero4<Real>();
+    for (int qy = 0; qy < nq; ++qy) {
+      const V4 w = src[qx + nq * (qy + nq * c)];
+#pragma unroll
+      for (int b = 0; b < NP; ++b) fma4(o[b], B[qy * NP + b], w);
+    }
+    V4* out = Bf + size_t(j) * SB;
+#pragma unroll
+    for (int b = 0; b < NP; ++b) out[qx + nq * (b + NP * c)] = o[b];
   }
   __syncthreads();
-  // along y: P1[qx + nq (b + np c)] = sum_qy B1[qy][b] P2[qx + nq (qy + nq c)]
-  for (int t = threadIdx.x; t < nq * np * np; t += blockDim.x) {
-    const int qx = t % nq, b = (t / nq) % np, c = t / (nq * np);
-    R4<Real> s = zero4<Real>();
-    for (int qy = 0; qy < nq; ++qy) fma4(s, B1[qy * np + b], bufA[qx + nq * (qy + nq * c)]);
-    bufB[t] = s;
+  // 5. back along x, to the cell buffer
+  for (int t = tid; t < nvb * NP * NP; t += nt) {
+    const int j = t / (NP * NP), line = t - j * NP * NP;
+    const V4* src = Bf + size_t(j) * SB + nq * line;
+    V4 o[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) o[a] = zero4<Real>();
+    for (int qx = 0; qx < nq; ++qx) {
+      const V4 w = src[qx];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) fma4(o[a], B[qx * NP + a], w);
+    }
+    V4* out = reinterpret_cast<V4*>(E) + (int64_t(v0 + j) * gridDim.x + e) * NL + NP * line;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) out[a] = o[a];
+  }
+}
+
+// Element matrices of the fused x-y pass: K and M along x (d = 0) and y (d = 1), [P + 1][P + 1]
+template <typename Real, int P>
+struct XYTab {
+  Real k[2][P + 1][P + 1], m[2][P + 1][P + 1];
+};
+
+// Tile of the fused x-y pass: whole elements, about 32 x 16 nodes
+template <int P>
+struct XYTile {
+  static constexpr int NEX = (32 + P - 1) / P, NEY = (16 + P - 1) / P;   // elements per tile row / column
+  static constexpr int TX = NEX * P, TY = NEY * P;
+  static constexpr int UY = TY + P + 1;                                     // t rows: y0 - P .. y0 + TY
+  static constexpr int THREADS = 128;
+};
+
+// The x and y passes of one z plane, fused: over a tile of whole elements,
+//   s1 = My Mx u,  s2 = Ky Mx u + My Kx u      (u = dinv in if dinv is given, else in)
+// One thread per (row, element) of the tile takes the element's P + 1 nodes and the left
+// element's P nodes straight from memory (the neighbouring threads' loads hit L1), and
+// writes t1 = Mx u and t2 = Kx u of the element's P nodes (a vertex sums its two elements'
+// rows) for the rows y0 - P .. y0 + TY into shared memory; then one thread per (column,
+// element) does the same along y from shared memory and writes s1 and s2.  Each staged value
+// is read about twice instead of once per tap.  Grid (x-y tiles, Gz, nvec).
+template <typename Real, int P>
+__global__ void __launch_bounds__(XYTile<P>::THREADS) fm_xy_kernel(const XYTab<Real, P> tab, int Gx, int Gy,
+                                                                   const Real* __restrict__ in, int64_t ldin,
+                                                                   const double* __restrict__ dinv,
+                                                                   Real* __restrict__ s1, Real* __restrict__ s2,
+                                                                   int64_t lds) {
+  using T = XYTile<P>;
+  using V4 = R4<Real>;
+  constexpr int TX = T::TX, UY = T::UY, NP = P + 1;
+  extern __shared__ __align__(16) unsigned char fm_xy_smem[];
+  V4* T1 = reinterpret_cast<V4*>(fm_xy_smem);   // [UY][TX]
+  V4* T2 = T1 + UY * TX;
+  XYTab<Real, P>* tb = reinterpret_cast<XYTab<Real, P>*>(T2 + UY * TX);
+  const int tid = threadIdx.x, nt = T::THREADS;
+  const int ntx = (Gx + TX - 1) / TX;
+  const int x0 = (blockIdx.x % ntx) * TX, y0 = (blockIdx.x / ntx) * T::TY;
+  const int z = blockIdx.y, v = blockIdx.z;
+  const int64_t plane = int64_t(Gx) * Gy, zoff = int64_t(z) * plane;
+  for (int i = tid; i < int(sizeof(XYTab<Real, P>) / sizeof(Real)); i += nt)
+    reinterpret_cast<Real*>(tb)[i] = reinterpret_cast<const Real*>(&tab)[i];
+  __syncthreads();
+  const V4* src = reinterpret_cast<const V4*>(in + 2 * int64_t(v) * ldin) + zoff;
+  // x: item (r, ei): row y = y0 - P + r, element ei of the tile (nodes x0 + ei P .. + P - 1)
+  for (int t = tid; t < UY * T::NEX; t += nt) {
+    const int r = t / T::NEX, ei = t - r * T::NEX;
+    const int xe = x0 + ei * P;
+    if (xe >= Gx) continue;
+    int yy = (y0 - P + r) % Gy;
+    if (yy < 0) yy += Gy;
+    const int64_t row = int64_t(Gx) * yy;
+    V4 u[2 * P + 1];   // x = xe - P .. xe + P
+#pragma unroll
+    for (int q = 0; q <= 2 * P; ++q) {
+      int xx = (xe - P + q) % Gx;
+      if (xx < 0) xx += Gx;
+      u[q] = ldg4(src + row + xx);
+      if (dinv) {
+        const Real d = Real(dinv[zoff + row + xx]);
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) u[q].v[c4] *= d;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+      V4 m1 = zero4<Real>(), k1 = zero4<Real>();
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        fma4(m1, tb->m[0][a][q], u[P + q]);
+        fma4(k1, tb->k[0][a][q], u[P + q]);
+      }
+      if (a == 0) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          fma4(m1, tb->m[0][P][q], u[q]);
+          fma4(k1, tb->k[0][P][q], u[q]);
+        }
+      }
+      T1[r * TX + ei * P + a] = m1;
+      T2[r * TX + ei * P + a] = k1;
+    }
   }
   __syncthreads();
-  // along x: E[a + np (b + np c)] = sum_qx B1[qx][a] P1[qx + nq (b + np c)]
-  R4<Real>* out = reinterpret_cast<R4<Real>*>(E) + (int64_t(v) * gridDim.x + e) * nl;
-  for (int t = threadIdx.x; t < nl; t += blockDim.x) {
-    const int a = t % np, bc = t / np;
-    R4<Real> s = zero4<Real>();
-    for (int qx = 0; qx < nq; ++qx) fma4(s, B1[qx * np + a], bufB[qx + nq * bc]);
-    out[t] = s;
+  // y: item (cx, ej): column x0 + cx, element ej of the tile (rows y0 + ej P .. + P - 1)
+  for (int t = tid; t < TX * T::NEY; t += nt) {
+    const int ej = t / TX, cx = t - ej * TX;
+    const int gx = x0 + cx, ye = y0 + ej * P;
+    if (gx >= Gx || ye >= Gy) continue;
+    V4 t1[2 * P + 1], t2[2 * P + 1];   // staged rows ej P .. ej P + 2 P (y = ye - P .. ye + P)
+#pragma unroll
+    for (int q = 0; q <= 2 * P; ++q) {
+      t1[q] = T1[(ej * P + q) * TX + cx];
+      t2[q] = T2[(ej * P + q) * TX + cx];
+    }
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+      V4 o1 = zero4<Real>(), o2 = zero4<Real>();
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const Real my = tb->m[1][b][q];
+        fma4(o1, my, t1[P + q]);
+        fma4(o2, tb->k[1][b][q], t1[P + q]);
+        fma4(o2, my, t2[P + q]);
+      }
+      if (b == 0) {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          const Real my = tb->m[1][P][q];
+          fma4(o1, my, t1[q]);
+          fma4(o2, tb->k[1][P][q], t1[q]);
+          fma4(o2, my, t2[q]);
+        }
+      }
+      const int64_t I = zoff + gx + int64_t(Gx) * (ye + b);
+      st4(reinterpret_cast<V4*>(s1 + 2 * int64_t(v) * lds) + I, o1);
+      st4(reinterpret_cast<V4*>(s2 + 2 * int64_t(v) * lds) + I, o2);
+    }
   }
+}
+
+// z-direction element matrices of the fused z pass: K and M, element-local [P + 1][P + 1]
+template <typename Real, int P>
+struct ZTab {
+  Real k[P + 1][P + 1], m[P + 1][P + 1];
+};
+
+// The z pass fused with the potential's node gather and the recurrence combination.  One
+// thread per (x, y) column of one vector marches through the z planes as the lumped step
+// kernel does: input plane c of element ez adds K[cc][c] s1 + M[cc][c] s2 to the element's
+// outputs cc (registers), and the element's P planes are written when its closing vertex
+// plane arrives, each as
+//   T = K u (the z pass) + the per-cell potential terms E of the up to 8 cells of the node
+//   mode 3 (H D^-1): out = A T + B in + C prev + g[v] rv
+//   mode 2 (D^-1 H): out = A dinv T + B in + C prev + g[v] rv
+// (in, prev, rv, E may be null).  Grid (ceil(Gx Gy / 128), nvec).
+template <typename Real, int P>
+__global__ void __launch_bounds__(128) fm_z_kernel(const ZTab<Real, P> zt, int Gx, int Gy, int Gz,
+                                                   const Real* __restrict__ s1, const Real* __restrict__ s2,
+                                                   int64_t lds, const Real* __restrict__ E, int mode, Real A,
+                                                   Real B, const Real* __restrict__ in, int64_t ldin, Real C,
+                                                   const Real* prev, int64_t ldprev, const double* __restrict__ g,
+                                                   const Real* __restrict__ rv, int64_t ldrv,
+                                                   const double* __restrict__ dinv, Real* out, int64_t ldout) {
+  using V4 = R4<Real>;
+  const int64_t plane = int64_t(Gx) * Gy;
+  const int64_t col = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y;
+  if (col >= plane) return;
+  const int i = int(col % Gx), j = int(col / Gx);
+  const int nx = Gx / P, ny = Gy / P, nzc = Gz / P;
+  constexpr int NL = (P + 1) * (P + 1) * (P + 1);
+  const V4* S1 = reinterpret_cast<const V4*>(s1 + 2 * int64_t(v) * lds) + col;
+  const V4* S2 = reinterpret_cast<const V4*>(s2 + 2 * int64_t(v) * lds) + col;
+  const V4* Ev = E ? reinterpret_cast<const V4*>(E) + int64_t(v) * nx * ny * nzc * NL : nullptr;
+  const Real gv = (rv && g) ? Real(g[v]) : Real(0);
+  // x and y cells of this column: (cell, local) pairs, two at an element vertex
+  int cxe[2], cxl[2], cye[2], cyl[2];
+  const int ax = i % P, ay = j % P;
+  cxe[0] = i / P; cxl[0] = ax; cxe[1] = (i / P + nx - 1) % nx; cxl[1] = P;
+  cye[0] = j / P; cyl[0] = ay; cye[1] = (j / P + ny - 1) % ny; cyl[1] = P;
+  const int ncx = ax == 0 ? 2 : 1, ncy = ay == 0 ? 2 : 1;
+
+  V4 acc[P];
+  auto emit = [&](int ez) {
+#pragma unroll
+    for (int cc = 0; cc < P; ++cc) {
+      const int k = ez * P + cc;
+      const int64_t I = col + int64_t(k) * plane;
+      V4 t = acc[cc];
+      if (Ev) {
+        for (int zc = 0; zc < (cc == 0 ? 2 : 1); ++zc) {
+          const int ez2 = zc == 0 ? ez : (ez + nzc - 1) % nzc, lz = zc == 0 ? cc : P;
+          for (int yc = 0; yc < ncy; ++yc)
+            for (int xc = 0; xc < ncx; ++xc) {
+              const int64_t e = cxe[xc] + int64_t(nx) * (cye[yc] + int64_t(ny) * ez2);
+              const V4 w = ldg4(Ev + e * NL + cxl[xc] + (P + 1) * (cyl[yc] + (P + 1) * lz));
+#pragma unroll
+              for (int c4 = 0; c4 < 4; ++c4) t.v[c4] += w.v[c4];
+            }
+        }
+      }
+      const Real a = mode == 2 ? Real(A * Real(dinv[I])) : A;
+      V4 o = zero4<Real>();
+      fma4(o, a, t);
+      if (in && B != Real(0)) fma4(o, B, ldg4(reinterpret_cast<const V4*>(in + 2 * int64_t(v) * ldin) + I));
+      if (prev) fma4(o, C, ld4(reinterpret_cast<const V4*>(prev + 2 * int64_t(v) * ldprev) + I));
+      if (rv && g) fma4(o, gv, ldg4(reinterpret_cast<const V4*>(rv + 2 * int64_t(v) * ldrv) + I));
+      st4(reinterpret_cast<V4*>(out + 2 * int64_t(v) * ldout) + I, o);
+    }
+  };
+  auto contrib = [&](V4& dst, int row, int c, const V4& a1, const V4& a2) {
+    fma4(dst, zt.k[row][c], a1);
+    fma4(dst, zt.m[row][c], a2);
+  };
+  // element -1 (planes Gz - P .. Gz - 1) adds row P of its matrices to the vertex plane 0
+  V4 accn = zero4<Real>();
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    const int64_t o = int64_t(Gz - P + c) * plane;
+    contrib(accn, P, c, ldg4(S1 + o), ldg4(S2 + o));
+  }
+  V4 n1 = ldg4(S1), n2 = ldg4(S2);   // the next plane, one ahead
+  for (int ez = 0; ez < nzc; ++ez) {
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      const int z = ez * P + c;
+      const V4 a1 = n1, a2 = n2;
+      if (z + 1 < Gz) {
+        n1 = ldg4(S1 + int64_t(z + 1) * plane);
+        n2 = ldg4(S2 + int64_t(z + 1) * plane);
+      }
+      if (c == 0) {
+        contrib(accn, P, P, a1, a2);
+        if (ez > 0) {
+#pragma unroll
+          for (int cc = 0; cc < P; ++cc) contrib(acc[cc], cc, P, a1, a2);
+          emit(ez - 1);
+        }
+        acc[0] = accn;
+#pragma unroll
+        for (int cc = 1; cc < P; ++cc) acc[cc] = zero4<Real>();
+#pragma unroll
+        for (int cc = 0; cc < P; ++cc) contrib(acc[cc], cc, 0, a1, a2);
+        accn = zero4<Real>();
+        contrib(accn, P, 0, a1, a2);
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < P; ++cc) contrib(acc[cc], cc, c, a1, a2);
+        contrib(accn, P, c, a1, a2);
+      }
+    }
+  }
+  // the last element closes on plane Gz = 0 (periodic)
+  {
+    const V4 a1 = ldg4(S1), a2 = ldg4(S2);
+#pragma unroll
+    for (int cc = 0; cc < P; ++cc) contrib(acc[cc], cc, P, a1, a2);
+  }
+  emit(nzc - 1);
 }
 
 // T[I] += sum over the cells e containing node I of E[v][e][local index of I in e]
@@ -330,6 +638,46 @@ int ws_block(rcf_ctx* ctx, int slot, const rcf_op* op, int nvec, Real** p) {
   return workspace(ctx, slot, sizeof(Real) * 4 * size_t(op->mesh->nnodes) * nvec, reinterpret_cast<void**>(p));
 }
 
+// the per-cell Gauss-point potential for degree P: E (cell buffer, [nvec][cells][(P+1)^3]
+// tuples) from in (times dinv if given); vectors per block from the shared memory they need
+template <typename Real, int P>
+int launch_fm_cell_p(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ldin, const double* dinv, Real* E,
+                     int nvec) {
+  const rcf_mesh* m = op->mesh;
+  const FullMass* fm = op->fm;
+  constexpr int NP = P + 1;
+  const int nq = fm->nq;
+  const int SB = std::max(nq * NP * NP, nq * nq * NP);
+  const size_t per_vec = 2 * size_t(SB) * sizeof(R4<Real>);
+  // vectors per block: every phase's lines (at most max(NP^2, nq NP, nq^2) per vector) in one
+  // pass of the 256 threads, within ~96 KB of shared memory
+  const int lines = std::max({NP * NP, nq * NP, nq * nq});
+  const int NVB = int(std::max<size_t>(
+      1, std::min<size_t>({8, size_t(256 / lines), size_t(96 * 1024) / per_vec, size_t(nvec)})));
+  const size_t smem = NVB * per_vec + sizeof(Real) * nq * NP;
+  auto kern = fm_cell_kernel<Real, P>;
+  if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  kern<<<dim3(unsigned(m->ncells), unsigned((nvec + NVB - 1) / NVB)), 256, smem, ctx->stream>>>(
+      nq, m->n[0], m->n[1], m->n[2], fm_b1<Real>(fm), fm_vq<Real>(fm), in, ldin, dinv, E, nvec, NVB, SB);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+template <typename Real>
+int launch_fm_cell(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ldin, const double* dinv, Real* E,
+                   int nvec) {
+  switch (op->mesh->p) {
+    case 1: return launch_fm_cell_p<Real, 1>(ctx, op, in, ldin, dinv, E, nvec);
+    case 2: return launch_fm_cell_p<Real, 2>(ctx, op, in, ldin, dinv, E, nvec);
+    case 3: return launch_fm_cell_p<Real, 3>(ctx, op, in, ldin, dinv, E, nvec);
+    case 4: return launch_fm_cell_p<Real, 4>(ctx, op, in, ldin, dinv, E, nvec);
+    case 5: return launch_fm_cell_p<Real, 5>(ctx, op, in, ldin, dinv, E, nvec);
+    case 6: return launch_fm_cell_p<Real, 6>(ctx, op, in, ldin, dinv, E, nvec);
+    case 7: return launch_fm_cell_p<Real, 7>(ctx, op, in, ldin, dinv, E, nvec);
+    case 8: return launch_fm_cell_p<Real, 8>(ctx, op, in, ldin, dinv, E, nvec);
+    default: return fail(ctx, RCF_ENOTSUP, "degree p=%d not built (1..8)", op->mesh->p);
+  }
+}
+
 // T = H u (kinetic with the consistent 1D masses, Gauss-point potential, projectors); u, T
 // node-tuple blocks with ld = 2M
 template <typename Real>
@@ -349,17 +697,11 @@ int hamiltonian_fm(rcf_ctx* ctx, const rcf_op* op, const Real* u, int64_t ldu, i
   RCF_TRY(pass<Real>(ctx, op, 2, Kz, Mz, nullptr, nullptr, s1, s2, ld, T, nullptr, ld, nvec));
   // Gauss-point potential: per-cell contributions, then summed at the nodes
   if (fm_vq<Real>(fm)) {
-    const int np = m->p + 1, nq = fm->nq;
+    const int np = m->p + 1;
     Real* E;
     RCF_TRY(workspace(ctx, WS_FM_CELL, sizeof(Real) * 4 * size_t(m->ncells) * np * np * np * nvec,
                       reinterpret_cast<void**>(&E)));
-    const int S4 = std::max(nq * nq * nq, np * np * np);
-    const size_t smem = 2 * size_t(S4) * sizeof(R4<Real>);
-    if (smem > 48 * 1024)
-      RCF_CUDA(ctx, cudaFuncSetAttribute(fm_cell_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    fm_cell_kernel<Real><<<dim3(unsigned(m->ncells), nvec), 128, smem, ctx->stream>>>(
-        m->p, nq, m->n[0], m->n[1], m->n[2], fm_b1<Real>(fm), fm_vq<Real>(fm), u, ldu, E, S4);
-    RCF_CHECK_LAUNCH(ctx);
+    RCF_TRY(launch_fm_cell<Real>(ctx, op, u, ldu, nullptr, E, nvec));
     fm_gather_kernel<Real><<<dim3(unsigned((m->nnodes + 255) / 256), nvec), 256, 0, ctx->stream>>>(
         m->p, m->n[0], m->n[1], m->n[2], m->ncells, E, T, ld);
     RCF_CHECK_LAUNCH(ctx);
@@ -395,11 +737,116 @@ int mass_apply_fm(rcf_ctx* ctx, const rcf_op* op, const Real* X, int64_t ldx, in
   return RCF_OK;
 }
 
+// the fused z pass for degree P
+template <typename Real, int P>
+int launch_fm_z(rcf_ctx* ctx, const rcf_op* op, const Real* s1, const Real* s2, int64_t lds, const Real* E,
+                int mode, const StepArgs<Real, Real>& a) {
+  const rcf_mesh* m = op->mesh;
+  const int np = P + 1;
+  ZTab<Real, P> zt;
+  for (int r = 0; r < np; ++r)
+    for (int c = 0; c < np; ++c) {
+      zt.k[r][c] = Real(op->fm->el[size_t(2) * np * np + size_t(r) * np + c]);
+      zt.m[r][c] = Real(op->fm->el[size_t(5) * np * np + size_t(r) * np + c]);
+    }
+  const int64_t cols = int64_t(m->G[0]) * m->G[1];
+  fm_z_kernel<Real, P><<<dim3(unsigned((cols + 127) / 128), a.nvec), 128, 0, ctx->stream>>>(
+      zt, m->G[0], m->G[1], m->G[2], s1, s2, lds, E, mode, a.A, a.B, a.in, a.ld_in, a.C, a.prev, a.ld_prev, a.g,
+      a.rv, a.ld_rv, m->d_inv_mass64, a.out, a.ld_out);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+
+// the fused x-y pass for degree P
+template <typename Real, int P>
+int launch_fm_xy(rcf_ctx* ctx, const rcf_op* op, const StepArgs<Real, Real>& a, const double* dinv, Real* s1,
+                 Real* s2, int64_t lds) {
+  using T = XYTile<P>;
+  const rcf_mesh* m = op->mesh;
+  constexpr int NP = P + 1;
+  XYTab<Real, P> tb;
+  for (int d = 0; d < 2; ++d)
+    for (int r = 0; r < NP; ++r)
+      for (int c = 0; c < NP; ++c) {
+        tb.k[d][r][c] = Real(op->fm->el[(size_t(d) * NP + r) * NP + c]);
+        tb.m[d][r][c] = Real(op->fm->el[(size_t(3 + d) * NP + r) * NP + c]);
+      }
+  const size_t smem = 2 * size_t(T::UY) * T::TX * sizeof(R4<Real>) + sizeof(XYTab<Real, P>);
+  auto kern = fm_xy_kernel<Real, P>;
+  if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  const int ntx = (m->G[0] + T::TX - 1) / T::TX, nty = (m->G[1] + T::TY - 1) / T::TY;
+  kern<<<dim3(unsigned(ntx * nty), unsigned(m->G[2]), unsigned(a.nvec)), T::THREADS, smem, ctx->stream>>>(
+      tb, m->G[0], m->G[1], a.in, a.ld_in, dinv, s1, s2, lds);
+  RCF_CHECK_LAUNCH(ctx);
+  return RCF_OK;
+}
+
+// Forms H D^-1 and D^-1 H of the recurrence step with the full mass, in three launches (plus
+// the projectors): the fused x-y pass per plane (s1, s2), the per-cell Gauss-point potential
+// (E), and the z pass fused with the node gather of E and the combination.  About 230 B per
+// node and vector move through HBM (u read twice, s1 and s2 written and read, E written and
+// read, in, Z_{k-1}, R read, out written) against ~390 B for the pass-by-pass form.
+template <typename Real>
+int apply_fm_fused(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real, Real>& a) {
+  const rcf_mesh* m = op->mesh;
+  const FullMass* fm = op->fm;
+  const int nvec = a.nvec, p = m->p;
+  const int64_t ld = 2 * m->nnodes;
+  if (m->G[2] > 65535 || nvec > 65535) return fail(ctx, RCF_ENOTSUP, "grid too large for the fused full-mass pass");
+  Real *s1, *s2;
+  RCF_TRY(ws_block<Real>(ctx, WS_FM_S1, op, nvec, &s1));
+  RCF_TRY(ws_block<Real>(ctx, WS_FM_S2, op, nvec, &s2));
+  const double* dinv = form == RCF_FORM_H_DINV ? m->d_inv_mass64 : nullptr;
+  switch (p) {
+    case 1: RCF_TRY((launch_fm_xy<Real, 1>(ctx, op, a, dinv, s1, s2, ld))); break;
+    case 2: RCF_TRY((launch_fm_xy<Real, 2>(ctx, op, a, dinv, s1, s2, ld))); break;
+    case 3: RCF_TRY((launch_fm_xy<Real, 3>(ctx, op, a, dinv, s1, s2, ld))); break;
+    case 4: RCF_TRY((launch_fm_xy<Real, 4>(ctx, op, a, dinv, s1, s2, ld))); break;
+    case 5: RCF_TRY((launch_fm_xy<Real, 5>(ctx, op, a, dinv, s1, s2, ld))); break;
+    case 6: RCF_TRY((launch_fm_xy<Real, 6>(ctx, op, a, dinv, s1, s2, ld))); break;
+    case 7: RCF_TRY((launch_fm_xy<Real, 7>(ctx, op, a, dinv, s1, s2, ld))); break;
+    case 8: RCF_TRY((launch_fm_xy<Real, 8>(ctx, op, a, dinv, s1, s2, ld))); break;
+    default: return fail(ctx, RCF_ENOTSUP, "degree p=%d not built (1..8)", p);
+  }
+  Real* E = nullptr;
+  if (fm_vq<Real>(fm)) {
+    const int np = p + 1;
+    RCF_TRY(workspace(ctx, WS_FM_CELL, sizeof(Real) * 4 * size_t(m->ncells) * np * np * np * nvec,
+                      reinterpret_cast<void**>(&E)));
+    RCF_TRY(launch_fm_cell<Real>(ctx, op, a.in, a.ld_in, dinv, E, nvec));
+  }
+  const int mode = form == RCF_FORM_H_DINV ? 3 : 2;
+  switch (p) {
+    case 1: RCF_TRY((launch_fm_z<Real, 1>(ctx, op, s1, s2, ld, E, mode, a))); break;
+    case 2: RCF_TRY((launch_fm_z<Real, 2>(ctx, op, s1, s2, ld, E, mode, a))); break;
+    case 3: RCF_TRY((launch_fm_z<Real, 3>(ctx, op, s1, s2, ld, E, mode, a))); break;
+    case 4: RCF_TRY((launch_fm_z<Real, 4>(ctx, op, s1, s2, ld, E, mode, a))); break;
+    case 5: RCF_TRY((launch_fm_z<Real, 5>(ctx, op, s1, s2, ld, E, mode, a))); break;
+    case 6: RCF_TRY((launch_fm_z<Real, 6>(ctx, op, s1, s2, ld, E, mode, a))); break;
+    case 7: RCF_TRY((launch_fm_z<Real, 7>(ctx, op, s1, s2, ld, E, mode, a))); break;
+    case 8: RCF_TRY((launch_fm_z<Real, 8>(ctx, op, s1, s2, ld, E, mode, a))); break;
+    default: return fail(ctx, RCF_ENOTSUP, "degree p=%d not built (1..8)", p);
+  }
+  // spin-orbit projectors onto out: the columns are stored as beta' = column / D_I, so the
+  // lumped operator's weights give P^H D^-1 in / P^H in and add D P C' / P C' (times A)
+  if (op->proj.natoms > 0) {
+    const size_t bytes = sizeof(Real) * 24 * size_t(op->proj.natoms) * nvec;
+    Real *Cc, *C2;
+    RCF_TRY(workspace(ctx, WS_NLC, bytes, reinterpret_cast<void**>(&Cc)));
+    RCF_TRY(workspace(ctx, WS_NLC2, bytes, reinterpret_cast<void**>(&C2)));
+    RCF_TRY((launch_nl_project<Real, Real>(ctx, op, a.in, a.ld_in, nvec, form == RCF_FORM_DINV_H ? 1 : 0, Cc)));
+    RCF_TRY(launch_nl_delta<Real>(ctx, op, Cc, nvec, a.A, C2));
+    RCF_TRY((launch_nl_addback<Real, Real>(ctx, op, C2, nvec, form == RCF_FORM_H_DINV ? 1 : 0, a.out, a.ld_out)));
+  }
+  return RCF_OK;
+}
+
 template <typename Real>
 int apply_full_fm(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real, Real>& a) {
   const int nvec = a.nvec;
   if (nvec == 0) return RCF_OK;
   if (a.rv_bfp) return fail(ctx, RCF_ENOTSUP, "BFP storage of R is not available with the full mass");
+  if (form == RCF_FORM_H_DINV || form == RCF_FORM_DINV_H) return apply_fm_fused<Real>(ctx, op, form, a);
   const int64_t ld = 2 * op->mesh->nnodes;
   const Real* u = a.in;
   int64_t ldu = a.ld_in;
@@ -574,6 +1021,12 @@ extern "C" int rcf_op_set_gauss(rcf_op* op, int nq) {
             T[size_t(a) * W + q - a + p] += sc * E[size_t(a) * np + q];
           }
         }
+    }
+  fm->el.assign(size_t(6) * np * np, 0.0);
+  for (int d = 0; d < 3; ++d)
+    for (int a = 0; a < np * np; ++a) {
+      fm->el[size_t(d) * np * np + a] = 0.5 * 2.0 / m->h[d] * m->K1[a];
+      fm->el[size_t(3 + d) * np * np + a] = m->h[d] / 2.0 * M1[a];
     }
   std::vector<float> t32(fm->tab.begin(), fm->tab.end()), b32(fm->B1.begin(), fm->B1.end());
   int st = upload_vec(ctx, &fm->d_tab64, fm->tab);

@@ -105,6 +105,9 @@ struct FullMass {
   // -p .. p: K = 1/2 (2 / h_d) K1 (stiffness), M = (h_d / 2) M1 (consistent mass);
   // layout [2 (K, M)][3][p][2p + 1]
   std::vector<double> tab;
+  // element matrices per direction d: K = 1/2 (2 / h_d) K1 and M = (h_d / 2) M1,
+  // layout [2 (K, M)][3][np][np]
+  std::vector<double> el;
   double* d_tab64 = nullptr;
   float* d_tab32 = nullptr;
   double* d_B1_64 = nullptr;      // [nq][np]
