@@ -89,14 +89,15 @@ __global__ void fm_pass_kernel(int d, int p, int Gx, int Gy, int Gz, const Real*
 template <typename Real, int P>
 __global__ void __launch_bounds__(256) fm_cell_kernel(int nq, int nx, int ny, int nz, const Real* __restrict__ B1,
                                                       const Real* __restrict__ vq, const Real* __restrict__ in,
-                                                      int64_t ldin, const double* __restrict__ dinv,
+                                                      int64_t ldin, const Real* __restrict__ dinv,
                                                       Real* __restrict__ E, int nvec, int NVB, int SB) {
   using V4 = R4<Real>;
   constexpr int NP = P + 1, NL = NP * NP * NP;
   extern __shared__ __align__(16) unsigned char fm_cell_smem[];
   V4* A = reinterpret_cast<V4*>(fm_cell_smem);   // [NVB][SB]
   V4* Bf = A + size_t(NVB) * SB;                  // [NVB][SB]
-  Real* B = reinterpret_cast<Real*>(Bf + size_t(NVB) * SB);   // [nq][NP]
+  V4* VQ = Bf + size_t(NVB) * SB;                 // [nq^3] the cell's w_q |J| (V, Bx, By, Bz)
+  Real* B = reinterpret_cast<Real*>(VQ + nq * nq * nq);   // [nq][NP]
   const int tid = threadIdx.x, nt = blockDim.x;
   const int64_t e = blockIdx.x;
   const int v0 = blockIdx.y * NVB, nvb = min(NVB, nvec - v0);
@@ -104,6 +105,10 @@ __global__ void __launch_bounds__(256) fm_cell_kernel(int nq, int nx, int ny, in
   const int Gx = nx * P, Gy = ny * P, Gz = nz * P;
   const int nq2 = nq * nq, nq3 = nq2 * nq;
   for (int i = tid; i < nq * NP; i += nt) B[i] = B1[i];
+  {
+    const V4* vc4 = reinterpret_cast<const V4*>(vq) + e * int64_t(nq3);
+    for (int i = tid; i < nq3; i += nt) VQ[i] = ldg4(vc4 + i);
+  }
   __syncthreads();
   // 1. gather and interpolate along x
   for (int t = tid; t < nvb * NP * NP; t += nt) {
@@ -121,12 +126,13 @@ __global__ void __launch_bounds__(256) fm_cell_kernel(int nq, int nx, int ny, in
       if (xx >= Gx) xx -= Gx;
       u[a] = ldg4(x + rowI + xx);
       if (dinv) {
-        const Real d = Real(dinv[rowI + xx]);
+        const Real d = dinv[rowI + xx];
 #pragma unroll
         for (int c4 = 0; c4 < 4; ++c4) u[a].v[c4] *= d;
       }
     }
     V4* out = A + size_t(j) * SB + nq * line;
+#pragma unroll 4
     for (int qx = 0; qx < nq; ++qx) {
       V4 s = zero4<Real>();
 #pragma unroll
@@ -144,6 +150,7 @@ __global__ void __launch_bounds__(256) fm_cell_kernel(int nq, int nx, int ny, in
 #pragma unroll
     for (int b = 0; b < NP; ++b) u[b] = src[qx + nq * (b + NP * c)];
     V4* out = Bf + size_t(j) * SB;
+#pragma unroll 4
     for (int qy = 0; qy < nq; ++qy) {
       V4 s = zero4<Real>();
 #pragma unroll
@@ -153,7 +160,6 @@ __global__ void __launch_bounds__(256) fm_cell_kernel(int nq, int nx, int ny, in
   }
   __syncthreads();
   // 3. along z to the points, the spinor potential, and back along z
-  const Real* vc = vq + 4 * e * int64_t(nq3);
   for (int t = tid; t < nvb * nq2; t += nt) {
     const int j = t / nq2, qxy = t - j * nq2;
     const V4* src = Bf + size_t(j) * SB;
@@ -163,12 +169,13 @@ __global__ void __launch_bounds__(256) fm_cell_kernel(int nq, int nx, int ny, in
       u[c] = src[qxy + nq2 * c];
       o[c] = zero4<Real>();
     }
+#pragma unroll 4
     for (int qz = 0; qz < nq; ++qz) {
       V4 w = zero4<Real>();
 #pragma unroll
       for (int c = 0; c < NP; ++c) fma4(w, B[qz * NP + c], u[c]);
-      const int q = qxy + nq2 * qz;
-      const Real V = vc[4 * q], Bx = vc[4 * q + 1], By = vc[4 * q + 2], Bz = vc[4 * q + 3];
+      const V4 pq = VQ[qxy + nq2 * qz];
+      const Real V = pq.v[0], Bx = pq.v[1], By = pq.v[2], Bz = pq.v[3];
       // up = (V + Bz) u_up + (Bx - i By) u_dn ; dn = (Bx + i By) u_up + (V - Bz) u_dn
       V4 h;
       h.v[0] = (V + Bz) * w.v[0] + Bx * w.v[2] + By * w.v[3];
@@ -191,6 +198,7 @@ __global__ void __launch_bounds__(256) fm_cell_kernel(int nq, int nx, int ny, in
     V4 o[NP];
 #pragma unroll
     for (int b = 0; b < NP; ++b) o[b] = zero4<Real>();
+#pragma unroll 4
     for (int qy = 0; qy < nq; ++qy) {
       const V4 w = src[qx + nq * (qy + nq * c)];
 #pragma unroll
@@ -208,6 +216,7 @@ __global__ void __launch_bounds__(256) fm_cell_kernel(int nq, int nx, int ny, in
     V4 o[NP];
 #pragma unroll
     for (int a = 0; a < NP; ++a) o[a] = zero4<Real>();
+#pragma unroll 4
     for (int qx = 0; qx < nq; ++qx) {
       const V4 w = src[qx];
 #pragma unroll
@@ -245,7 +254,7 @@ struct XYTile {
 template <typename Real, int P>
 __global__ void __launch_bounds__(XYTile<P>::THREADS) fm_xy_kernel(const XYTab<Real, P> tab, int Gx, int Gy,
                                                                    const Real* __restrict__ in, int64_t ldin,
-                                                                   const double* __restrict__ dinv,
+                                                                   const Real* __restrict__ dinv,
                                                                    Real* __restrict__ s1, Real* __restrict__ s2,
                                                                    int64_t lds) {
   using T = XYTile<P>;
@@ -279,7 +288,7 @@ __global__ void __launch_bounds__(XYTile<P>::THREADS) fm_xy_kernel(const XYTab<R
       if (xx < 0) xx += Gx;
       u[q] = ldg4(src + row + xx);
       if (dinv) {
-        const Real d = Real(dinv[zoff + row + xx]);
+        const Real d = dinv[zoff + row + xx];
 #pragma unroll
         for (int c4 = 0; c4 < 4; ++c4) u[q].v[c4] *= d;
       }
@@ -336,7 +345,7 @@ __global__ void __launch_bounds__(XYTile<P>::THREADS) fm_xy_kernel(const XYTab<R
       }
       const int64_t I = zoff + gx + int64_t(Gx) * (ye + b);
       st4(reinterpret_cast<V4*>(s1 + 2 * int64_t(v) * lds) + I, o1);
-      st4(reinterpret_cast<V4*>(s2 + 2 * int64_t(v) * lds) + I, o2);
+      if (s2) st4(reinterpret_cast<V4*>(s2 + 2 * int64_t(v) * lds) + I, o2);
     }
   }
 }
@@ -363,7 +372,7 @@ __global__ void __launch_bounds__(128) fm_z_kernel(const ZTab<Real, P> zt, int G
                                                    Real B, const Real* __restrict__ in, int64_t ldin, Real C,
                                                    const Real* prev, int64_t ldprev, const double* __restrict__ g,
                                                    const Real* __restrict__ rv, int64_t ldrv,
-                                                   const double* __restrict__ dinv, Real* out, int64_t ldout) {
+                                                   const Real* __restrict__ dinv, Real* out, int64_t ldout) {
   using V4 = R4<Real>;
   const int64_t plane = int64_t(Gx) * Gy;
   const int64_t col = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -402,7 +411,7 @@ __global__ void __launch_bounds__(128) fm_z_kernel(const ZTab<Real, P> zt, int G
             }
         }
       }
-      const Real a = mode == 2 ? Real(A * Real(dinv[I])) : A;
+      const Real a = mode == 2 ? A * dinv[I] : A;
       V4 o = zero4<Real>();
       fma4(o, a, t);
       if (in && B != Real(0)) fma4(o, B, ldg4(reinterpret_cast<const V4*>(in + 2 * int64_t(v) * ldin) + I));
@@ -638,10 +647,18 @@ int ws_block(rcf_ctx* ctx, int slot, const rcf_op* op, int nvec, Real** p) {
   return workspace(ctx, slot, sizeof(Real) * 4 * size_t(op->mesh->nnodes) * nvec, reinterpret_cast<void**>(p));
 }
 
+// 1 / M_I in the arithmetic type (the FP32 copy is the rounding of the FP64 one)
+template <typename Real>
+const Real* inv_mass_of(const rcf_mesh* m);
+template <>
+const double* inv_mass_of<double>(const rcf_mesh* m) { return m->d_inv_mass64; }
+template <>
+const float* inv_mass_of<float>(const rcf_mesh* m) { return m->d_inv_mass32; }
+
 // the per-cell Gauss-point potential for degree P: E (cell buffer, [nvec][cells][(P+1)^3]
 // tuples) from in (times dinv if given); vectors per block from the shared memory they need
 template <typename Real, int P>
-int launch_fm_cell_p(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ldin, const double* dinv, Real* E,
+int launch_fm_cell_p(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ldin, const Real* dinv, Real* E,
                      int nvec) {
   const rcf_mesh* m = op->mesh;
   const FullMass* fm = op->fm;
@@ -654,7 +671,7 @@ int launch_fm_cell_p(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ldi
   const int lines = std::max({NP * NP, nq * NP, nq * nq});
   const int NVB = int(std::max<size_t>(
       1, std::min<size_t>({8, size_t(256 / lines), size_t(96 * 1024) / per_vec, size_t(nvec)})));
-  const size_t smem = NVB * per_vec + sizeof(Real) * nq * NP;
+  const size_t smem = NVB * per_vec + sizeof(R4<Real>) * nq * nq * nq + sizeof(Real) * nq * NP;
   auto kern = fm_cell_kernel<Real, P>;
   if (smem > 48 * 1024) RCF_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   kern<<<dim3(unsigned(m->ncells), unsigned((nvec + NVB - 1) / NVB)), 256, smem, ctx->stream>>>(
@@ -663,7 +680,7 @@ int launch_fm_cell_p(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ldi
   return RCF_OK;
 }
 template <typename Real>
-int launch_fm_cell(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ldin, const double* dinv, Real* E,
+int launch_fm_cell(rcf_ctx* ctx, const rcf_op* op, const Real* in, int64_t ldin, const Real* dinv, Real* E,
                    int nvec) {
   switch (op->mesh->p) {
     case 1: return launch_fm_cell_p<Real, 1>(ctx, op, in, ldin, dinv, E, nvec);
@@ -722,44 +739,33 @@ int hamiltonian_fm(rcf_ctx* ctx, const rcf_op* op, const Real* u, int64_t ldu, i
 
 }  // namespace
 
-template <typename Real>
-int mass_apply_fm(rcf_ctx* ctx, const rcf_op* op, const Real* X, int64_t ldx, int nvec, Real* Y, int64_t ldy) {
-  const int64_t ld = 2 * op->mesh->nnodes;
-  Real *t1, *s1;
-  RCF_TRY(ws_block<Real>(ctx, WS_FM_T1, op, nvec, &t1));
-  RCF_TRY(ws_block<Real>(ctx, WS_FM_S1, op, nvec, &s1));
-  RCF_TRY(pass<Real>(ctx, op, 0, table<Real>(op, 1, 0), nullptr, nullptr, nullptr, X, nullptr, ldx, t1, nullptr,
-                     ld, nvec));
-  RCF_TRY(pass<Real>(ctx, op, 1, table<Real>(op, 1, 1), nullptr, nullptr, nullptr, t1, nullptr, ld, s1, nullptr,
-                     ld, nvec));
-  RCF_TRY(pass<Real>(ctx, op, 2, table<Real>(op, 1, 2), nullptr, nullptr, nullptr, s1, nullptr, ld, Y, nullptr,
-                     ldy, nvec));
-  return RCF_OK;
-}
-
 // the fused z pass for degree P
+// (mass_only: out = Mz s1, Mz in the slot that multiplies s1 and no second input)
 template <typename Real, int P>
 int launch_fm_z(rcf_ctx* ctx, const rcf_op* op, const Real* s1, const Real* s2, int64_t lds, const Real* E,
-                int mode, const StepArgs<Real, Real>& a) {
+                int mode, const StepArgs<Real, Real>& a, bool mass_only = false) {
   const rcf_mesh* m = op->mesh;
   const int np = P + 1;
   ZTab<Real, P> zt;
   for (int r = 0; r < np; ++r)
     for (int c = 0; c < np; ++c) {
-      zt.k[r][c] = Real(op->fm->el[size_t(2) * np * np + size_t(r) * np + c]);
-      zt.m[r][c] = Real(op->fm->el[size_t(5) * np * np + size_t(r) * np + c]);
+      const Real kz = Real(op->fm->el[size_t(2) * np * np + size_t(r) * np + c]);
+      const Real mz = Real(op->fm->el[size_t(5) * np * np + size_t(r) * np + c]);
+      zt.k[r][c] = mass_only ? mz : kz;
+      zt.m[r][c] = mass_only ? Real(0) : mz;
     }
+  if (mass_only) s2 = s1;   // read but multiplied by zero
   const int64_t cols = int64_t(m->G[0]) * m->G[1];
   fm_z_kernel<Real, P><<<dim3(unsigned((cols + 127) / 128), a.nvec), 128, 0, ctx->stream>>>(
       zt, m->G[0], m->G[1], m->G[2], s1, s2, lds, E, mode, a.A, a.B, a.in, a.ld_in, a.C, a.prev, a.ld_prev, a.g,
-      a.rv, a.ld_rv, m->d_inv_mass64, a.out, a.ld_out);
+      a.rv, a.ld_rv, inv_mass_of<Real>(m), a.out, a.ld_out);
   RCF_CHECK_LAUNCH(ctx);
   return RCF_OK;
 }
 
 // the fused x-y pass for degree P
 template <typename Real, int P>
-int launch_fm_xy(rcf_ctx* ctx, const rcf_op* op, const StepArgs<Real, Real>& a, const double* dinv, Real* s1,
+int launch_fm_xy(rcf_ctx* ctx, const rcf_op* op, const StepArgs<Real, Real>& a, const Real* dinv, Real* s1,
                  Real* s2, int64_t lds) {
   using T = XYTile<P>;
   const rcf_mesh* m = op->mesh;
@@ -796,7 +802,7 @@ int apply_fm_fused(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real
   Real *s1, *s2;
   RCF_TRY(ws_block<Real>(ctx, WS_FM_S1, op, nvec, &s1));
   RCF_TRY(ws_block<Real>(ctx, WS_FM_S2, op, nvec, &s2));
-  const double* dinv = form == RCF_FORM_H_DINV ? m->d_inv_mass64 : nullptr;
+  const Real* dinv = form == RCF_FORM_H_DINV ? inv_mass_of<Real>(m) : nullptr;
   switch (p) {
     case 1: RCF_TRY((launch_fm_xy<Real, 1>(ctx, op, a, dinv, s1, s2, ld))); break;
     case 2: RCF_TRY((launch_fm_xy<Real, 2>(ctx, op, a, dinv, s1, s2, ld))); break;
@@ -839,6 +845,32 @@ int apply_fm_fused(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real
     RCF_TRY((launch_nl_addback<Real, Real>(ctx, op, C2, nvec, form == RCF_FORM_H_DINV ? 1 : 0, a.out, a.ld_out)));
   }
   return RCF_OK;
+}
+
+// Y = M X: the x-y kernel's s1 = My Mx X and the z march with Mz (two launches)
+template <typename Real>
+int mass_apply_fm(rcf_ctx* ctx, const rcf_op* op, const Real* X, int64_t ldx, int nvec, Real* Y, int64_t ldy) {
+  const rcf_mesh* m = op->mesh;
+  if (nvec == 0) return RCF_OK;
+  if (m->G[2] > 65535 || nvec > 65535) return fail(ctx, RCF_ENOTSUP, "grid too large for the fused full-mass pass");
+  const int64_t ld = 2 * m->nnodes;
+  Real* s1;
+  RCF_TRY(ws_block<Real>(ctx, WS_FM_S1, op, nvec, &s1));
+  StepArgs<Real, Real> a{};
+  a.in = X; a.ld_in = ldx;
+  a.out = Y; a.ld_out = ldy;
+  a.A = Real(1); a.B = Real(0); a.C = Real(0);
+  a.nvec = nvec;
+  switch (m->p) {
+#define RCF_FM_MASS(P)                                                                     \
+    case P:                                                                                \
+      RCF_TRY((launch_fm_xy<Real, P>(ctx, op, a, nullptr, s1, nullptr, ld)));              \
+      return launch_fm_z<Real, P>(ctx, op, s1, nullptr, ld, nullptr, 3, a, true);
+    RCF_FM_MASS(1) RCF_FM_MASS(2) RCF_FM_MASS(3) RCF_FM_MASS(4)
+    RCF_FM_MASS(5) RCF_FM_MASS(6) RCF_FM_MASS(7) RCF_FM_MASS(8)
+#undef RCF_FM_MASS
+    default: return fail(ctx, RCF_ENOTSUP, "degree p=%d not built (1..8)", m->p);
+  }
 }
 
 template <typename Real>
