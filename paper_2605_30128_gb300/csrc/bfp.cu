@@ -90,6 +90,34 @@ __global__ void __launch_bounds__(kBfpThreads) bfp_decode_kernel(const unsigned 
   }
 }
 
+// Decode with 16-byte loads (stream and values 16-byte aligned): each warp takes a chunk of
+// 32 consecutive blocks, whose 192 (12 bits) or 160 (10 bits) stream bytes its first 12 or
+// 10 lanes load as 16-byte words into shared memory; then lane l assembles block l from
+// there, decodes it and stores its 4 values as one 16-byte word (coalesced across the
+// warp).  Chunks c < nchunks hold only whole 4-value groups; the caller decodes the rest
+// with bfp_decode_kernel.
+template <int NB>
+__global__ void __launch_bounds__(kBfpThreads) bfp_decode_vec_kernel(const uint4* __restrict__ s, int64_t nchunks,
+                                                                       float4* __restrict__ y) {
+  constexpr int V = NB - 2, BYTES = NB / 2, WORDS = 32 * BYTES / 16;   // 16-byte words per chunk: 12 or 10
+  static_assert(32 * BYTES % 16 == 0, "a chunk is whole 16-byte words");
+  __shared__ uint4 buf[kBfpThreads / 32][WORDS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t nw = int64_t(gridDim.x) * (blockDim.x / 32);
+  for (int64_t c = int64_t(blockIdx.x) * (blockDim.x / 32) + wid; c < nchunks; c += nw) {
+    if (lane < WORDS) buf[wid][lane] = __ldg(s + c * WORDS + lane);
+    __syncwarp();
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(buf[wid]) + lane * BYTES;
+    uint64_t w = 0;
+#pragma unroll
+    for (int j = 0; j < BYTES; ++j) w |= uint64_t(b[j]) << (8 * j);
+    float r[4];
+    bfp_decode4_fast<V>(w, r);
+    y[c * 32 + lane] = make_float4(r[0], r[1], r[2], r[3]);
+    __syncwarp();   // the chunk's words are read before the next chunk overwrites them
+  }
+}
+
 // 12-bit storage of a residual block (the FP32 recurrence with R kept as a BFP stream):
 // every block of x is encoded into s and x is overwritten by the decoded values, so
 // that the uses of R that read x and those that read s see the same numbers.  x is
@@ -186,14 +214,33 @@ extern "C" int rcf_bfp_decode(rcf_ctx* ctx, const void* stream, int64_t n, int n
   if (!ctx) return RCF_EINVAL;
   RCF_TRY(check_bfp_args(ctx, y, n, nbits, stream, "y"));
   if (n == 0) return RCF_OK;
-  const int64_t nblk = (n + 3) / 4;
   const int vec4 = (reinterpret_cast<uintptr_t>(y) % 16) == 0;
   const unsigned char* s = static_cast<const unsigned char*>(stream);
-  const unsigned grid = bfp_grid(nblk);
+  if (nbits != 16 && vec4 && (reinterpret_cast<uintptr_t>(stream) % 16) == 0) {
+    // whole chunks of 32 blocks through 16-byte words, the rest below
+    const int bpg = 32;
+    const int64_t ngroups = (n / 4) / bpg;
+    if (ngroups > 0) {
+      const unsigned g = unsigned(std::min<int64_t>((ngroups + kBfpThreads / 32 - 1) / (kBfpThreads / 32), 152 * 16));
+      if (nbits == 12)
+        bfp_decode_vec_kernel<12><<<g, kBfpThreads, 0, ctx->stream>>>(reinterpret_cast<const uint4*>(s), ngroups,
+                                                                          reinterpret_cast<float4*>(y));
+      else
+        bfp_decode_vec_kernel<10><<<g, kBfpThreads, 0, ctx->stream>>>(reinterpret_cast<const uint4*>(s), ngroups,
+                                                                          reinterpret_cast<float4*>(y));
+      RCF_CHECK_LAUNCH(ctx);
+    }
+    const int64_t done = ngroups * bpg * 4;   // values decoded
+    if (done == n) return RCF_OK;
+    s += done / 4 * bfp_bytes_per_block(nbits);
+    y += done;
+    n -= done;
+  }
+  const unsigned grid2 = bfp_grid((n + 3) / 4);
   switch (nbits) {
-    case 16: bfp_decode_kernel<16><<<grid, kBfpThreads, 0, ctx->stream>>>(s, n, y, vec4); break;
-    case 12: bfp_decode_kernel<12><<<grid, kBfpThreads, 0, ctx->stream>>>(s, n, y, vec4); break;
-    default: bfp_decode_kernel<10><<<grid, kBfpThreads, 0, ctx->stream>>>(s, n, y, vec4); break;
+    case 16: bfp_decode_kernel<16><<<grid2, kBfpThreads, 0, ctx->stream>>>(s, n, y, vec4); break;
+    case 12: bfp_decode_kernel<12><<<grid2, kBfpThreads, 0, ctx->stream>>>(s, n, y, vec4); break;
+    default: bfp_decode_kernel<10><<<grid2, kBfpThreads, 0, ctx->stream>>>(s, n, y, vec4); break;
   }
   RCF_CHECK_LAUNCH(ctx);
   return RCF_OK;

@@ -108,28 +108,31 @@ struct BlockIO<10> {
   }
 };
 
-// 12-bit block decode without integer-to-float conversions (same values as bfp_decode4<10>):
-// with k = e - 136 (the scale 2^(e_max - v + 1)), coefficient q is placed in the float
+// Block decode without integer-to-float conversions (same values as bfp_decode4<V>): with
+// k = e - 127 - V + 1 (the scale 2^(e_max - V + 1)), coefficient q is placed in the float
 // 3 2^22 + q by adding q to the bits of 3 2^22 (exact for |q| < 2^22), and one FMA
 // (3 2^22 + q) 2^k - 3 2^22 2^k gives q 2^k exactly: the product and the constant are exact
 // and their sum is representable.  Valid for -126 <= k <= 104 (2^k normal, 3 2^(22+k) finite);
 // zero blocks and the other exponents take the general path.
-__device__ __forceinline__ void bfp12_decode(uint64_t w, float y[4]) {
+template <int V>
+__device__ __forceinline__ void bfp_decode4_fast(uint64_t w, float y[4]) {
   const int e = int(w & 0xFFu);
-  const int k = e - 136;
+  const int k = e - 127 - V + 1;
   if (e != 0 && k >= -126 && k <= 104) {
     const float s = __int_as_float((k + 127) << 23);
     const float c = -12582912.0f * s;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const uint32_t fld = uint32_t(w >> (8 + 10 * i)) & 0x3FFu;   // q + 512 after flipping the sign bit
-      const float m = __int_as_float(int(0x4B400000u - 512u + (fld ^ 512u)));
+      // the field with its sign bit flipped is q + 2^(V-1)
+      const uint32_t fld = uint32_t(w >> (8 + V * i)) & ((1u << V) - 1u);
+      const float m = __int_as_float(int(0x4B400000u - (1u << (V - 1)) + (fld ^ (1u << (V - 1)))));
       y[i] = __fmaf_rn(m, s, c);
     }
   } else {
-    bfp_decode4<10>(w, y);
+    bfp_decode4<V>(w, y);
   }
 }
+__device__ __forceinline__ void bfp12_decode(uint64_t w, float y[4]) { bfp_decode4_fast<10>(w, y); }
 
 // Block b of a 12-bit stream (6 bytes at byte 6 b, as three little-endian 16-bit words)
 // read with one aligned 4-byte and one 2-byte load and no byte outside the block: for even
