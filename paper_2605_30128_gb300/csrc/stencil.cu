@@ -69,7 +69,12 @@ __global__ void __launch_bounds__(TX* TY, TileOf<Real, P>::MINB)
   const int tid = threadIdx.x;
   for (int i = tid; i < 2 * (P + 1) * (P + 1); i += NT) ST[i] = (&tab.c[0][0][0])[i];
 
-  const int lx = tid % TX, ly = tid / TX;
+  // FP64 is bound by the FP64 pipe: threads grouped by node class (tile_position), so that
+  // the element-vertex taps are executed by the vertex warps only.  FP32 is latency bound
+  // and keeps the row-major order (its rows of consecutive nodes read shared memory
+  // without bank conflicts).
+  int lx = tid % TX, ly = tid / TX;
+  if constexpr (sizeof(Real) == 8) tile_position<P, TX, TY>(tid, lx, ly);
   const int ntx = (Gx + TX - 1) / TX;
   const int x0 = (blockIdx.x % ntx) * TX;
   const int y0 = (blockIdx.x / ntx) * TY;
