@@ -197,3 +197,57 @@ def test_rchfsi_with_diagonal_D_reaches_full_mass_eigenpairs_chfsi_stalls(fm, sp
     floor = hist[-10:]
     assert min(floor) > 1e-3 and max(floor) / min(floor) < 1.01
     assert np.abs(lam[:nw] - ev[:nw]).max() > 1e-5
+
+
+@pytest.mark.parametrize("ncell,side,p,nq", [
+    ((3, 2, 2), (6.0, 4.0, 4.0), 2, 4),      # unequal edges
+    ((8, 2, 1), (16.0, 4.0, 2.0), 5, 7),     # two x tiles (the second ragged), a single z cell
+    ((1, 3, 2), (2.0, 6.0, 4.0), 7, 8),      # one x cell: a node is its own periodic image
+    ((1, 2, 1), (2.0, 4.0, 2.0), 8, 9),
+    ((4, 3, 2), (8.0, 6.0, 4.0), 1, 3),
+], ids=lambda v: str(v))
+def test_fused_forms_and_mass_across_meshes(ncell, side, p, nq):
+    """The fused full-mass kernels (x-y plane pass, per-cell potential, z march with the
+    combination; M X on the same kernels) against the oracle for several degrees, tile counts
+    and single-cell directions, with projectors: H D^-1 and D^-1 H combined with the recurrence
+    terms, in FP64 (1e-12) and FP32 (2e-6), and M X."""
+    import torch
+    from paper_2605_30128_gb300 import rchfsi as R
+    mesh = Mesh(ncell, side, p)
+    H0 = FullMassHamiltonian(mesh, nq, np.zeros((mesh.ncells, nq ** 3)))
+    xq = H0.gauss_coords().reshape(-1, 3)
+    V, B = _fields(xq)
+    atoms = np.array([[0.3 * side[0], 0.5 * side[1], 0.4 * side[2]]])
+    H = FullMassHamiltonian(mesh, nq, V.reshape(mesh.ncells, -1), B.reshape(3, mesh.ncells, -1), atoms,
+                            WIDTHS[:1], HCOUP[:1])
+    ctx = R.rcf_create(0)
+    gm = R.rcf_mesh_create(ctx, ncell, side, p)
+    op = R.rcf_op_create(ctx, gm)
+    try:
+        R.rcf_op_set_gauss(ctx, op, nq)
+        R.rcf_potential_set(ctx, op, V.reshape(mesh.ncells, -1), B.reshape(3, mesh.ncells, -1))
+        R.rcf_projectors_set(ctx, op, atoms, WIDTHS[:1], HCOUP[:1])
+        nv = 3
+        Zk = workloads.complex_normal(31, (H.N, nv))
+        Zm = workloads.complex_normal(32, (H.N, nv))
+        Rr = workloads.complex_normal(33, (H.N, nv))
+        g = np.array([0.4, -0.9, 1.3])
+        a, b, c = 0.37, -0.52, -0.81
+        Dinv = 1.0 / H.Mdiag[:, None]
+        for form in (R.RCF_FORM_DINV_H, R.RCF_FORM_H_DINV):
+            for prec, dt, tol in ((R.RCF_FP64, torch.complex128, 1e-12), (R.RCF_FP32, torch.complex64, 2e-6)):
+                cast = (lambda X: X.astype(np.complex64).astype(np.complex128)) if prec == R.RCF_FP32 else (lambda X: X)
+                zk, zm, rr = cast(Zk), cast(Zm), cast(Rr)
+                op_zk = Dinv * H.apply(zk) if form == R.RCF_FORM_DINV_H else H.apply(Dinv * zk)
+                ref = a * op_zk + b * zk + c * zm + rr * g[None, :]
+                out = torch.empty_like(to_dev(Zk, dt))
+                R.rcf_cheb_step(ctx, op, form, prec, to_dev(Zk, dt), to_dev(Zm, dt), to_dev(Rr, dt), a, b, c,
+                                torch.from_numpy(g).cuda(), out)
+                assert rel(to_host(out), ref) < tol, (form, prec)
+        Md = torch.zeros_like(to_dev(Zk))
+        R.rcf_mass_apply(ctx, op, to_dev(Zk), Md, R.RCF_FP64)
+        assert rel(to_host(Md), H.mass_apply(Zk)) < 1e-13
+    finally:
+        R.rcf_op_destroy(op)
+        R.rcf_mesh_destroy(gm)
+        R.rcf_destroy(ctx)
