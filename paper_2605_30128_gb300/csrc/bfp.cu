@@ -100,21 +100,31 @@ template <int NB>
 __global__ void __launch_bounds__(kBfpThreads) bfp_decode_vec_kernel(const uint4* __restrict__ s, int64_t nchunks,
                                                                        float4* __restrict__ y) {
   constexpr int V = NB - 2, BYTES = NB / 2, WORDS = 32 * BYTES / 16;   // 16-byte words per chunk: 12 or 10
+  constexpr int CH = 2;                                                // chunks in flight per warp
   static_assert(32 * BYTES % 16 == 0, "a chunk is whole 16-byte words");
-  __shared__ uint4 buf[kBfpThreads / 32][WORDS];
+  __shared__ uint4 buf[kBfpThreads / 32][CH][WORDS];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t nw = int64_t(gridDim.x) * (blockDim.x / 32);
-  for (int64_t c = int64_t(blockIdx.x) * (blockDim.x / 32) + wid; c < nchunks; c += nw) {
-    if (lane < WORDS) buf[wid][lane] = __ldg(s + c * WORDS + lane);
-    __syncwarp();
-    const unsigned char* b = reinterpret_cast<const unsigned char*>(buf[wid]) + lane * BYTES;
-    uint64_t w = 0;
+  for (int64_t c0 = int64_t(blockIdx.x) * (blockDim.x / 32) + wid; c0 < nchunks; c0 += CH * nw) {
 #pragma unroll
-    for (int j = 0; j < BYTES; ++j) w |= uint64_t(b[j]) << (8 * j);
-    float r[4];
-    bfp_decode4_fast<V>(w, r);
-    y[c * 32 + lane] = make_float4(r[0], r[1], r[2], r[3]);
-    __syncwarp();   // the chunk's words are read before the next chunk overwrites them
+    for (int h = 0; h < CH; ++h) {
+      const int64_t c = c0 + h * nw;
+      if (lane < WORDS && c < nchunks) buf[wid][h][lane] = __ldg(s + c * WORDS + lane);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < CH; ++h) {
+      const int64_t c = c0 + h * nw;
+      if (c >= nchunks) break;
+      const unsigned char* b = reinterpret_cast<const unsigned char*>(buf[wid][h]) + lane * BYTES;
+      uint64_t w = 0;
+#pragma unroll
+      for (int j = 0; j < BYTES; ++j) w |= uint64_t(b[j]) << (8 * j);
+      float r[4];
+      bfp_decode4_fast<V>(w, r);
+      y[c * 32 + lane] = make_float4(r[0], r[1], r[2], r[3]);
+    }
+    __syncwarp();   // the chunks' words are read before the next pass overwrites them
   }
 }
 
@@ -221,7 +231,7 @@ extern "C" int rcf_bfp_decode(rcf_ctx* ctx, const void* stream, int64_t n, int n
     const int bpg = 32;
     const int64_t ngroups = (n / 4) / bpg;
     if (ngroups > 0) {
-      const unsigned g = unsigned(std::min<int64_t>((ngroups + kBfpThreads / 32 - 1) / (kBfpThreads / 32), 152 * 16));
+      const unsigned g = unsigned(std::min<int64_t>((ngroups + kBfpThreads / 16 - 1) / (kBfpThreads / 16), 152 * 16));
       if (nbits == 12)
         bfp_decode_vec_kernel<12><<<g, kBfpThreads, 0, ctx->stream>>>(reinterpret_cast<const uint4*>(s), ngroups,
                                                                           reinterpret_cast<float4*>(y));
