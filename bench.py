@@ -474,9 +474,9 @@ def fullmass_leg(R, ctx, prob, w, dev, gen, timed, nvec=64):
         return {"vectors": nvec, "gauss_points_per_direction": nq, "step_ms": fm_ms, "lumped_step_ms": lumped_ms,
                 "ratio_to_lumped": fm_ms / lumped_ms, "mass_apply_ms": m_ms,
                 "step_algorithmic_gbs": alg / (fm_ms * 1e-3) / 1e9,
-                "note": "rcf_cheb_step, FP32, form H D^-1 with the consistent mass (three tensor-product "
-                        "passes, per-cell Gauss-point potential and node gather, projectors); algorithmic "
-                        "bytes as the lumped step's (32 B per unit)"}
+                "note": "rcf_cheb_step, FP32, form H D^-1 with the consistent mass (fused x-y pass per plane, "
+                        "per-cell Gauss-point potential, z march with the node gather and the combination, "
+                        "projectors); algorithmic bytes as the lumped step's (32 B per unit)"}
     except Exception as exc:
         return {"error": repr(exc)[:300]}
     finally:
