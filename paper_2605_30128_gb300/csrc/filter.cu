@@ -238,6 +238,29 @@ int rchfsi_step(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int k, const St*
   return apply_full<Real, St>(ctx, op, RCF_FORM_H_DINV, a);
 }
 
+// R-ChFSI coefficient table of a block (q + 1 rows of nvec): row 0: -Lambda; rows k = 1 .. q-1:
+// a_k Lambda_k (the R term of step k); row q: Lambda_q (the recovery)
+void rchfsi_table(const Cheb& ch, const double* lam_h, int nvec, int q, double* tab) {
+  std::vector<double> L;
+  ritz_filter_values(ch, lam_h, nvec, q, &L);
+  for (int v = 0; v < nvec; ++v) tab[v] = -lam_h[v];
+  for (int k = 1; k < q; ++k) {
+    const double ak = 2.0 * ch.sigma[k + 1] / ch.e;
+    for (int v = 0; v < nvec; ++v) tab[size_t(k) * nvec + v] = ak * L[size_t(k) * nvec + v];
+  }
+  for (int v = 0; v < nvec; ++v) tab[size_t(q) * nvec + v] = L[size_t(q) * nvec + v];
+}
+// the table into the context's coefficient slot (one host-to-device copy on the context's stream)
+int upload_rchfsi_table(rcf_ctx* ctx, const Cheb& ch, const double* lam_h, int nvec, int q, const double** out) {
+  std::vector<double> tab(size_t(q + 1) * nvec);
+  rchfsi_table(ch, lam_h, nvec, q, tab.data());
+  double* tab_d = nullptr;
+  RCF_TRY(workspace(ctx, WS_COEF, sizeof(double) * tab.size(), reinterpret_cast<void**>(&tab_d)));
+  RCF_CUDA(ctx, cudaMemcpyAsync(tab_d, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
+  *out = tab_d;
+  return RCF_OK;
+}
+
 // df: the residual in double-float arithmetic, written straight to its FP32 rounding
 // (FP32 recurrence, q >= 2); otherwise in FP64 and rounded by a separate pass.
 // bfp (FP32, q >= 2): R stored as a 12-bit BFP stream (Section III-C-3's block format, one
@@ -245,25 +268,17 @@ int rchfsi_step(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int k, const St*
 // values, and every step reads its g[v] R term from the stream (6 bytes per node and vector
 // instead of 16).  The recurrence is linear in R, so the storage rounding of R enters the
 // result as R-ChFSI applied to that rounding: an error proportional to ||R||.
+// tab_dev: the block's coefficient table already on the device (else it is built and uploaded).
 template <typename Real>
 int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
-                 int nvec, const double* lam_h, double* Y, int64_t ldy, bool df = false, bool bfp = false) {
+                 int nvec, const double* lam_h, double* Y, int64_t ldy, bool df = false, bool bfp = false,
+                 const double* tab_dev = nullptr) {
   const rcf_mesh* m = op->mesh;
   const int64_t rows = 2 * m->nnodes;
   const int64_t ld = rows;   // internal buffers: ld = 2M
   // device coefficient table: row 0: -Lambda; rows k=1..q-1: a_k Lambda_k; row q: Lambda_q
-  std::vector<double> L;
-  ritz_filter_values(ch, lam_h, nvec, q, &L);
-  std::vector<double> tab(size_t(q + 1) * nvec);
-  for (int v = 0; v < nvec; ++v) tab[v] = -lam_h[v];
-  for (int k = 1; k < q; ++k) {
-    const double ak = 2.0 * ch.sigma[k + 1] / ch.e;
-    for (int v = 0; v < nvec; ++v) tab[size_t(k) * nvec + v] = ak * L[size_t(k) * nvec + v];
-  }
-  for (int v = 0; v < nvec; ++v) tab[size_t(q) * nvec + v] = L[size_t(q) * nvec + v];
-  double* tab_d = nullptr;
-  RCF_TRY(workspace(ctx, WS_COEF, sizeof(double) * tab.size(), reinterpret_cast<void**>(&tab_d)));
-  RCF_CUDA(ctx, cudaMemcpyAsync(tab_d, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
+  const double* tab_d = tab_dev;
+  if (!tab_d) RCF_TRY(upload_rchfsi_table(ctx, ch, lam_h, nvec, q, &tab_d));
 
   const double s = ch.sigma[1] / ch.e;
   const double* lamq_d = tab_d + size_t(q) * nvec;
@@ -322,23 +337,13 @@ int rchfsi_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const do
 // returns exactly in the recovery), q >= 2.
 template <typename St>
 int rchfsi_block16(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, const double* X, int64_t ldx,
-                   int nvec, const double* lam_h, double* Y, int64_t ldy) {
-  if (q < 2) return rchfsi_block<float>(ctx, op, ch, q, X, ldx, nvec, lam_h, Y, ldy, true);
+                   int nvec, const double* lam_h, double* Y, int64_t ldy, const double* tab_dev = nullptr) {
+  if (q < 2) return rchfsi_block<float>(ctx, op, ch, q, X, ldx, nvec, lam_h, Y, ldy, true, false, tab_dev);
   const rcf_mesh* m = op->mesh;
   const int64_t rows = 2 * m->nnodes;
   const int64_t ld = rows;
-  std::vector<double> L;
-  ritz_filter_values(ch, lam_h, nvec, q, &L);
-  std::vector<double> tab(size_t(q + 1) * nvec);
-  for (int v = 0; v < nvec; ++v) tab[v] = -lam_h[v];
-  for (int k = 1; k < q; ++k) {
-    const double ak = 2.0 * ch.sigma[k + 1] / ch.e;
-    for (int v = 0; v < nvec; ++v) tab[size_t(k) * nvec + v] = ak * L[size_t(k) * nvec + v];
-  }
-  for (int v = 0; v < nvec; ++v) tab[size_t(q) * nvec + v] = L[size_t(q) * nvec + v];
-  double* tab_d = nullptr;
-  RCF_TRY(workspace(ctx, WS_COEF, sizeof(double) * tab.size(), reinterpret_cast<void**>(&tab_d)));
-  RCF_CUDA(ctx, cudaMemcpyAsync(tab_d, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, ctx->stream));
+  const double* tab_d = tab_dev;
+  if (!tab_d) RCF_TRY(upload_rchfsi_table(ctx, ch, lam_h, nvec, q, &tab_d));
   // R (double-float) -> FP32 rounding -> column scale -> 16-bit copy
   float* R32 = nullptr;
   RCF_TRY(workspace(ctx, WS_R32, sizeof(float) * 2 * size_t(ld) * nvec, reinterpret_cast<void**>(&R32)));
@@ -448,18 +453,19 @@ namespace rcf {
 namespace {
 
 // one band block of the filter in the requested mode and precision
+// tab: the block's R-ChFSI coefficient table on the device, or null (built and uploaded here)
 int filter_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, int mode, int prec, const double* X,
-                 int64_t ldx, int n, const double* lam, double* Y, int64_t ldy) {
+                 int64_t ldx, int n, const double* lam, double* Y, int64_t ldy, const double* tab = nullptr) {
   if (mode == RCF_RCHFSI) {
     switch (prec) {
-      case RCF_FP64: return rchfsi_block<double>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy);
-      case RCF_FP32: return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, false);
-      case RCF_FP32_DF: return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, true);
-      case RCF_FP16: return rchfsi_block16<__half>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy);
-      case RCF_BF16: return rchfsi_block16<__nv_bfloat16>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy);
+      case RCF_FP64: return rchfsi_block<double>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, false, false, tab);
+      case RCF_FP32: return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, false, false, tab);
+      case RCF_FP32_DF: return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, true, false, tab);
+      case RCF_FP16: return rchfsi_block16<__half>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, tab);
+      case RCF_BF16: return rchfsi_block16<__nv_bfloat16>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, tab);
       case RCF_FP32_BFP12:
         if (op->fm) return fail(ctx, RCF_ENOTSUP, "BFP storage of R is not available with the full mass");
-        return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, false, true);
+        return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, false, true, tab);
       default: return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
     }
   }
@@ -631,7 +637,7 @@ extern "C" int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64
     const double* Xb = X + 2 * int64_t(b0) * ldx;
     double* Yb = Y + 2 * int64_t(b0) * ldy;
     RCF_TRY(filter_block(ctx, op, ch, degree, mode, prec, Xb, ldx, n, ritz ? ritz + b0 : nullptr, Yb, ldy));
-    // the per-block coefficient table is a host vector copied asynchronously
+    // one block in flight at a time (the next block's table goes into the same device slot)
     RCF_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   }
   return check_device_error(ctx);
@@ -681,6 +687,23 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
     return RCF_OK;
   };
   auto count = [&](int b) { return std::min(nb, nvec - b * nb); };
+  // R-ChFSI: every block's coefficient table built and uploaded here, in one copy queued
+  // before the first block copy, so that no small host-to-device copy waits behind a block
+  // copy on the copy engine in the middle of the pipeline (a filter whose table upload is
+  // queued behind an 8 GB block copy starts only when that copy ends)
+  std::vector<size_t> tab_off(nblk + 1, 0);
+  const double* tabs_d = nullptr;
+  if (st == RCF_OK && mode == RCF_RCHFSI) {
+    for (int b = 0; b < nblk; ++b) tab_off[b + 1] = tab_off[b] + size_t(degree + 1) * count(b);
+    std::vector<double> tabs(tab_off[nblk]);
+    for (int b = 0; b < nblk; ++b) rchfsi_table(ch, ritz + int64_t(b) * nb, count(b), degree, tabs.data() + tab_off[b]);
+    double* d = nullptr;
+    st = workspace(ctx, WS_HTAB, sizeof(double) * tabs.size(), reinterpret_cast<void**>(&d));
+    if (st == RCF_OK)
+      st = cuda_check(ctx, cudaMemcpyAsync(d, tabs.data(), sizeof(double) * tabs.size(), cudaMemcpyHostToDevice,
+                                           ctx->stream));
+    tabs_d = d;
+  }
   // block b into its X slot once the block that used the slot before (b - S) is filtered
   auto copy_in = [&](int b) -> int {
     if (b >= S) RCF_TRY(cuda_check(ctx, cudaStreamWaitEvent(ctx->copy_in, ev_done[b - S], 0)));
@@ -697,21 +720,19 @@ extern "C" int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, 
       double* xs = dx(b);
       double* ys = dy(b);
       st = filter_block(ctx, op, ch, degree, mode, prec, xs, rows, n, ritz ? ritz + int64_t(b) * nb : nullptr,
-                        ys, rows);
+                        ys, rows, tabs_d ? tabs_d + tab_off[b] : nullptr);
     }
     if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_done[b], ctx->stream));
-    // The next block's copy is queued only now, behind this block's own small
-    // host-to-device copy (its coefficient table): host-to-device copies of one device
-    // run in issue order, and with every block copy queued up front each block's filter
-    // waited for them (measured: 966 ms per 1024 vectors against 714 ms for the filter
-    // and 211 ms for all copies).  The copy then runs while this block is filtered.
+    // The next block's copy is queued now and runs while this block is filtered (host-to-
+    // device copies of one device run in issue order; the coefficient tables went ahead of
+    // all block copies, above).
     if (st == RCF_OK && b + 1 < nblk) st = copy_in(b + 1);
     // copy the filtered block out while the next one is filtered
     if (st == RCF_OK) st = cuda_check(ctx, cudaStreamWaitEvent(ctx->copy_out, ev_done[b], 0));
     if (st == RCF_OK)
       st = copy_rows(Y + 2 * int64_t(b) * nb * ldy, ldy, dy(b), rows, n, cudaMemcpyDeviceToHost, ctx->copy_out);
     if (st == RCF_OK) st = cuda_check(ctx, cudaEventRecord(ev_out[b], ctx->copy_out));
-    // the per-block coefficient table is a host vector copied asynchronously
+    // one block of filter work in flight at a time: the next is queued once this one has run
     if (st == RCF_OK) st = cuda_check(ctx, cudaStreamSynchronize(ctx->stream));
   }
   // drain both copy streams (also on failure, before the events go away)

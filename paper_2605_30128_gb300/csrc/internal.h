@@ -158,7 +158,7 @@ enum WsSlot {
   WS_R64 = 0, WS_R32, WS_ZA, WS_ZB, WS_COEF, WS_NLC, WS_NLC2, WS_LANCZOS, WS_RR_W, WS_RR_S,
   WS_RR_T, WS_RR_INFO, WS_RR_WORK, WS_GRAD, WS_CKPT, WS_ADJ_A, WS_ADJ_B, WS_ADJ_C, WS_ADJ_U,
   WS_NORM, WS_DF_LAM, WS_DF_C2, WS_DF_NL, WS_HX0, WS_HY0, WS_R16, WS_SCALE, WS_GEMM_PART, WS_TC_A, WS_TC_B, WS_TC_E, WS_TC_C, WS_TC_Q, WS_PCG, WS_FM_U, WS_FM_T, WS_FM_T1, WS_FM_T2,
-  WS_FM_S1, WS_FM_S2, WS_FM_CELL, WS_FM_W, WS_RBFP, WS_COUNT
+  WS_FM_S1, WS_FM_S2, WS_FM_CELL, WS_FM_W, WS_RBFP, WS_HTAB, WS_COUNT
 };
 
 // ---------------------------------------------------------------------------
