@@ -28,6 +28,18 @@ __device__ __forceinline__ St from_real(Real x) {
   else return St(x);
 }
 
+// (re, im) of one complex value as a single 8-byte (float) or 16-byte (double) load
+__device__ __forceinline__ void ld_pair(const float* p, float& re, float& im) {
+  const float2 t = __ldg(reinterpret_cast<const float2*>(p));
+  re = t.x;
+  im = t.y;
+}
+__device__ __forceinline__ void ld_pair(const double* p, double& re, double& im) {
+  const double2 t = __ldg(reinterpret_cast<const double2*>(p));
+  re = t.x;
+  im = t.y;
+}
+
 template <typename Real>
 __device__ __forceinline__ Real warp_sum(Real x) {
 #pragma unroll
@@ -158,12 +170,15 @@ __global__ void nl_addback_kernel(const int* __restrict__ unode, const int* __re
       const Real b = beta[6 * int64_t(e) + f6];
 #pragma unroll
       for (int sg = 0; sg < 2; ++sg) {
+        // the complex coefficients of NV consecutive vectors, one (re, im) word each
         const Real* c = C2 + 2 * ((int64_t(a) * 12 + 2 * f6 + sg) * nvec + v0);
 #pragma unroll
         for (int j = 0; j < NV; ++j)
           if (j < nv) {
-            s[j][2 * sg + 0] += b * c[2 * j];
-            s[j][2 * sg + 1] += b * c[2 * j + 1];
+            Real re, im;
+            ld_pair(c + 2 * j, re, im);
+            s[j][2 * sg + 0] += b * re;
+            s[j][2 * sg + 1] += b * im;
           }
       }
     }
