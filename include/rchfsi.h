@@ -292,9 +292,12 @@ int rcf_residual_df(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx
 /* Y = filtered block of X, degree q = `degree` >= 1, bounds = {lambda_min,
  * lambda_T, lambda_max} (host; need lambda_min < lambda_T < lambda_max).
  * mode RCF_RCHFSI: R = H X - M X Lambda (FP64; double-float for
- * RCF_FP32_DF), Z_0 = 0, Z_1 = sigma_1 R / e,
- * the residual recurrence in `prec`, Lambda_k propagated in FP64, recovery
- * Y = D^{-1} Z_q + X Lambda_q in FP64.  mode RCF_CHFSI: Eq. ChFSIrecurrence
+ * RCF_FP32_DF, FP16 and BF16), Z_0 = 0, Z_1 = sigma_1 R / e,
+ * the residual recurrence in `prec` (RCF_FP32_BFP12: FP32 with R read from its
+ * 12-bit BFP stream), Lambda_k propagated in FP64, recovery
+ * Y = D^{-1} Z_q + X Lambda_q in FP64.  With the full mass (rcf_op_set_gauss)
+ * R uses the consistent M and the products its Gauss-point operator, with D
+ * the GLL-integrated diagonal (Section III-B-2); FP64 and FP32 only.  mode RCF_CHFSI: Eq. ChFSIrecurrence
  * with M^{-1} = D^{-1}; ritz may be NULL.  Vectors are processed in band
  * blocks of `block` columns (block <= 0: all at once).  X and Y are c128 and
  * must not overlap; ritz: host [nvec]. */
@@ -308,8 +311,10 @@ int rcf_filter(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int
  * copied out on two copy streams of the context while a block is filtered on
  * its compute stream, so copies and filtering overlap when X and Y are
  * page-locked (pinned) host memory; pageable memory works but its copies do
- * not overlap.  Device scratch: up to four blocks of `block` c128 vectors
- * besides the filter's own.  Synchronises; returns after Y is complete. */
+ * not overlap.  The coefficient tables of all blocks go to the device in one
+ * copy ahead of the first block copy.  Device scratch: up to four blocks of
+ * `block` c128 vectors besides the filter's own.  Synchronises; returns after Y
+ * is complete. */
 int rcf_filter_host(rcf_ctx* ctx, const rcf_op* op, const double* X, int64_t ldx, int nvec,
                     const double* ritz, int degree, const double bounds[3], int mode, int prec,
                     int block, double* Y, int64_t ldy);
