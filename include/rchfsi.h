@@ -85,7 +85,8 @@ typedef enum {
  * Zk, Zkm1 and out are complex64 and R is such a stream: block v * nnodes + I
  * holds node I of column v, 4-byte aligned, 6 nnodes nvec bytes.  The paper
  * uses the format for communicated data; this storage use is the library's.
- * Not available with the full mass (RCF_ENOTSUP); rejected by rcf_apply. */
+ * With the full mass it applies to the recurrence forms (rcf_cheb_step forms
+ * H D^-1 and D^-1 H); rejected by rcf_apply. */
 
 /* Filter form: plain ChFSI (Eq. ChFSIrecurrence) or R-ChFSI (Eq. rChFSIrecurrence). */
 typedef enum { RCF_CHFSI = 0, RCF_RCHFSI = 1 } rcf_mode;

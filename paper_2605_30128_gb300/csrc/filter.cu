@@ -464,7 +464,6 @@ int filter_block(rcf_ctx* ctx, const rcf_op* op, const Cheb& ch, int q, int mode
       case RCF_FP16: return rchfsi_block16<__half>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, tab);
       case RCF_BF16: return rchfsi_block16<__nv_bfloat16>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, tab);
       case RCF_FP32_BFP12:
-        if (op->fm) return fail(ctx, RCF_ENOTSUP, "BFP storage of R is not available with the full mass");
         return rchfsi_block<float>(ctx, op, ch, q, X, ldx, n, lam, Y, ldy, false, true, tab);
       default: return fail(ctx, RCF_EINVAL, "unknown precision %d", prec);
     }
@@ -535,7 +534,7 @@ extern "C" int rcf_cheb_step(rcf_ctx* ctx, const rcf_op* op, int form, int prec,
   const int64_t nn = op->mesh->nnodes;
   if (R && bfp) {
     if (!aligned(R, 4)) return fail(ctx, RCF_EINVAL, "R: the BFP stream must be 4-byte aligned");
-    if (op->fm) return fail(ctx, RCF_ENOTSUP, "BFP storage of R is not available with the full mass");
+    if (op->fm && form == RCF_FORM_H) return fail(ctx, RCF_ENOTSUP, "BFP storage of R applies to the recurrence forms");
   } else if (R) {
     RCF_TRY(check_block(ctx, op, R, ld, nvec, real, "R"));
   }

@@ -19,9 +19,11 @@
 // The spin-orbit projector columns int N_I beta are computed with the same Gauss rule at
 // set-up and applied by the nonlocal kernels of the lumped operator.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <vector>
 
+#include "bfp_common.cuh"
 #include "internal.h"
 #include "stencil_common.cuh"
 
@@ -364,7 +366,8 @@ struct ZTab {
 //   T = K u (the z pass) + the per-cell potential terms E of the up to 8 cells of the node
 //   mode 3 (H D^-1): out = A T + B in + C prev + g[v] rv
 //   mode 2 (D^-1 H): out = A dinv T + B in + C prev + g[v] rv
-// (in, prev, rv, E may be null).  Grid (ceil(Gx Gy / 128), nvec).
+// (in, prev, rv, E may be null; rv_bfp: R read from its 12-bit BFP stream instead of rv,
+// block v nnodes + node).  Grid (ceil(Gx Gy / 128), nvec).
 template <typename Real, int P>
 __global__ void __launch_bounds__(128) fm_z_kernel(const ZTab<Real, P> zt, int Gx, int Gy, int Gz,
                                                    const Real* __restrict__ s1, const Real* __restrict__ s2,
@@ -372,6 +375,7 @@ __global__ void __launch_bounds__(128) fm_z_kernel(const ZTab<Real, P> zt, int G
                                                    Real B, const Real* __restrict__ in, int64_t ldin, Real C,
                                                    const Real* prev, int64_t ldprev, const double* __restrict__ g,
                                                    const Real* __restrict__ rv, int64_t ldrv,
+                                                   const unsigned char* __restrict__ rv_bfp,
                                                    const Real* __restrict__ dinv, Real* out, int64_t ldout) {
   using V4 = R4<Real>;
   const int64_t plane = int64_t(Gx) * Gy;
@@ -384,7 +388,7 @@ __global__ void __launch_bounds__(128) fm_z_kernel(const ZTab<Real, P> zt, int G
   const V4* S1 = reinterpret_cast<const V4*>(s1 + 2 * int64_t(v) * lds) + col;
   const V4* S2 = reinterpret_cast<const V4*>(s2 + 2 * int64_t(v) * lds) + col;
   const V4* Ev = E ? reinterpret_cast<const V4*>(E) + int64_t(v) * nx * ny * nzc * NL : nullptr;
-  const Real gv = (rv && g) ? Real(g[v]) : Real(0);
+  const Real gv = ((rv || rv_bfp) && g) ? Real(g[v]) : Real(0);
   // x and y cells of this column: (cell, local) pairs, two at an element vertex
   int cxe[2], cxl[2], cye[2], cyl[2];
   const int ax = i % P, ay = j % P;
@@ -416,7 +420,18 @@ __global__ void __launch_bounds__(128) fm_z_kernel(const ZTab<Real, P> zt, int G
       fma4(o, a, t);
       if (in && B != Real(0)) fma4(o, B, ldg4(reinterpret_cast<const V4*>(in + 2 * int64_t(v) * ldin) + I));
       if (prev) fma4(o, C, ld4(reinterpret_cast<const V4*>(prev + 2 * int64_t(v) * ldprev) + I));
-      if (rv && g) fma4(o, gv, ldg4(reinterpret_cast<const V4*>(rv + 2 * int64_t(v) * ldrv) + I));
+      if (rv_bfp && g) {
+        if constexpr (std::is_same<Real, float>::value) {
+          uint32_t w, h;
+          const int64_t b = int64_t(v) * plane * Gz + I;
+          bfp12_fetch(rv_bfp, b, w, h);
+          V4 r;
+          bfp12_decode(bfp12_join(int(b & 1), w, h), r.v);
+          fma4(o, gv, r);
+        }
+      } else if (rv && g) {
+        fma4(o, gv, ldg4(reinterpret_cast<const V4*>(rv + 2 * int64_t(v) * ldrv) + I));
+      }
       st4(reinterpret_cast<V4*>(out + 2 * int64_t(v) * ldout) + I, o);
     }
   };
@@ -758,7 +773,7 @@ int launch_fm_z(rcf_ctx* ctx, const rcf_op* op, const Real* s1, const Real* s2, 
   const int64_t cols = int64_t(m->G[0]) * m->G[1];
   fm_z_kernel<Real, P><<<dim3(unsigned((cols + 127) / 128), a.nvec), 128, 0, ctx->stream>>>(
       zt, m->G[0], m->G[1], m->G[2], s1, s2, lds, E, mode, a.A, a.B, a.in, a.ld_in, a.C, a.prev, a.ld_prev, a.g,
-      a.rv, a.ld_rv, inv_mass_of<Real>(m), a.out, a.ld_out);
+      a.rv, a.ld_rv, a.rv_bfp, inv_mass_of<Real>(m), a.out, a.ld_out);
   RCF_CHECK_LAUNCH(ctx);
   return RCF_OK;
 }
@@ -877,8 +892,10 @@ template <typename Real>
 int apply_full_fm(rcf_ctx* ctx, const rcf_op* op, int form, const StepArgs<Real, Real>& a) {
   const int nvec = a.nvec;
   if (nvec == 0) return RCF_OK;
-  if (a.rv_bfp) return fail(ctx, RCF_ENOTSUP, "BFP storage of R is not available with the full mass");
+  if (a.rv_bfp && !std::is_same<Real, float>::value)
+    return fail(ctx, RCF_ENOTSUP, "a BFP residual stream needs FP32 storage");
   if (form == RCF_FORM_H_DINV || form == RCF_FORM_DINV_H) return apply_fm_fused<Real>(ctx, op, form, a);
+  if (a.rv_bfp) return fail(ctx, RCF_ENOTSUP, "BFP storage of R applies to the recurrence forms only");
   const int64_t ld = 2 * op->mesh->nnodes;
   const Real* u = a.in;
   int64_t ldu = a.ld_in;

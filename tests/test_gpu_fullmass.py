@@ -131,8 +131,6 @@ def test_unsupported_paths_are_refused(fm):
     Y = torch.zeros_like(X)
     for fn in (lambda: R.rcf_filter(fm.ctx, fm.op, X, np.zeros(2), 4, (-1.0, 0.0, 50.0), R.RCF_RCHFSI,
                                     R.RCF_FP32_DF, 0, Y),
-               lambda: R.rcf_filter(fm.ctx, fm.op, X, np.zeros(2), 4, (-1.0, 0.0, 50.0), R.RCF_RCHFSI,
-                                    R.RCF_FP32_BFP12, 0, Y),
                lambda: R.rcf_apply_noalloc(fm.ctx, fm.op, 0, X, Y, R.RCF_FP64)):
         with pytest.raises(R.RcfError) as ei:
             fn()
@@ -251,3 +249,44 @@ def test_fused_forms_and_mass_across_meshes(ncell, side, p, nq):
         R.rcf_op_destroy(op)
         R.rcf_mesh_destroy(gm)
         R.rcf_destroy(ctx)
+
+
+def test_bfp_stored_residual_with_the_full_mass(fm, spectrum):
+    """R kept as a 12-bit BFP stream with the full mass: the step given a stream of the oracle's
+    codec equals, bit for bit, the FP32 step given the decoded R; the filter matches the FP64
+    recurrence on the BFP rounding of the oracle's residual (full M) within the FP32
+    recurrence's own error."""
+    import torch
+    from lowprec_emulation import rchfsi_filter_bfp_residual, rchfsi_filter_fp32
+    from oracle import rayleigh_ritz
+    from oracle.bfp import bfp_decode, bfp_encode
+    from paper_2605_30128_gb300 import rchfsi as R
+    H = fm.H
+    nv = 3
+    Zk = to_dev(workloads.complex_normal(41, (H.N, nv)), torch.complex64)
+    Zm = to_dev(workloads.complex_normal(42, (H.N, nv)), torch.complex64)
+    Rr = workloads.complex_normal(43, (H.N, nv))
+    vals = np.ascontiguousarray(Rr.T).astype(np.complex64).view(np.float32).ravel()
+    s = bfp_encode(vals, 12)
+    Rdec = bfp_decode(s, vals.size, 12).astype(np.float32).view(np.complex64).reshape(nv, -1)
+    stream = torch.from_numpy(np.frombuffer(s.tobytes(), dtype=np.uint8).copy()).cuda()
+    g = torch.tensor([0.5, -1.2, 0.8], dtype=torch.float64, device="cuda")
+    for form in (R.RCF_FORM_H_DINV, R.RCF_FORM_DINV_H):
+        ob, of = torch.empty_like(Zk), torch.empty_like(Zk)
+        R.rcf_cheb_step(fm.ctx, fm.op, form, R.RCF_FP32_BFP12, Zk, Zm, stream, 0.3, -0.4, -0.9, g, ob)
+        R.rcf_cheb_step(fm.ctx, fm.op, form, R.RCF_FP32, Zk, Zm, torch.from_numpy(Rdec).cuda(), 0.3, -0.4, -0.9,
+                        g, of)
+        assert torch.equal(torch.view_as_real(ob), torch.view_as_real(of))
+    _, lmax = spectrum
+    X, lam = rayleigh_ritz(H, workloads.complex_normal(44, (H.N, 8)))
+    b = (float(lam.min()), float(lam.max()), lmax)
+    Xd = to_dev(X)
+    Yd = torch.zeros_like(Xd)
+    R.rcf_filter(fm.ctx, fm.op, Xd, lam, 8, b, R.RCF_RCHFSI, R.RCF_FP32_BFP12, 0, Yd)
+    emul = rchfsi_filter_bfp_residual(H, X, lam, *b, 8, 12)
+    ref = rchfsi_filter_fp32(H, X, lam, *b, 8)
+    from oracle import rchfsi_filter
+    exact = rchfsi_filter(H, X, lam, *b, 8)
+    e32 = rel(ref, exact)
+    assert rel(to_host(Yd), emul) < 3 * e32 + 1e-12, (rel(to_host(Yd), emul), e32)
+    assert rel(emul, exact) > 10 * e32      # the 12-bit storage is what separates them
