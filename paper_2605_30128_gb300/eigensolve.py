@@ -4,6 +4,8 @@ phase timed on the stream: residual check, filter, Cholesky-QR2, Rayleigh-Ritz.
     python -m paper_2605_30128_gb300.eigensolve --workload cfg5 --cycles 2
     python -m paper_2605_30128_gb300.eigensolve --workload cfg3 --nvec 256 --block 256 \\
         --cycles 30 --tol 1e-8 --nwanted 224
+    python -m paper_2605_30128_gb300.eigensolve --workload cfg4 --gauss 6 --cycles 40 \\
+        --runs rchfsi_fp64,rchfsi_fp32,chfsi_fp64      # full consistent mass, diagonal D
 
 Every run starts from the same seeded block and the same initial Rayleigh-Ritz step, then
 runs each requested filter (default: mixed R-ChFSI with the double-float residual, mixed
@@ -50,13 +52,30 @@ class Timer:
         return out, self.e0.elapsed_time(self.e1)
 
 
-def run(w, runs, cycles, tol, nwanted, seed=0, device=0, rr_arith=None):
+def use_full_mass(prob, w, nq):
+    """Switch the problem's operator to the full consistent mass with nq Gauss points per
+    direction (Section III-A; Section III-B-2): the same synthetic V, B and projectors,
+    V and B evaluated at the Gauss points."""
+    ctx, op = prob.ctx, prob.op
+    R.rcf_op_set_gauss(ctx, op, nq)
+    xq = R.rcf_op_gauss_points(ctx, op, prob.ncells, nq).reshape(-1, 3)
+    prm = prob.params
+    V = workloads.gaussian_sum_potential(xq, prm["centres"], prm["depths"], prm["widths"], prm["L"])
+    B = workloads.smooth_periodic_field(xq, prm["kvec"], prm["amps"], prm["phases"], prm["L"], prm["bmax"])
+    R.rcf_potential_set(ctx, op, V.reshape(prob.ncells, -1), B.reshape(3, prob.ncells, -1))
+    if w.natoms > 0:
+        R.rcf_projectors_set(ctx, op, prm["atoms"], prm["proj_width"], prm["proj_h"])
+
+
+def run(w, runs, cycles, tol, nwanted, seed=0, device=0, rr_arith=None, gauss=0):
     import torch
     dev = torch.device("cuda", device)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
     tm = Timer(torch, stream)
     prob = GPUProblem(w, device=device, stream=stream)
+    if gauss:
+        use_full_mass(prob, w, gauss)
     ctx, op = prob.ctx, prob.op
     if rr_arith is not None:
         R.rcf_set_rr_arith(ctx, rr_arith)
@@ -76,7 +95,8 @@ def run(w, runs, cycles, tol, nwanted, seed=0, device=0, rr_arith=None):
     X = torch.empty_like(Xinit)
     cn = torch.zeros(nvec, dtype=torch.float64, device=dev)
     out = {"workload": f"{w.name}: {w.ncell}^3 cells, p={w.p}, {N:,} complex DoF, {w.natoms} atoms, "
-                       f"{nvec} vectors in blocks of {w.block}, degree {w.degree}",
+                       f"{nvec} vectors in blocks of {w.block}, degree {w.degree}"
+                       + (f", full consistent mass with {gauss}^3 Gauss points per cell" if gauss else ""),
            "lanczos_ms": t_lz, "initial_cholqr2_ms": t_q0, "initial_rr_ms": t_r0,
            "lambda_max": lmax, "nwanted": nwanted, "tol": tol, "runs": {}}
     ref_name, ref_lam = None, None
@@ -141,6 +161,8 @@ def main(argv=None):
     ap.add_argument("--nwanted", type=int, default=None,
                     help="wanted vectors (default: all but a buffer of max(4, nvec/10))")
     ap.add_argument("--runs", default="rchfsi_fp32_df,rchfsi_fp32,chfsi_fp64")
+    ap.add_argument("--gauss", type=int, default=0,
+                    help="full consistent mass with this many Gauss points per direction (0: lumped)")
     ap.add_argument("--rr", default="tc", choices=["fp64", "df", "tc", "mixed"],
                     help="tall products of Cholesky-QR2 and Rayleigh-Ritz: cuBLAS FP64, double-float, tensor "
                          "cores, or tensor cores with the mixed-precision rotation")
@@ -157,7 +179,7 @@ def main(argv=None):
     t0 = time.time()
     out = run(w, runs, a.cycles, a.tol, nw,
               rr_arith={"fp64": R.RCF_RR_FP64, "df": R.RCF_RR_DF, "tc": R.RCF_RR_TC,
-                        "mixed": R.RCF_RR_MIXED}[a.rr])
+                        "mixed": R.RCF_RR_MIXED}[a.rr], gauss=a.gauss)
     out["rr_arith"] = a.rr
     out["wall_s"] = time.time() - t0
     print(json.dumps(out), flush=True)
